@@ -1,0 +1,458 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+None of these checks re-types the oracle's own formula: each compares the
+oracle with a closed form, a brute-force computation written differently, a
+library routine for a special case, or an invariant.  A dropped term, a wrong
+sign or a transposed index in the oracle fails at least one of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.special
+
+import oracle
+
+LOG2PIE_HALF = 1.4189385332046727  # entropy of N(0,1), the 1.4189 of the padding section
+
+
+# ---------------------------------------------------------------- helpers
+def cofactor_det(A):
+    """Determinant by Laplace expansion along the first row (tiny n only)."""
+    n = len(A)
+    if n == 0:
+        return 1.0
+    if n == 1:
+        return A[0][0]
+    s = 0.0
+    for j in range(n):
+        minor = [row[:j] + row[j + 1:] for row in A[1:]]
+        s += (-1) ** j * A[0][j] * cofactor_det(minor)
+    return s
+
+
+def entropy_bf(S, idx):
+    if len(idx) == 0:
+        return 0.0
+    sub = [[S[a][b] for b in idx] for a in idx]
+    return 0.5 * (len(idx) * math.log(2 * math.pi * math.e) + math.log(cofactor_det(sub)))
+
+
+def measures_bf(S, idx):
+    """TC/DTC/O/S from eqs. TC, DTC, O-info, S-info with cofactor determinants."""
+    k = len(idx)
+    HS = entropy_bf(S, idx)
+    singles = [entropy_bf(S, [i]) for i in idx]
+    loo = [entropy_bf(S, [i for i in idx if i != j]) for j in idx]
+    tc = sum(singles) - HS
+    dtc = HS - sum(HS - h for h in loo)
+    return np.array([HS, tc, dtc, tc - dtc, tc + dtc])
+
+
+def rand_spd(rng, n, ridge=0.3):
+    W = rng.standard_normal((n, n))
+    A = W @ W.T + ridge * np.eye(n)
+    return A
+
+
+# ---------------------------------------------------------------- counts
+@pytest.mark.parametrize("N", [3, 5, 10, 20, 30, 40, 60])
+def test_count_formula(N):
+    # Supp. eq. comb: sum_{k=3}^{N} C(N,k) = 2^N - 1 - N - N(N-1)/2
+    assert oracle.count(N, range(3, N + 1)) == 2 ** N - 1 - N - N * (N - 1) // 2
+
+
+def test_count_c4():
+    assert oracle.count(60, [3, 4, 5]) == 34220 + 487635 + 5461512 == 5983367
+
+
+# ---------------------------------------------------------------- enumeration
+@pytest.mark.parametrize("N", [1, 2, 4, 6])
+def test_enumeration_bruteforce(N):
+    orders = list(range(1, N + 1))
+    got = oracle.enumerate_subsets(N, orders)
+    exp = []
+    for k in orders:
+        subs = [tuple(i for i in range(N) if (m >> i) & 1) for m in range(1 << N)
+                if bin(m).count("1") == k]
+        exp += sorted(subs)  # lexicographic order of the sorted tuple
+    assert len(got) == len(exp)
+    for row, e in zip(got, exp):
+        assert tuple(int(x) for x in row if x >= 0) == e
+
+
+def test_enumeration_itertools_n12():
+    N, orders = 12, [5, 3, 7]  # caller's order list is honoured
+    got = oracle.enumerate_subsets(N, orders)
+    exp = [c for k in orders for c in itertools.combinations(range(N), k)]
+    assert len(got) == len(exp)
+    for row, e in zip(got, exp):
+        assert tuple(int(x) for x in row if x >= 0) == e
+
+
+def test_unrank_counting_matches_successor():
+    N, orders = 14, list(range(1, 15))
+    walk = oracle.enumerate_subsets(N, orders)
+    ids = np.arange(len(walk), dtype=np.uint64)
+    un = oracle.unrank_ids(N, orders, ids)
+    assert np.array_equal(walk, un)
+
+
+def test_unrank_n30_spot():
+    N, orders = 30, list(range(3, 31))
+    rng = np.random.default_rng(5)
+    total = oracle.count(N, orders)
+    ids = np.unique(np.concatenate([rng.integers(0, total, 2000, dtype=np.uint64),
+                                    np.array([0, total - 1], dtype=np.uint64)]))
+    sub = oracle.unrank_ids(N, orders, ids)
+    offs = np.cumsum([0] + [math.comb(N, k) for k in orders])
+    for gid, row in zip(ids, sub):
+        s = int(np.searchsorted(offs[1:], gid, side="right"))
+        k = orders[s]
+        r = int(gid) - int(offs[s])
+        c = tuple(int(x) for x in row if x >= 0)
+        assert len(c) == k and list(c) == sorted(set(c))
+        # lexicographic rank of c by counting the subsets that precede it
+        rk, prev = 0, -1
+        for i, ci in enumerate(c):
+            for x in range(prev + 1, ci):
+                rk += math.comb(N - 1 - x, k - 1 - i)
+            prev = ci
+        assert rk == r
+
+
+# ---------------------------------------------------------------- measures
+def test_identity_all_zero():
+    # Sigma = I: H = k * 1/2 log(2 pi e); all dependence measures vanish
+    for k in range(1, 7):
+        out, fl = oracle.measures(np.eye(6), [k])
+        assert not fl.any()
+        np.testing.assert_allclose(out[0], k * LOG2PIE_HALF, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(out[1:], 0.0, rtol=0, atol=1e-13)
+
+
+def _equicorr_logdet(k, rho):
+    return (k - 1) * math.log(1 - rho) + math.log(1 + (k - 1) * rho)
+
+
+@pytest.mark.parametrize("rho", [-0.08, 0.1, 0.5, 0.9])
+def test_equicorrelated_closed_form(rho):
+    N = 9
+    S = np.full((N, N), rho) + (1 - rho) * np.eye(N)
+    for k in range(2, N + 1):
+        out, _ = oracle.measures(S, [k], 0, 1)
+        ld = _equicorr_logdet(k, rho)
+        tc = -0.5 * ld
+        dtc = 0.5 * (k * _equicorr_logdet(k - 1, rho) - (k - 1) * ld)
+        np.testing.assert_allclose(out[:, 0], [0.5 * (k * math.log(2 * math.pi * math.e) + ld),
+                                               tc, dtc, tc - dtc, tc + dtc], rtol=0, atol=1e-12)
+
+
+def test_pair_mi_equivalence():
+    # eqs. MI-tc and MI-dtc coincide for two variables: O = 0, TC = DTC = MI
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        a, b = rng.uniform(0.2, 3.0, 2)
+        rho = rng.uniform(-0.99, 0.99)
+        S = np.array([[a, rho * math.sqrt(a * b)], [rho * math.sqrt(a * b), b]])
+        out, _ = oracle.measures(S, [2])
+        mi = -0.5 * math.log(1 - rho * rho)
+        np.testing.assert_allclose(out[1:4, 0], [mi, mi, 0.0], rtol=0, atol=1e-12)
+
+
+def test_tc_dtc_nonnegative():
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        S = rand_spd(rng, 8)
+        out, _ = oracle.measures(S, range(2, 9))
+        assert (out[1] > -1e-12).all() and (out[2] > -1e-12).all()
+
+
+def _rsys(n, c):
+    S = np.full((n + 1, n + 1), c * c)
+    S[np.arange(n), np.arange(n)] = c * c + 1
+    S[:n, n] = S[n, :n] = c
+    S[n, n] = 1.0
+    return S
+
+
+def _ssys(n, c):
+    S = np.eye(n + 1)
+    S[:n, n] = S[n, :n] = c
+    S[n, n] = n * c * c + 1
+    return S
+
+
+def _closed_measures(logdet, var, idx):
+    """TC/DTC/O from a closed-form logdet(idx) (entropy definitions)."""
+    k = len(idx)
+    L = logdet(idx)
+    tc = 0.5 * (sum(math.log(var(i)) for i in idx) - L)
+    dtc = 0.5 * L - sum(0.5 * L - 0.5 * logdet([i for i in idx if i != j]) for j in idx)
+    return tc, dtc, tc - dtc
+
+
+@pytest.mark.parametrize("c", [0.5, 1.0])
+def test_r_and_s_systems(c):
+    n = 6
+    # R-system (tail-to-tail, PGM section): det of m X's = 1 + m c^2, with Y: 1
+    R = _rsys(n, c)
+    r_ld = lambda idx: 0.0 if n in idx else math.log(1 + len(idx) * c * c)
+    r_var = lambda i: 1.0 if i == n else c * c + 1
+    # S-system (head-to-head): det of m X's = 1, with Y: 1 + (n - m) c^2
+    S = _ssys(n, c)
+    s_ld = lambda idx: math.log(1 + (n - (len(idx) - 1)) * c * c) if n in idx else 0.0
+    s_var = lambda i: n * c * c + 1 if i == n else 1.0
+    orders = list(range(3, n + 2))
+    outR, _ = oracle.measures(R, orders)
+    outS, _ = oracle.measures(S, orders)
+    subs = oracle.enumerate_subsets(n + 1, orders)
+    for q, row in enumerate(subs):
+        idx = [int(x) for x in row if x >= 0]
+        np.testing.assert_allclose(outR[1:4, q], _closed_measures(r_ld, r_var, idx), atol=1e-12)
+        np.testing.assert_allclose(outS[1:4, q], _closed_measures(s_ld, s_var, idx), atol=1e-12)
+        # sign convention of eq. O-info: redundancy > 0, synergy < 0
+        assert outR[3, q] > 1e-9
+        if n in idx:
+            assert outS[3, q] < -1e-9
+        else:
+            assert abs(outS[3, q]) < 1e-12
+
+
+def test_additivity_independent_blocks():
+    # independent blocks: every measure of A u B is the sum over the blocks
+    rng = np.random.default_rng(3)
+    A, B = rand_spd(rng, 3), rand_spd(rng, 4)
+    S = np.zeros((7, 7))
+    S[:3, :3], S[3:, 3:] = A, B
+    full, _ = oracle.measures(S, [7])
+    a, _ = oracle.measures(A, [3])
+    b, _ = oracle.measures(B, [4])
+    np.testing.assert_allclose(full[:, 0], a[:, 0] + b[:, 0], atol=1e-12)
+
+
+@pytest.mark.parametrize("N", [3, 4, 5, 6])
+def test_bruteforce_cofactor(N):
+    rng = np.random.default_rng(10 + N)
+    S = rand_spd(rng, N)
+    orders = list(range(1, N + 1))
+    out, fl = oracle.measures(S, orders)
+    subs = oracle.enumerate_subsets(N, orders)
+    Sl = S.tolist()
+    for q, row in enumerate(subs):
+        idx = [int(x) for x in row if x >= 0]
+        np.testing.assert_allclose(out[:, q], measures_bf(Sl, idx), rtol=1e-11, atol=1e-11)
+
+
+def test_padding_identity():
+    # padding Sigma_S with an independent identity block adds (n-k) * 1.4189
+    rng = np.random.default_rng(4)
+    A = rand_spd(rng, 4)
+    P = np.eye(7)
+    P[:4, :4] = A
+    h_pad = oracle.entropy(P, range(7))
+    h = oracle.entropy(A, range(4))
+    assert abs(h_pad - (h + 3 * LOG2PIE_HALF)) < 1e-12
+
+
+def test_not_pd_marked():
+    S = np.eye(5)
+    S[0, 1] = S[1, 0] = 1.0  # duplicated variable: singular
+    out, fl = oracle.measures(S, [2, 3])
+    subs = oracle.enumerate_subsets(5, [2, 3])
+    for q, row in enumerate(subs):
+        bad = 0 in row and 1 in row
+        assert bool(fl[q]) == bad
+        assert np.isnan(out[:, q]).all() == bad
+
+
+def test_measures_ids_match_range():
+    rng = np.random.default_rng(6)
+    S = rand_spd(rng, 12)
+    orders = list(range(3, 13))
+    full, _ = oracle.measures(S, orders)
+    ids = rng.choice(full.shape[1], 300, replace=False).astype(np.uint64)
+    part, _ = oracle.measures_ids(S, orders, ids)
+    np.testing.assert_array_equal(part, full[:, ids.astype(np.int64)])
+
+
+# ---------------------------------------------------------------- copula front end
+def test_ndtri_library_and_roundtrip():
+    us = np.concatenate([np.linspace(1e-4, 1 - 1e-4, 997), [0.5, 1 / 2001, 2000 / 2001]])
+    for u in us:
+        z = oracle.ndtri(u)
+        assert abs(z - scipy.special.ndtri(u)) < 2e-14 * max(1.0, abs(z))
+        if u <= 0.5:
+            # the best double z misses u by at most phi(z) * ulp(z) / 2, plus
+            # the rounding of erfc itself (relative, a few ulp)
+            phi = math.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+            tol = phi * math.ulp(z) + 6e-16 * u
+            assert abs(0.5 * math.erfc(-z / math.sqrt(2)) - u) <= tol
+    assert oracle.ndtri(0.5) == 0.0
+    T = 999
+    for r in range(T):
+        assert oracle.ndtri_ratio(r + 1, T + 1) == -oracle.ndtri_ratio(T - r, T + 1)
+
+
+def test_rank_bruteforce_with_ties():
+    rng = np.random.default_rng(7)
+    T, N = 40, 5
+    X = rng.integers(-3, 4, size=(T, N)).astype(np.float64)  # many ties
+    X[3, 0], X[9, 0] = -0.0, 0.0
+    R = oracle.rank(X)
+    for j in range(N):
+        for t in range(T):
+            exp = sum(1 for s in range(T) if X[s, j] < X[t, j]) + \
+                  sum(1 for s in range(t) if X[s, j] == X[t, j])
+            assert R[t, j] == exp
+        assert sorted(R[:, j]) == list(range(T))
+
+
+def test_rank_rejects_nan():
+    X = np.ones((5, 2))
+    X[2, 1] = np.nan
+    with pytest.raises(RuntimeError):
+        oracle.rank(X)
+
+
+def test_copula_invariance_under_monotone_maps():
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((300, 6))
+    S = oracle.copula_cov(X)
+    for f in (np.exp, lambda x: x ** 3, lambda x: 2.5 * x - 7.0):
+        assert np.array_equal(oracle.copula_cov(f(X)), S)
+
+
+def test_copula_cov_vs_numpy():
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((500, 7))
+    S, Z = oracle.copula_cov(X, return_z=True)
+    R = oracle.rank(X)
+    Zs = scipy.special.ndtri((R + 1) / (X.shape[0] + 1))
+    np.testing.assert_allclose(Z, Zs, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(S, np.cov(Z, rowvar=False), rtol=0, atol=1e-14)
+    # every column is a permutation of the same table: equal diagonals, zero mean
+    assert np.ptp(np.diag(S)) < 1e-14
+    assert abs(Z.mean()) < 1e-15
+
+
+def test_column_permutation_permutes_results():
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((200, 6))
+    perm = np.array([3, 0, 5, 1, 4, 2])
+    S = oracle.copula_cov(X)
+    Sp = oracle.copula_cov(X[:, perm])
+    np.testing.assert_array_equal(Sp, S[np.ix_(perm, perm)])
+    out, _ = oracle.measures(S, [6])
+    outp, _ = oracle.measures(Sp, [6])
+    np.testing.assert_allclose(out, outp, atol=1e-13)
+
+
+# ---------------------------------------------------------------- bias corrector
+def test_digamma_library():
+    for x in [0.3, 1.0, 2.5, 7.0, 24.5, 999.5]:
+        assert abs(oracle.digamma(x) - scipy.special.digamma(x)) < 1e-13 * max(1, abs(x))
+
+
+def test_bias_eta_monte_carlo():
+    # E[1/2 logdet(sample cov)] - 1/2 logdet(Sigma) = eta_m (Wishart moment);
+    # the reading with 1/2 on the digamma sum, not the printed one
+    rng = np.random.default_rng(12)
+    m, T, reps = 3, 50, 6000
+    A = rand_spd(rng, m)
+    L = np.linalg.cholesky(A)
+    vals = np.empty(reps)
+    for r in range(reps):
+        Xs = rng.standard_normal((T, m)) @ L.T
+        vals[r] = 0.5 * np.linalg.slogdet(np.cov(Xs, rowvar=False))[1]
+    mc = vals.mean() - 0.5 * np.linalg.slogdet(A)[1]
+    se = vals.std() / math.sqrt(reps)
+    eta = oracle.bias_eta(m, T)
+    assert abs(mc - eta) < 5 * se
+    printed = 0.5 * m * math.log(2 / (T - 1)) + sum(scipy.special.digamma((T - j) / 2)
+                                                     for j in range(1, m + 1))
+    assert abs(mc - printed) > 50 * se
+
+
+def test_bias_applied_per_entropy():
+    rng = np.random.default_rng(13)
+    S = rand_spd(rng, 5)
+    T = 300
+    raw, _ = oracle.measures(S, [4])
+    cor, _ = oracle.measures(S, [4], T_bias=T)
+    e = [oracle.bias_eta(m, T) for m in range(6)]
+    k = 4
+    np.testing.assert_allclose(cor[0], raw[0] - e[k], atol=1e-12)
+    np.testing.assert_allclose(cor[1], raw[1] - k * e[1] + e[k], atol=1e-12)
+    np.testing.assert_allclose(cor[2], raw[2] + (k - 1) * e[k] - k * e[k - 1], atol=1e-12)
+
+
+# ---------------------------------------------------------------- gradient
+@pytest.mark.parametrize("measure", ["H", "TC", "DTC", "O", "S"])
+def test_grad_fd(measure):
+    rng = np.random.default_rng(14)
+    N = 7
+    A = rand_spd(rng, N, ridge=1.0)
+    d = np.sqrt(np.diag(A))
+    S = A / np.outer(d, d)
+    orders = [3, 4, 5]
+    G = oracle.grad(S, orders, measure)
+    assert np.allclose(G, G.T, atol=1e-10)
+    for i in range(N):
+        for j in range(i, N):
+            fd = oracle.fd_grad_entry(S, orders, measure, i, j, h=1e-6)
+            an = G[i, j] if i == j else 2 * G[i, j]
+            assert abs(fd - an) < 2e-6 * max(1.0, abs(an)), (i, j, fd, an)
+
+
+# ---------------------------------------------------------------- reductions
+def test_reduce_per_order_bruteforce():
+    rng = np.random.default_rng(15)
+    N, orders = 9, [3, 4, 5]
+    S = rand_spd(rng, N)
+    vals, flags = oracle.measures(S, orders)
+    # plant exact ties to exercise the smallest-id rule
+    vals[3, 10] = vals[3, 20] = vals[3, 5]
+    ids = np.arange(vals.shape[1], dtype=np.uint64)
+    recs = oracle.reduce_per_order(N, orders, vals, ids, flags, top_m=7)
+    off = 0
+    for s, k in enumerate(orders):
+        n = math.comb(N, k)
+        rec = recs[s]
+        assert rec["count"] == n
+        for m in range(5):
+            best_min = best_max = None
+            for q in range(off, off + n):  # pure-python scan, first occurrence wins
+                v = vals[m, q]
+                if best_min is None or v < vals[m, best_min]:
+                    best_min = q
+                if best_max is None or v > vals[m, best_max]:
+                    best_max = q
+            assert rec["argmin"][m] == best_min and rec["argmax"][m] == best_max
+            assert abs(rec["mean"][m] - sum(vals[m, off:off + n]) / n) < 1e-12
+        pairs = sorted(((vals[3, q], q) for q in range(off, off + n)), key=lambda p: (-p[0], p[1]))
+        assert [int(q) for _, q in pairs[:7]] == [int(x) for x in rec["top_hi_id"]]
+        pairs = sorted(((vals[3, q], q) for q in range(off, off + n)), key=lambda p: (p[0], p[1]))
+        assert [int(q) for _, q in pairs[:7]] == [int(x) for x in rec["top_lo_id"]]
+        assert rec["neg_O"] == int((vals[3, off:off + n] < 0).sum())
+        off += n
+
+
+# ---------------------------------------------------------------- planted structure
+def test_planted_signs():
+    import workloads
+    X, _ = workloads.planted30()
+    S = oracle.copula_cov(X)
+    red = np.array([[0, 1, 2, 3, 4]])
+    syn = np.array([[10, 11, 12, 13, 19]])
+    for c, sign in ((red, 1), (syn, -1)):
+        k = c.shape[1]
+        # global id of a subset of one order: its lexicographic rank
+        rk, prev = 0, -1
+        for i, ci in enumerate(c[0]):
+            for x in range(prev + 1, ci):
+                rk += math.comb(30 - 1 - x, k - 1 - i)
+            prev = ci
+        out, _ = oracle.measures_ids(S, [k], [rk])
+        assert np.sign(out[3, 0]) == sign
