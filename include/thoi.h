@@ -1,0 +1,258 @@
+/*
+ * thoi.h -- C ABI of the GB300 library for exhaustive Gaussian-copula
+ * higher-order information (arXiv 2501.03381, "THOI").
+ *
+ * Given a T x N sample matrix, the library estimates the Gaussian-copula
+ * covariance (Supp. eq. gaussian_copula_covariance_estimator) on the GPU and
+ * evaluates, for every subset ("nplet") of k of the N variables, the joint
+ * entropy H (Supp. eq. gaussian_differential_entropy), the total correlation
+ * TC (eq. TC), the dual total correlation DTC (eq. DTC), the O-information
+ * O = TC - DTC (eq. O-info) and the S-information S = TC + DTC (eq. S-info).
+ * All entropies are in nats.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers are plain host or device pointers; the header needs no CUDA
+ *    headers.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Device pointers must belong to the current device.
+ *  - Ownership: the caller owns X, every output buffer and the stream.  The
+ *    context owns its covariance copies, tables and workspace and frees them
+ *    in thoi_destroy().
+ *  - Ordering: work is queued on `stream`; calls return once it is queued
+ *    unless stated otherwise.  Argument errors are returned immediately.
+ *    Errors found on the device (a non-positive-definite nplet, a workspace
+ *    overflow) are returned by the call that synchronises (thoi_create and
+ *    the record/grad entry points read a status word back before returning).
+ *  - Threads: a context may be used by one host thread at a time.  The only
+ *    global state is the autotuner cache, guarded by a mutex.
+ *  - Enumeration (Supp. eq. comb): the requested orders are visited in the
+ *    caller's order; within an order, k-subsets c_0 < ... < c_{k-1} come in
+ *    lexicographic order.  The global id of a nplet is its position in that
+ *    sequence (order offset + lexicographic rank).
+ */
+#ifndef THOI_API_H_
+#define THOI_API_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define THOI_MAX_N 64      /* largest number of variables */
+#define THOI_MAX_TOP_M 1024 /* largest top-M list per order and side */
+
+typedef struct thoi_ctx thoi_ctx;
+
+typedef enum {
+  THOI_OK = 0,
+  THOI_ERR_INVALID_ARG = 1,     /* bad size, order, pointer or option */
+  THOI_ERR_NONFINITE_INPUT = 2, /* X holds NaN or Inf */
+  THOI_ERR_TOO_LARGE = 3,       /* N > THOI_MAX_N, or a size beyond a documented limit */
+  THOI_ERR_NOT_PD = 4,          /* some nplet is not positive definite even in FP64;
+                                   its measures are NaN and it is left out of reductions */
+  THOI_ERR_OOM = 5,             /* a device allocation failed */
+  THOI_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+  THOI_ERR_TIMEOUT = 7,         /* a bounded device wait gave up */
+  THOI_ERR_CANCELLED = 8,       /* the cancel flag was raised */
+  THOI_ERR_WORKSPACE = 9        /* more flagged nplets than the re-factor list holds */
+} thoi_status;
+
+typedef enum {
+  THOI_F32_FIX64 = 0, /* FP32 Cholesky; flagged nplets re-factored in FP64 */
+  THOI_F64 = 1        /* every nplet in FP64 */
+} thoi_precision;
+
+typedef enum {
+  THOI_RED_NONE = 0,     /* per-nplet SoA output */
+  THOI_RED_PER_ORDER = 1 /* per-order reduction records */
+} thoi_reduction_kind;
+
+typedef enum { THOI_DTYPE_F32 = 0, THOI_DTYPE_F64 = 1 } thoi_dtype;
+
+typedef enum { THOI_H = 0, THOI_TC = 1, THOI_DTC = 2, THOI_O = 3, THOI_S = 4 } thoi_measure;
+
+typedef enum {
+  THOI_SIGMA32_TENSORCORE = 0, /* split-BF16 tensor-core GEMM, FP32 accumulation */
+  THOI_SIGMA32_FROM_F64 = 1    /* FP32 rounding of the FP64 covariance */
+} thoi_sigma32_source;
+
+/* Options; fill with thoi_default_options() and change what you need. */
+typedef struct {
+  int32_t precision;     /* thoi_precision; default THOI_F32_FIX64 */
+  float pivot_tau;       /* re-factor a nplet in FP64 when its smallest Cholesky pivot
+                            of the correlation submatrix is below this; default 1e-2 */
+  float trace_tau;       /* ... or when trace((R_S)^-1) exceeds this; default 100 */
+  int32_t bias_correct;  /* subtract the Gaussian entropy bias (Supp. eq. bias_corrector,
+                            with 1/2 on the digamma sum) from every entropy; default 0 */
+  int32_t top_m;         /* length of the top-M lists by O per order and side, 0..1024;
+                            default 256 */
+  int32_t out_f64;       /* per-nplet output in FP64 (1) or FP32 (0); default: 1 for
+                            THOI_F64, 0 otherwise */
+  int32_t sigma32_source;/* thoi_sigma32_source; default THOI_SIGMA32_TENSORCORE */
+  int32_t autotune;      /* use the autotuner's launch shapes (1) or the built-in ones (0);
+                            default 1 */
+  uint64_t flag_capacity;/* entries of the FP64 re-factor list; 0 = automatic */
+} thoi_options;
+
+/* Per-order reduction record (Fig. 1A caption: a function applied to every
+ * batch, e.g. the minimum O, read as this fixed set).  Measures are indexed
+ * by thoi_measure.  Ties in min/max go to the smallest global id.  Nplets
+ * that are not positive definite are counted in n_not_pd and left out. */
+typedef struct {
+  int32_t k;
+  int32_t top_count;     /* valid entries in each top list (min(top_m, count)) */
+  uint64_t count;        /* nplets of order k inside [id_begin, id_end) */
+  uint64_t count_neg_O;  /* nplets with O < 0 */
+  uint64_t n_refactored; /* nplets re-computed in FP64 (FP32 path) */
+  uint64_t n_not_pd;     /* nplets not positive definite in FP64 either */
+  double min[5];
+  double max[5];
+  double mean[5];
+  uint64_t argmin[5];    /* global ids */
+  uint64_t argmax[5];
+} thoi_order_record;
+
+/* One top-M entry: value of O and global id. */
+typedef struct {
+  double value;
+  uint64_t id;
+} thoi_top_entry;
+
+/* Statistics of the last thoi_measures call (filled after it synchronises). */
+typedef struct {
+  uint64_t nplets;       /* nplets evaluated */
+  uint64_t n_refactored; /* nplets re-computed in FP64 */
+  uint64_t n_not_pd;     /* nplets not positive definite */
+  int32_t launches;      /* kernel launches queued by the call */
+  int32_t pad;
+} thoi_stats;
+
+/* Fill `opt` with the defaults listed above. */
+void thoi_default_options(thoi_options* opt);
+
+/* Create a context from a T x N sample matrix (rows = samples).
+ *  X      : host or device pointer (detected), element (t, i) at X[t*ld + i]
+ *  T, N   : samples and variables, 2 <= N <= THOI_MAX_N, T >= N + 1, T <= 2^24
+ *  ld     : leading dimension in elements, ld >= N
+ *  dtype  : thoi_dtype of X
+ *  opt    : options (NULL = defaults)
+ * Runs the copula transform (per-column ordinal rank with ties broken by
+ * sample index, u = (r+1)/(T+1), z = Phi^{-1}(u)) and the covariance (centred,
+ * divided by T-1) on the device (Supp. eq.
+ * gaussian_copula_covariance_estimator), then synchronises `stream`.
+ * Returns THOI_ERR_NONFINITE_INPUT when X holds NaN or Inf.  X may be freed
+ * once the call returns. */
+thoi_status thoi_create(thoi_ctx** out, const void* X, int64_t T, int64_t N, int64_t ld,
+                        int32_t dtype, const thoi_options* opt, void* stream);
+
+/* Create a context from an explicit N x N covariance (host or device,
+ * row-major FP64).  T_for_bias is the sample count used by the bias
+ * corrector (ignored unless opt->bias_correct).  Synchronises `stream`. */
+thoi_status thoi_create_from_cov(thoi_ctx** out, const double* Sigma, int64_t N,
+                                 int64_t T_for_bias, const thoi_options* opt, void* stream);
+
+/* Copy the context's covariance out: Sigma64 (N x N FP64) and/or Sigma32
+ * (N x N FP32, the matrix the FP32 path starts from); either may be NULL.
+ * Host or device destinations; synchronises `stream`. */
+thoi_status thoi_get_cov(thoi_ctx* ctx, double* Sigma64, float* Sigma32, void* stream);
+
+/* Copy the per-column ordinal ranks (T x N int32, row-major) of the sample
+ * matrix the context was created from (host or device destination).
+ * THOI_ERR_INVALID_ARG for a context made by thoi_create_from_cov. */
+thoi_status thoi_get_ranks(thoi_ctx* ctx, int32_t* ranks, void* stream);
+
+/* Number of variables of the context. */
+int64_t thoi_n(const thoi_ctx* ctx);
+
+/* Exact number of nplets over the listed orders (host). */
+uint64_t thoi_count(int64_t N, const int32_t* orders, int32_t n_orders);
+
+/* Subset of a global id (host): writes k indices c_0 < ... < c_{k-1} to
+ * idx_out (room for THOI_MAX_N) and k to *k_out. */
+thoi_status thoi_unrank(int64_t N, const int32_t* orders, int32_t n_orders, uint64_t id,
+                        int32_t* idx_out, int32_t* k_out);
+
+/* Subsets of n global ids computed on the device with the kernels' own
+ * unranking (combinatorial number system) -- exposed so the enumeration can
+ * be checked.  ids: device u64[n]; idx_out: device int8[n * kmax], each row
+ * holding the indices then -1 padding; kmax >= the largest listed order. */
+thoi_status thoi_unrank_device(int64_t N, const int32_t* orders, int32_t n_orders,
+                               const uint64_t* ids, int64_t n, int32_t kmax, int8_t* idx_out,
+                               void* stream);
+
+/* Bytes of the per-order record output for n_orders orders: the records,
+ * then for each order its top-M largest O (descending) and top-M smallest O
+ * (ascending), top_m thoi_top_entry each:
+ *   [thoi_order_record x n_orders][thoi_top_entry x n_orders x 2 x top_m] */
+size_t thoi_records_bytes(int32_t n_orders, int32_t top_m);
+
+/* Evaluate the five measures of every nplet with global id in
+ * [id_begin, id_end) (id_end = UINT64_MAX means all).
+ *  orders  : host int32[n_orders], each 1 <= k <= N
+ *  kind    : THOI_RED_NONE -- `out` is a device array of 5 x n values (SoA,
+ *            out[m * n + (id - id_begin)]), FP32 or FP64 per opt.out_f64;
+ *            THOI_RED_PER_ORDER -- `out` is a host or device buffer of
+ *            thoi_records_bytes(n_orders, top_m) bytes laid out as above.
+ *  out_bytes : size of `out`, checked
+ *  stats   : optional, filled after the call synchronises
+ * The FP32 path factors each correlation submatrix R_S = L L^T in FP32 and
+ * gets every leave-one-out log-determinant from log det R_S +
+ * log (R_S^{-1})_jj; nplets whose smallest pivot is below pivot_tau, whose
+ * trace(R_S^{-1}) exceeds trace_tau, or whose result is not finite are
+ * re-factored in FP64.  The call synchronises `stream` before returning
+ * (it reads the re-factor count back).  Returns THOI_ERR_NOT_PD when some
+ * nplet is not positive definite in FP64. */
+thoi_status thoi_measures(thoi_ctx* ctx, const int32_t* orders, int32_t n_orders,
+                          uint64_t id_begin, uint64_t id_end, int32_t kind, void* out,
+                          size_t out_bytes, thoi_stats* stats, void* stream);
+
+/* Gradient of L = sum over every nplet of the listed orders of one measure
+ * (thoi_measure) with respect to the covariance Sigma, its N^2 entries taken
+ * as independent (the convention of d log det Sigma / d Sigma = Sigma^{-1}).
+ * Per nplet with P = Sigma_S^{-1}, p_j = P_jj (from eq.
+ * gaussian_differential_entropy):
+ *   dO/dSigma_S = 1/2 [diag(1/Sigma_ii) - 2P + P diag(1/p) P]
+ *   dS/dSigma_S = 1/2 [diag(1/Sigma_ii) - P diag(1/p) P]
+ * (H, TC, DTC likewise), scattered into the N x N result.  dL_dSigma is a
+ * device float[N*N] (row-major) owned by the caller.  The forward pass uses
+ * the FP32 path with the FP64 re-factor; accumulation is in FP64.
+ * Synchronises `stream`. */
+thoi_status thoi_measures_grad(thoi_ctx* ctx, const int32_t* orders, int32_t n_orders,
+                               int32_t measure, float* dL_dSigma, thoi_stats* stats,
+                               void* stream);
+
+/* Per-order reduction records for D contexts in one persistent launch per
+ * order (the paper processes several datasets together, Methods "Parallel
+ * and batched computation of HOI"; here they may differ in N and T).
+ * Context d evaluates the orders kmin..min(kmax, N_d).  out is a host or
+ * device buffer: for each context in turn, (kmax - kmin + 1) records then
+ * their top lists, i.e. thoi_records_bytes(kmax - kmin + 1, top_m) bytes per
+ * context (orders above N_d get count 0).  All contexts must use the same
+ * precision and top_m.  The launches are captured once in a CUDA graph and
+ * replayed.  Synchronises `stream`. */
+thoi_status thoi_batch_measures(thoi_ctx* const* ctxs, int32_t D, int32_t kmin, int32_t kmax,
+                                void* out, size_t out_bytes, thoi_stats* stats, void* stream);
+
+/* Autotune the FP32 kernels' launch shapes for orders kmin..kmax on the
+ * current GPU (timed on the device) and store the choice in the process-wide
+ * cache; if cache_path is not NULL the cache is also written there as JSON
+ * keyed by GPU name and SM count (and read from there first). */
+thoi_status thoi_autotune(thoi_ctx* ctx, int32_t kmin, int32_t kmax, const char* cache_path,
+                          void* stream);
+
+/* Raise (1) or clear (0) the context's cancel flag; running and later
+ * thoi_measures calls stop early and return THOI_ERR_CANCELLED. */
+thoi_status thoi_set_cancel(thoi_ctx* ctx, int32_t flag);
+
+/* Human-readable name of a status. */
+const char* thoi_status_string(thoi_status s);
+
+/* Free the context and everything it owns. */
+void thoi_destroy(thoi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THOI_API_H_ */

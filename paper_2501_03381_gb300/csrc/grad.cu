@@ -1,0 +1,199 @@
+// Adjoint of L = sum over nplets of one measure with respect to the
+// covariance.  The paper evaluates the measures only; gradients of O are
+// named as future work (Discussion).  Per nplet, with P = R_S^-1 and
+// p_j = P_jj on the correlation submatrix R_S (derivatives of eq.
+// gaussian_differential_entropy, d log det R = R^-1, d (R^-1)_jj =
+// -(P dR P)_jj), the contribution in correlation coordinates is
+//   H: 1/2 P      TC: 1/2 (I - P)      DTC: 1/2 (P - Q)
+//   O: 1/2 (I - 2P + Q)                S: 1/2 (I - Q),   Q = P diag(1/p) P,
+// and the gradient with respect to Sigma is G_ab / sqrt(Sigma_aa Sigma_bb).
+#include <type_traits>
+
+#include "nplet_common.cuh"
+
+namespace thoi {
+
+#define IXG(i, j) ((i) * ((i) + 1) / 2 + (j))
+constexpr int GRAD_FLUSH = 8;  // rounds between flushes of the shared accumulator
+
+template <typename V>
+__device__ __forceinline__ V grad_entry(int measure, int a, int b, const V* P, const V* Q, int k) {
+  const V pab = P[a * k + b], qab = Q[a * k + b];
+  const V id = a == b ? (V)1 : (V)0;
+  switch (measure) {
+    case THOI_H: return (V)0.5 * pab;
+    case THOI_TC: return (V)0.5 * (id - pab);
+    case THOI_DTC: return (V)0.5 * (pab - qab);
+    case THOI_O: return (V)0.5 * (id - (V)2 * pab + qab);
+    default: return (V)0.5 * (id - qab);
+  }
+}
+
+// FP32 pass over a dense rank range (flagged nplets appended to the re-factor
+// list) or FP64 pass over that list.
+template <typename V, int KMAX, bool LIST, typename M>
+__global__ void __launch_bounds__(RED_NT) k_grad(const NpletArgs a, const int measure,
+                                                 double* __restrict__ Gpart) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_stop;
+  constexpr bool FP32_PATH = !LIST;
+  const int N = a.N, k = a.k, ldr = row_stride(N);
+  const SmemLayout L = smem_layout(N, k, ldr, sizeof(V), sizeof(unsigned), 0);
+  float* Gs = reinterpret_cast<float*>(smem + L.total);  // N*N FP32 accumulator (FP32 pass)
+  if (threadIdx.x == 0) s_stop = 0;
+  if (FP32_PATH)
+    for (int q = threadIdx.x; q < N * N; q += RED_NT) Gs[q] = 0.f;
+  load_tables<V>(a, smem, L, FP32_PATH ? (const V*)a.R32 : (const V*)a.R64);
+  const unsigned long long* sb = reinterpret_cast<const unsigned long long*>(smem + L.binom);
+  const V* sR = reinterpret_cast<const V*>(smem + L.R);
+  double* Gb = Gpart + (size_t)blockIdx.x * N * N;
+  V A[KMAX * (KMAX + 1) / 2];
+  V P[KMAX * KMAX];
+  V Q[KMAX * KMAX];
+  int c[KMAX];
+  unsigned long long n;
+  if (LIST) {
+    const unsigned long long cnt = *a.flag_count;
+    n = cnt < a.flag_cap ? cnt : a.flag_cap;
+  } else {
+    n = a.rank_end - a.rank_begin;
+  }
+  const unsigned long long stride = (unsigned long long)gridDim.x * RED_NT;
+  const unsigned long long rounds = (n + stride - 1) / stride;
+  for (unsigned long long rd = 0; rd < rounds; rd++) {
+    const unsigned long long e = rd * stride + (unsigned long long)blockIdx.x * RED_NT + threadIdx.x;
+    if (e < n) {
+      unsigned long long r, gid;
+      if (LIST) { gid = a.flag_ids[e]; r = gid - a.id_base; }
+      else { r = a.rank_begin + e; gid = a.id_base + r; }
+      M m = unrank_s<M>(r, k, N, sb, k + 1);
+      for (int i = 0; i < k; i++) {
+        const int hb = hibit(m);
+        m ^= (M)1 << hb;
+        c[i] = N - 1 - hb;
+      }
+      for (int i = 0; i < k; i++)
+        for (int j = 0; j <= i; j++) A[IXG(i, j)] = sR[c[i] * ldr + c[j]];
+      // Cholesky, smallest pivot, W = L^-1 (in place), P = W^T W
+      bool bad = false;
+      V pmin = pinf<V>();
+      for (int p = 0; p < k; p++) {
+        const V d = A[IXG(p, p)];
+        pmin = d < pmin ? d : pmin;
+        bad |= !(d > (V)0);
+        const V inv = (V)1 / sqrt(d);
+        A[IXG(p, p)] = inv;
+        for (int i = p + 1; i < k; i++) A[IXG(i, p)] *= inv;
+        for (int i = p + 1; i < k; i++) {
+          const V lip = A[IXG(i, p)];
+          for (int j = p + 1; j <= i; j++) A[IXG(i, j)] = fma(-lip, A[IXG(j, p)], A[IXG(i, j)]);
+        }
+      }
+      for (int j = 0; j < k; j++) {
+        const V wjj = A[IXG(j, j)];
+        for (int i = j + 1; i < k; i++) {
+          V s = A[IXG(i, j)] * wjj;
+          for (int q = j + 1; q < i; q++) s = fma(A[IXG(i, q)], A[IXG(q, j)], s);
+          A[IXG(i, j)] = -A[IXG(i, i)] * s;
+        }
+      }
+      V trace = 0;
+      for (int x = 0; x < k; x++)
+        for (int y = 0; y <= x; y++) {
+          V s = 0;
+          for (int i = x; i < k; i++) s = fma(A[IXG(i, x)], A[IXG(i, y)], s);
+          P[x * k + y] = s;
+          P[y * k + x] = s;
+          if (x == y) trace += s;
+        }
+      if (FP32_PATH) {
+        bad |= !(pmin >= (V)a.tau_piv) | !(trace <= (V)a.tau_tr) | !isfinite((double)trace);
+        flag_append(a, bad, gid);
+      } else if (bad) {
+        atomicOr(a.status, ST_NOT_PD);
+      }
+      if (!bad) {
+        for (int x = 0; x < k; x++)
+          for (int y = 0; y <= x; y++) {
+            V s = 0;
+            for (int j = 0; j < k; j++) s += P[x * k + j] * P[j * k + y] / P[j * k + j];
+            Q[x * k + y] = s;
+            Q[y * k + x] = s;
+          }
+        for (int x = 0; x < k; x++)
+          for (int y = 0; y <= x; y++) {
+            const V g = grad_entry<V>(measure, x, y, P, Q, k);
+            if (FP32_PATH) {
+              atomicAdd(&Gs[c[x] * N + c[y]], (float)g);
+              if (x != y) atomicAdd(&Gs[c[y] * N + c[x]], (float)g);
+            } else {
+              atomicAdd(&Gb[c[x] * N + c[y]], (double)g);
+              if (x != y) atomicAdd(&Gb[c[y] * N + c[x]], (double)g);
+            }
+          }
+      }
+    }
+    if (threadIdx.x == 0 && a.cancel && *(volatile const int*)a.cancel) s_stop = 1;
+    if (FP32_PATH && ((rd + 1) % GRAD_FLUSH == 0 || rd + 1 == rounds)) {
+      __syncthreads();
+      for (int q = threadIdx.x; q < N * N; q += RED_NT) {
+        Gb[q] += (double)Gs[q];
+        Gs[q] = 0.f;
+      }
+    }
+    __syncthreads();
+    if (s_stop) {
+      if (threadIdx.x == 0) atomicOr(a.status, ST_CANCELLED);
+      if (FP32_PATH)
+        for (int q = threadIdx.x; q < N * N; q += RED_NT) Gb[q] += (double)Gs[q];
+      break;
+    }
+  }
+}
+
+// Sum the per-block partials in block order and scale to Sigma coordinates.
+__global__ void k_grad_finish(const double* __restrict__ Gpart, int nblk, const double* __restrict__ sig64,
+                              int N, float* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * N) return;
+  const int x = idx / N, y = idx % N;
+  double s = 0;
+  for (int b = 0; b < nblk; b++) s += Gpart[(size_t)b * N * N + idx];
+  out[idx] = (float)(s / sqrt(sig64[x * N + x] * sig64[y * N + y]));
+}
+
+template <typename V, int KMAX, bool LIST>
+static cudaError_t launch_grad_t(const NpletArgs& a, double* Gpart, int grid, int measure,
+                                 cudaStream_t s) {
+  const SmemLayout L = smem_layout(a.N, a.k, row_stride(a.N), sizeof(V), sizeof(unsigned), 0);
+  const size_t sm = L.total + (LIST ? 0 : (size_t)a.N * a.N * sizeof(float));
+  void (*fn)(const NpletArgs, const int, double*);
+  if (a.N > 32) fn = k_grad<V, KMAX, LIST, unsigned long long>;
+  else fn = k_grad<V, KMAX, LIST, unsigned>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, RED_NT, sm, s>>>(a, measure, Gpart);
+  return cudaGetLastError();
+}
+
+// grid: number of blocks (<= the Gpart regions allocated).
+cudaError_t launch_grad_pass(const NpletArgs& a, double* Gpart, int grid, int measure, bool list,
+                             cudaStream_t s) {
+  const int kb = a.k <= 8 ? 8 : (a.k <= 16 ? 16 : 32);
+  if (list) {
+    if (kb == 8) return launch_grad_t<double, 8, true>(a, Gpart, grid, measure, s);
+    if (kb == 16) return launch_grad_t<double, 16, true>(a, Gpart, grid, measure, s);
+    return launch_grad_t<double, 32, true>(a, Gpart, grid, measure, s);
+  }
+  if (kb == 8) return launch_grad_t<float, 8, false>(a, Gpart, grid, measure, s);
+  if (kb == 16) return launch_grad_t<float, 16, false>(a, Gpart, grid, measure, s);
+  return launch_grad_t<float, 32, false>(a, Gpart, grid, measure, s);
+}
+
+cudaError_t launch_grad_finish(const double* Gpart, int nblk, const double* sig64, int N, float* out,
+                               cudaStream_t s) {
+  k_grad_finish<<<(N * N + 255) / 256, 256, 0, s>>>(Gpart, nblk, sig64, N, out);
+  return cudaGetLastError();
+}
+
+}  // namespace thoi

@@ -1,0 +1,197 @@
+// Internal declarations shared by the library's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "thoi.h"
+
+namespace thoi {
+
+constexpr int NB = THOI_MAX_N + 1;  // side of the binomial table C(n, m), n, m <= 64
+constexpr int KREG_MAX = 20;        // largest order with a register-resident FP32 kernel
+constexpr int RED_NT = 128;         // threads per block of the nplet kernels
+constexpr int TOP_CAP = 2048;       // top-M candidate buffer per side (power of two)
+
+// Device status bits (OR-ed into the context's status word).
+enum : int {
+  ST_NOT_PD = 1,
+  ST_FLAG_OVERFLOW = 2,
+  ST_NONFINITE = 4,
+  ST_CANCELLED = 8,
+  ST_TIMEOUT = 16,
+  ST_BAD_ARG = 32
+};
+
+// One block's partial reduction over one launch (one order).  Values are
+// widened to double; ids are global ids.
+struct PartRec {
+  double vmin[5], vmax[5];
+  unsigned long long imin[5], imax[5];
+  double s_lr, s_sp, s_ls;  // sums of log det R_S, sum_j log p_j, sum_i log Sigma_ii
+  unsigned long long count, neg, notpd;
+  int top_hi, top_lo;       // valid entries in this block's top lists
+};
+
+struct TopEnt {
+  double v;
+  unsigned long long id;
+};
+static_assert(sizeof(TopEnt) == sizeof(thoi_top_entry), "layout");
+
+// Constants of the combine step for one order k (Methods eqs. TC, DTC,
+// O-info, S-info on the correlation matrix R = D^-1/2 Sigma D^-1/2):
+//   TC  = -1/2 Lr + tc_c
+//   DTC =  1/2 (Lr + Sp) + dtc_c
+//   O = TC - DTC,  S = TC + DTC
+//   H   = h_c + 1/2 (Lr + Ls)
+// with Lr = log det R_S, Sp = sum_j log (R_S^-1)_jj, Ls = sum_{i in S} log Sigma_ii.
+// The constants carry 1/2 k log(2 pi e) and the optional bias terms.
+struct Combine {
+  double h_c, tc_c, dtc_c;
+};
+
+// Everything a nplet kernel needs for one order.
+struct NpletArgs {
+  int N;
+  int k;
+  const float* R32;     // N x N correlation, FP32 (row-major, stride N)
+  const double* R64;    // N x N correlation, FP64
+  const double* ls;     // log Sigma_ii, N entries
+  const unsigned long long* binom;  // NB x NB table C(n, m)
+  unsigned long long rank_begin, rank_end;  // lexicographic ranks within order k
+  unsigned long long id_base;  // global id of rank 0 of this order
+  Combine cmb;
+  float tau_piv, tau_tr;
+  // outputs
+  int mode;             // 0: per-nplet SoA, 1: reduction partials
+  void* out;            // mode 0: SoA base
+  int out_f64;
+  unsigned long long out_n;      // stride between measures in `out`
+  unsigned long long out_first;  // global id stored at out index 0
+  PartRec* part;        // mode 1: [gridDim.x]
+  TopEnt* part_top;     // mode 1: [gridDim.x][2][top_m]
+  int top_m;
+  // FP64 re-factor list (FP32 kernels append; the re-factor kernel reads)
+  unsigned long long* flag_ids;
+  unsigned long long* flag_count;
+  unsigned long long flag_cap;
+  int* status;
+  const int* cancel;    // device flag polled per round (may be null)
+};
+
+// ------------------------------------------------------------------ launchers
+struct Shape {
+  int blocks_per_sm;  // 0 = occupancy maximum
+  int chunk;          // nplets per thread per round (multiple of 1)
+};
+
+// Workspace of the copula front end (device pointers owned by the context).
+struct CopulaWs {
+  int* rank;          // T x N
+  double* ztab;       // T
+  double* Z;          // N x T, variable-major
+  double* mu;         // N
+  double* sig64;      // N x N
+  void* zh;           // Np x Tp BF16 (hi, mid, lo terms of Z - mu)
+  void* zm;
+  void* zl;
+  float* part;        // n_chunks x Np x Np FP32 chunk tiles
+  double* sig32acc;   // N x N, FP64 sum of the FP32 chunk tiles
+};
+struct CopulaWsSizes {
+  int Np;
+  long long Tp;
+  int n_chunks;
+};
+void copula_ws_sizes(long long T, int N, CopulaWsSizes* z);
+cudaError_t launch_copula(const void* X, int dtype, long long T, int N, long long ld,
+                          const CopulaWs& w, int tc_cov, int* d_status, cudaStream_t s);
+cudaError_t launch_normalise(const double* sig64, const double* sig32acc, int N, double* R64,
+                             float* R32, double* ls, float* sig32_out, int* status,
+                             cudaStream_t s);
+cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
+                             int* grid_out, int max_blocks);
+cudaError_t launch_nplet_f64(const NpletArgs& a, int num_sms, cudaStream_t s, int* grid_out,
+                             int max_blocks);
+cudaError_t launch_refactor(const NpletArgs& a, int num_sms, cudaStream_t s, int* grid_out,
+                            int max_blocks);
+// One order slot of a merge: where its FP32 and FP64 partials live.
+struct MergeDesc {
+  int p32_off, g32;   // first partial and count (FP32 path or FP64 path)
+  int p64_off, g64;   // FP64 re-factor partials
+  int k;
+  int pad;
+  Combine cmb;
+  const unsigned long long* refactored;  // device counter of re-factored nplets (or null)
+};
+constexpr int MAX_SLOTS = 64;
+struct MergeDescs {
+  MergeDesc d[MAX_SLOTS];
+};
+cudaError_t launch_merge(const MergeDescs& D, int n_slots, const PartRec* p32, const TopEnt* t32,
+                         const PartRec* p64, const TopEnt* t64, int top_m, thoi_order_record* recs,
+                         TopEnt* tops, cudaStream_t s);
+cudaError_t launch_unrank_ids(int N, const int* d_orders, const unsigned long long* d_offsets,
+                              int n_orders, const unsigned long long* binom,
+                              const unsigned long long* ids, long long n, int kmax,
+                              int8_t* idx_out, cudaStream_t s);
+cudaError_t launch_grad_pass(const NpletArgs& a, double* Gpart, int grid, int measure, bool list,
+                             cudaStream_t s);
+cudaError_t launch_grad_finish(const double* Gpart, int nblk, const double* sig64, int N, float* out,
+                               cudaStream_t s);
+
+// ------------------------------------------------------------------ device helpers
+#ifdef __CUDACC__
+
+__device__ __forceinline__ unsigned long long binom_at(const unsigned long long* b, int n, int m) {
+  return b[n * NB + m];
+}
+
+// Lexicographic rank r of a k-subset of {0..N-1} -> reversed bitmask (bit
+// N-1-c set for every member c).  Combinatorial number system: with
+// r' = C(N,k) - 1 - r, the members satisfy r' = sum_i C(d_i, k-i) with
+// d_i = N-1-c_i strictly decreasing; each d_i is the largest d whose
+// binomial still fits into what is left of r'.
+template <typename M>
+__device__ __forceinline__ M unrank_mask(unsigned long long r, int k, int N,
+                                         const unsigned long long* b) {
+  unsigned long long rr = binom_at(b, N, k) - 1ull - r;
+  M mask = 0;
+  int d = N - 1;
+  for (int i = 0; i < k; i++) {
+    const int m = k - i;
+    unsigned long long cd = binom_at(b, d, m);
+    while (cd > rr) {
+      d--;
+      cd = binom_at(b, d, m);
+    }
+    rr -= cd;
+    mask |= (M)1 << d;
+    d--;
+  }
+  return mask;
+}
+
+__device__ __forceinline__ int ctz_m(unsigned int x) { return __ffs(x) - 1; }
+__device__ __forceinline__ int ctz_m(unsigned long long x) { return __ffsll((long long)x) - 1; }
+__device__ __forceinline__ int hibit(unsigned int x) { return 31 - __clz(x); }
+__device__ __forceinline__ int hibit(unsigned long long x) { return 63 - __clzll((long long)x); }
+
+// Lexicographic successor in the reversed-bitmask encoding: lexicographic
+// order of sorted tuples is decreasing numeric order of the reversed mask,
+// so the successor is the next smaller N-bit number with the same number of
+// ones, i.e. the complement of the next larger number with the complement's
+// popcount (Gosper's rule).
+template <typename M>
+__device__ __forceinline__ M lex_succ(M x, M full) {
+  M y = ~x & full;
+  M t = y & (~y + 1);
+  M r = y + t;
+  M nx = r | (((y ^ r) >> 2) >> ctz_m(t));
+  return ~nx & full;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace thoi

@@ -1,0 +1,817 @@
+// Host side of the C ABI declared in include/thoi.h: validation, context
+// and workspace ownership, the per-order launch plan, the FP64 re-factor and
+// the merge, and the status word.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace thoi;
+
+namespace thoi {
+cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
+                             int* grid_out, int max_blocks);
+Shape tuned_shape(int k, int num_sms, const char* gpu_name, int use_tuner);
+}  // namespace thoi
+
+#define CK(x)                                        \
+  do {                                               \
+    cudaError_t e_ = (x);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_);     \
+  } while (0)
+
+static thread_local char g_last_cuda[256];
+
+static thoi_status cuda_fail(cudaError_t e) {
+  snprintf(g_last_cuda, sizeof g_last_cuda, "%s", cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return THOI_ERR_OOM;
+  return THOI_ERR_CUDA;
+}
+
+// ------------------------------------------------------------------ context
+struct thoi_ctx {
+  int device = 0;
+  int num_sms = 0;
+  char gpu_name[256] = {0};
+  int N = 0;
+  long long T = 0;
+  long long T_bias = 0;
+  int has_ranks = 0;
+  thoi_options opt;
+  // tables (device)
+  double* sig64 = nullptr;   // N x N covariance (FP64)
+  float* sig32 = nullptr;    // N x N covariance the FP32 path starts from
+  double* R64 = nullptr;
+  float* R32 = nullptr;
+  double* ls = nullptr;
+  unsigned long long* binom = nullptr;  // NB x NB
+  int* ranks = nullptr;      // T x N
+  int* status = nullptr;
+  int* h_cancel = nullptr;   // mapped host flag
+  int* d_cancel = nullptr;
+  // workspace
+  unsigned long long* flag_ids = nullptr;
+  size_t flag_cap = 0;
+  unsigned long long* flag_counts = nullptr;  // [MAX_SLOTS]
+  PartRec* part32 = nullptr;
+  TopEnt* top32 = nullptr;
+  size_t part32_cap = 0;      // blocks
+  PartRec* part64 = nullptr;
+  TopEnt* top64 = nullptr;
+  size_t part64_cap = 0;
+  int part_top_m = 0;
+  unsigned char* rec_buf = nullptr;  // device staging for records
+  size_t rec_cap = 0;
+  double* gpart = nullptr;    // gradient partials
+  size_t gpart_cap = 0;       // doubles
+};
+
+static void free_ptr(void* p) {
+  if (p) cudaFree(p);
+}
+
+template <typename T>
+static thoi_status grow(T** p, size_t* cap, size_t need_elems) {
+  if (*cap >= need_elems && *p) return THOI_OK;
+  free_ptr(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (need_elems == 0) return THOI_OK;
+  CK(cudaMalloc((void**)p, need_elems * sizeof(T)));
+  *cap = need_elems;
+  return THOI_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------------ host math
+static uint64_t binom_host(int n, int k) {
+  static uint64_t tab[NB][NB];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int a = 0; a < NB; a++) {
+      tab[a][0] = 1;
+      for (int b = 1; b < NB; b++) tab[a][b] = a == 0 ? 0 : tab[a - 1][b - 1] + tab[a - 1][b];
+    }
+  });
+  if (n < 0 || k < 0 || n >= NB || k >= NB) return 0;
+  return tab[n][k];
+}
+
+// Digamma by upward recurrence to x >= 8 and the Stirling-type series.
+static double digamma_host(double x) {
+  double acc = 0.0;
+  for (; x < 8.0; x += 1.0) acc -= 1.0 / x;
+  const double x2 = 1.0 / (x * x);
+  const double series =
+      x2 * (1.0 / 12 - x2 * (1.0 / 120 - x2 * (1.0 / 252 - x2 * (1.0 / 240 - x2 * (1.0 / 132)))));
+  return acc + log(x) - 0.5 / x - series;
+}
+
+// Gaussian entropy bias of m variables from T samples (Supp. eq.
+// bias_corrector read with 1/2 on the digamma sum).
+static double eta_host(int m, long long T) {
+  if (m <= 0) return 0.0;
+  double s = m * log(2.0 / (double)(T - 1));
+  for (int j = 1; j <= m; j++) s += digamma_host(0.5 * (double)(T - j));
+  return 0.5 * s;
+}
+
+static Combine combine_for(const thoi_ctx* c, int k) {
+  const double LOG2PIE = 2.8378770664093454835606594728112;
+  Combine cb;
+  cb.h_c = 0.5 * k * LOG2PIE;
+  cb.tc_c = 0.0;
+  cb.dtc_c = 0.0;
+  if (c->opt.bias_correct && c->T_bias > k + 1) {
+    const double ek = eta_host(k, c->T_bias), e1 = eta_host(1, c->T_bias),
+                 ekm = eta_host(k - 1, c->T_bias);
+    cb.h_c -= ek;
+    cb.tc_c = -k * e1 + ek;
+    cb.dtc_c = (k - 1) * ek - k * ekm;
+  }
+  return cb;
+}
+
+// ------------------------------------------------------------------ API: misc
+extern "C" void thoi_default_options(thoi_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->precision = THOI_F32_FIX64;
+  o->pivot_tau = 1e-2f;
+  o->trace_tau = 100.0f;
+  o->bias_correct = 0;
+  o->top_m = 256;
+  o->out_f64 = -1;
+  o->sigma32_source = THOI_SIGMA32_TENSORCORE;
+  o->autotune = 1;
+  o->flag_capacity = 0;
+}
+
+extern "C" const char* thoi_status_string(thoi_status s) {
+  switch (s) {
+    case THOI_OK: return "ok";
+    case THOI_ERR_INVALID_ARG: return "invalid argument";
+    case THOI_ERR_NONFINITE_INPUT: return "input holds NaN or Inf";
+    case THOI_ERR_TOO_LARGE: return "size beyond a documented limit";
+    case THOI_ERR_NOT_PD: return "a nplet is not positive definite";
+    case THOI_ERR_OOM: return "device allocation failed";
+    case THOI_ERR_CUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
+    case THOI_ERR_TIMEOUT: return "bounded device wait gave up";
+    case THOI_ERR_CANCELLED: return "cancelled";
+    case THOI_ERR_WORKSPACE: return "re-factor list overflow";
+  }
+  return "unknown status";
+}
+
+extern "C" uint64_t thoi_count(int64_t N, const int32_t* orders, int32_t n_orders) {
+  if (N < 1 || N > THOI_MAX_N || !orders || n_orders < 1) return 0;
+  uint64_t s = 0;
+  for (int i = 0; i < n_orders; i++) s += binom_host((int)N, orders[i]);
+  return s;
+}
+
+extern "C" size_t thoi_records_bytes(int32_t n_orders, int32_t top_m) {
+  if (n_orders < 0 || top_m < 0) return 0;
+  return (size_t)n_orders * sizeof(thoi_order_record) +
+         (size_t)n_orders * 2 * (size_t)top_m * sizeof(thoi_top_entry);
+}
+
+static bool orders_ok(int N, const int32_t* orders, int32_t n_orders) {
+  if (!orders || n_orders < 1 || n_orders > MAX_SLOTS) return false;
+  for (int i = 0; i < n_orders; i++)
+    if (orders[i] < 1 || orders[i] > N) return false;
+  return true;
+}
+
+// Host unrank: the same combinatorial number system as the device code.
+extern "C" thoi_status thoi_unrank(int64_t N, const int32_t* orders, int32_t n_orders, uint64_t id,
+                                   int32_t* idx_out, int32_t* k_out) {
+  if (N < 1 || N > THOI_MAX_N || !orders_ok((int)N, orders, n_orders) || !idx_out)
+    return THOI_ERR_INVALID_ARG;
+  for (int s = 0; s < n_orders; s++) {
+    const uint64_t c = binom_host((int)N, orders[s]);
+    if (id < c) {
+      const int k = orders[s];
+      uint64_t rr = c - 1 - id;
+      int d = (int)N - 1;
+      for (int i = 0; i < k; i++) {
+        const int m = k - i;
+        while (binom_host(d, m) > rr) d--;
+        rr -= binom_host(d, m);
+        idx_out[i] = (int32_t)(N - 1 - d);
+        d--;
+      }
+      if (k_out) *k_out = k;
+      return THOI_OK;
+    }
+    id -= c;
+  }
+  return THOI_ERR_INVALID_ARG;
+}
+
+extern "C" thoi_status thoi_unrank_device(int64_t N, const int32_t* orders, int32_t n_orders,
+                                          const uint64_t* ids, int64_t n, int32_t kmax,
+                                          int8_t* idx_out, void* stream) {
+  if (N < 1 || N > THOI_MAX_N || !orders_ok((int)N, orders, n_orders) || n < 0 || !ids ||
+      !idx_out)
+    return THOI_ERR_INVALID_ARG;
+  for (int i = 0; i < n_orders; i++)
+    if (orders[i] > kmax) return THOI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<unsigned long long> hb(NB * NB), offs(n_orders + 1);
+  for (int a = 0; a < NB; a++)
+    for (int b = 0; b < NB; b++) hb[a * NB + b] = binom_host(a, b);
+  offs[0] = 0;
+  for (int i = 0; i < n_orders; i++) offs[i + 1] = offs[i] + binom_host((int)N, orders[i]);
+  unsigned long long *d_b = nullptr, *d_o = nullptr;
+  int* d_ord = nullptr;
+  thoi_status st = THOI_OK;
+  cudaError_t e = cudaMalloc(&d_b, hb.size() * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&d_o, offs.size() * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&d_ord, n_orders * 4);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_b, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_o, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ord, orders, n_orders * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_unrank_ids((int)N, d_ord, d_o, n_orders, d_b, (const unsigned long long*)ids, n, kmax,
+                          idx_out, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) st = cuda_fail(e);
+  free_ptr(d_b);
+  free_ptr(d_o);
+  free_ptr(d_ord);
+  return st;
+}
+
+extern "C" int64_t thoi_n(const thoi_ctx* c) { return c ? c->N : 0; }
+
+extern "C" thoi_status thoi_set_cancel(thoi_ctx* c, int32_t flag) {
+  if (!c || !c->h_cancel) return THOI_ERR_INVALID_ARG;
+  *(volatile int*)c->h_cancel = flag ? 1 : 0;
+  return THOI_OK;
+}
+
+extern "C" void thoi_destroy(thoi_ctx* c) {
+  if (!c) return;
+  free_ptr(c->sig64);
+  free_ptr(c->sig32);
+  free_ptr(c->R64);
+  free_ptr(c->R32);
+  free_ptr(c->ls);
+  free_ptr(c->binom);
+  free_ptr(c->ranks);
+  free_ptr(c->status);
+  if (c->h_cancel) cudaFreeHost(c->h_cancel);
+  free_ptr(c->flag_ids);
+  free_ptr(c->flag_counts);
+  free_ptr(c->part32);
+  free_ptr(c->top32);
+  free_ptr(c->part64);
+  free_ptr(c->top64);
+  free_ptr(c->rec_buf);
+  free_ptr(c->gpart);
+  delete c;
+}
+
+// ------------------------------------------------------------------ API: create
+static thoi_status ctx_common(thoi_ctx* c, int N, const thoi_options* opt) {
+  if (opt) c->opt = *opt;
+  else thoi_default_options(&c->opt);
+  if (c->opt.out_f64 < 0) c->opt.out_f64 = c->opt.precision == THOI_F64 ? 1 : 0;
+  if (c->opt.precision != THOI_F32_FIX64 && c->opt.precision != THOI_F64) return THOI_ERR_INVALID_ARG;
+  if (c->opt.top_m < 0 || c->opt.top_m > THOI_MAX_TOP_M) return THOI_ERR_INVALID_ARG;
+  if (!(c->opt.pivot_tau >= 0.0f) || !(c->opt.trace_tau > 0.0f)) return THOI_ERR_INVALID_ARG;
+  if (c->opt.sigma32_source != THOI_SIGMA32_TENSORCORE &&
+      c->opt.sigma32_source != THOI_SIGMA32_FROM_F64)
+    return THOI_ERR_INVALID_ARG;
+  c->N = N;
+  CK(cudaGetDevice(&c->device));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, c->device));
+  c->num_sms = prop.multiProcessorCount;
+  snprintf(c->gpu_name, sizeof c->gpu_name, "%s", prop.name);
+  CK(cudaMalloc(&c->sig64, (size_t)N * N * 8));
+  CK(cudaMalloc(&c->sig32, (size_t)N * N * 4));
+  CK(cudaMalloc(&c->R64, (size_t)N * N * 8));
+  CK(cudaMalloc(&c->R32, (size_t)N * N * 4));
+  CK(cudaMalloc(&c->ls, (size_t)N * 8));
+  CK(cudaMalloc(&c->binom, (size_t)NB * NB * 8));
+  CK(cudaMalloc(&c->status, sizeof(int)));
+  CK(cudaMalloc(&c->flag_counts, MAX_SLOTS * sizeof(unsigned long long)));
+  CK(cudaHostAlloc(&c->h_cancel, sizeof(int), cudaHostAllocMapped));
+  *c->h_cancel = 0;
+  CK(cudaHostGetDevicePointer((void**)&c->d_cancel, c->h_cancel, 0));
+  std::vector<unsigned long long> hb(NB * NB);
+  for (int a = 0; a < NB; a++)
+    for (int b = 0; b < NB; b++) hb[a * NB + b] = binom_host(a, b);
+  CK(cudaMemcpy(c->binom, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice));
+  return THOI_OK;
+}
+
+static thoi_status read_status(thoi_ctx* c, cudaStream_t s, int* out) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *out = h;
+  return THOI_OK;
+}
+
+extern "C" thoi_status thoi_create(thoi_ctx** out, const void* X, int64_t T, int64_t N, int64_t ld,
+                                   int32_t dtype, const thoi_options* opt, void* stream) {
+  if (!out || !X) return THOI_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (N > THOI_MAX_N) return THOI_ERR_TOO_LARGE;
+  if (N < 2 || T < N + 1 || ld < N || (dtype != THOI_DTYPE_F32 && dtype != THOI_DTYPE_F64))
+    return THOI_ERR_INVALID_ARG;
+  if (T > (1ll << 24)) return THOI_ERR_TOO_LARGE;
+  cudaStream_t s = (cudaStream_t)stream;
+  thoi_ctx* c = new thoi_ctx();
+  thoi_status st = ctx_common(c, (int)N, opt);
+  if (st != THOI_OK) { thoi_destroy(c); return st; }
+  c->T = T;
+  c->T_bias = T;
+  c->has_ranks = 1;
+  const size_t esz = dtype == THOI_DTYPE_F64 ? 8 : 4;
+  const bool dev = is_device_ptr(X);
+  void* dX = nullptr;
+  const void* Xuse = X;
+  CopulaWs w;
+  memset(&w, 0, sizeof w);
+  CopulaWsSizes z;
+  copula_ws_sizes(T, (int)N, &z);
+  const int tc = c->opt.sigma32_source == THOI_SIGMA32_TENSORCORE;
+  cudaError_t e = cudaSuccess;
+#define TRY(x) if (e == cudaSuccess) e = (x)
+  if (!dev) {
+    TRY(cudaMalloc(&dX, (size_t)T * ld * esz));
+    TRY(cudaMemcpyAsync(dX, X, (size_t)T * ld * esz, cudaMemcpyHostToDevice, s));
+    Xuse = dX;
+  }
+  TRY(cudaMalloc(&c->ranks, (size_t)T * N * 4));
+  w.rank = c->ranks;
+  TRY(cudaMalloc(&w.ztab, (size_t)T * 8));
+  TRY(cudaMalloc(&w.Z, (size_t)T * N * 8));
+  TRY(cudaMalloc(&w.mu, (size_t)N * 8));
+  w.sig64 = c->sig64;
+  if (tc) {
+    const size_t nz = (size_t)z.Np * z.Tp * 2;
+    TRY(cudaMalloc(&w.zh, nz));
+    TRY(cudaMalloc(&w.zm, nz));
+    TRY(cudaMalloc(&w.zl, nz));
+    TRY(cudaMalloc(&w.part, (size_t)z.n_chunks * z.Np * z.Np * 4));
+    TRY(cudaMalloc(&w.sig32acc, (size_t)N * N * 8));
+  }
+  TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  TRY(launch_copula(Xuse, dtype, T, (int)N, ld, w, tc, c->status, s));
+  TRY(launch_normalise(c->sig64, tc ? w.sig32acc : nullptr, (int)N, c->R64, c->R32, c->ls, c->sig32,
+                       c->status, s));
+  TRY(cudaStreamSynchronize(s));
+#undef TRY
+  free_ptr(dX);
+  free_ptr(w.ztab);
+  free_ptr(w.Z);
+  free_ptr(w.mu);
+  free_ptr(w.zh);
+  free_ptr(w.zm);
+  free_ptr(w.zl);
+  free_ptr(w.part);
+  free_ptr(w.sig32acc);
+  if (e != cudaSuccess) { thoi_destroy(c); return cuda_fail(e); }
+  int hs = 0;
+  st = read_status(c, s, &hs);
+  if (st != THOI_OK) { thoi_destroy(c); return st; }
+  if (hs & ST_NONFINITE) { thoi_destroy(c); return THOI_ERR_NONFINITE_INPUT; }
+  if (hs & ST_BAD_ARG) { thoi_destroy(c); return THOI_ERR_INVALID_ARG; }
+  *out = c;
+  return THOI_OK;
+}
+
+extern "C" thoi_status thoi_create_from_cov(thoi_ctx** out, const double* Sigma, int64_t N,
+                                            int64_t T_for_bias, const thoi_options* opt,
+                                            void* stream) {
+  if (!out || !Sigma) return THOI_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (N > THOI_MAX_N) return THOI_ERR_TOO_LARGE;
+  if (N < 1) return THOI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  thoi_ctx* c = new thoi_ctx();
+  thoi_status st = ctx_common(c, (int)N, opt);
+  if (st != THOI_OK) { thoi_destroy(c); return st; }
+  c->T = 0;
+  c->T_bias = T_for_bias;
+  if (c->opt.bias_correct && T_for_bias < N + 2) { thoi_destroy(c); return THOI_ERR_INVALID_ARG; }
+  cudaError_t e = cudaMemcpyAsync(c->sig64, Sigma, (size_t)N * N * 8, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = launch_normalise(c->sig64, nullptr, (int)N, c->R64, c->R32, c->ls, c->sig32, c->status, s);
+  if (e != cudaSuccess) { thoi_destroy(c); return cuda_fail(e); }
+  int hs = 0;
+  st = read_status(c, s, &hs);
+  if (st != THOI_OK) { thoi_destroy(c); return st; }
+  if (hs & ST_BAD_ARG) { thoi_destroy(c); return THOI_ERR_INVALID_ARG; }
+  *out = c;
+  return THOI_OK;
+}
+
+extern "C" thoi_status thoi_get_cov(thoi_ctx* c, double* S64, float* S32, void* stream) {
+  if (!c) return THOI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)c->N * c->N;
+  if (S64) CK(cudaMemcpyAsync(S64, c->sig64, n * 8, cudaMemcpyDefault, s));
+  if (S32) CK(cudaMemcpyAsync(S32, c->sig32, n * 4, cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
+  return THOI_OK;
+}
+
+extern "C" thoi_status thoi_get_ranks(thoi_ctx* c, int32_t* ranks, void* stream) {
+  if (!c || !ranks || !c->has_ranks) return THOI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(ranks, c->ranks, (size_t)c->T * c->N * 4, cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
+  return THOI_OK;
+}
+
+// ------------------------------------------------------------------ API: measures
+namespace {
+
+struct SlotRange {
+  int k;
+  unsigned long long off;     // global id of rank 0
+  unsigned long long r0, r1;  // rank range inside [id_begin, id_end)
+};
+
+constexpr int MAX_BLOCKS_PER_SM_RED = 4;   // cap for reduction launches (partials per block)
+constexpr int MAX_BLOCKS_PER_SM_OUT = 8;
+constexpr int REFACTOR_BLOCKS_PER_SM = 2;
+constexpr unsigned long long LAUNCH_SPLIT = 0xffffffffull;  // ranks per launch (u32 local ids)
+
+}  // namespace
+
+static thoi_status plan_slots(const thoi_ctx* c, const int32_t* orders, int32_t n_orders,
+                              uint64_t id_begin, uint64_t* id_end, std::vector<SlotRange>* slots) {
+  const uint64_t total = thoi_count(c->N, orders, n_orders);
+  if (*id_end == UINT64_MAX) *id_end = total;
+  if (id_begin > *id_end || *id_end > total) return THOI_ERR_INVALID_ARG;
+  unsigned long long off = 0;
+  slots->clear();
+  for (int s = 0; s < n_orders; s++) {
+    const unsigned long long cnt = binom_host(c->N, orders[s]);
+    SlotRange r;
+    r.k = orders[s];
+    r.off = off;
+    const unsigned long long a = id_begin > off ? id_begin - off : 0;
+    const unsigned long long b = *id_end > off ? (*id_end - off < cnt ? *id_end - off : cnt) : 0;
+    r.r0 = a < cnt ? a : cnt;
+    r.r1 = b > r.r0 ? b : r.r0;
+    slots->push_back(r);
+    off += cnt;
+  }
+  return THOI_OK;
+}
+
+static thoi_status ensure_flag_ws(thoi_ctx* c, unsigned long long max_slot_nplets) {
+  size_t need = c->opt.flag_capacity;
+  if (need == 0) {
+    // automatic: 1/16 of the largest order, at least 1M, at most 64M entries
+    unsigned long long a = max_slot_nplets / 16 + 1;
+    if (a < (1ull << 20)) a = 1ull << 20;
+    if (a > (64ull << 20)) a = 64ull << 20;
+    if (a > max_slot_nplets) a = max_slot_nplets > 0 ? max_slot_nplets : 1;
+    need = (size_t)a;
+  }
+  return grow(&c->flag_ids, &c->flag_cap, need);
+}
+
+static NpletArgs base_args(thoi_ctx* c, const SlotRange& r) {
+  NpletArgs a;
+  memset(&a, 0, sizeof a);
+  a.N = c->N;
+  a.k = r.k;
+  a.R32 = c->R32;
+  a.R64 = c->R64;
+  a.ls = c->ls;
+  a.binom = c->binom;
+  a.rank_begin = r.r0;
+  a.rank_end = r.r1;
+  a.id_base = r.off;
+  a.cmb = combine_for(c, r.k);
+  a.tau_piv = c->opt.pivot_tau;
+  a.tau_tr = c->opt.trace_tau;
+  a.status = c->status;
+  a.cancel = c->d_cancel;
+  a.flag_ids = c->flag_ids;
+  a.flag_cap = c->flag_cap;
+  return a;
+}
+
+static thoi_status finish_status(thoi_ctx* c, cudaStream_t s, int n_slots, thoi_stats* stats,
+                                 uint64_t nplets, int launches) {
+  int hs = 0;
+  unsigned long long fc[MAX_SLOTS];
+  CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (n_slots > 0)
+    CK(cudaMemcpyAsync(fc, c->flag_counts, n_slots * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  unsigned long long nref = 0;
+  for (int i = 0; i < n_slots; i++) nref += fc[i] < c->flag_cap ? fc[i] : c->flag_cap;
+  if (stats) {
+    stats->nplets = nplets;
+    stats->n_refactored = nref;
+    stats->n_not_pd = 0;
+    stats->launches = launches;
+  }
+  if (hs & ST_FLAG_OVERFLOW) return THOI_ERR_WORKSPACE;
+  if (hs & ST_CANCELLED) return THOI_ERR_CANCELLED;
+  if (hs & ST_NOT_PD) return THOI_ERR_NOT_PD;
+  return THOI_OK;
+}
+
+// Queue the whole measure pass (no synchronisation).  Used directly by the
+// batched entry point, which captures it into a CUDA graph.
+static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t n_orders,
+                                    uint64_t id_begin, uint64_t id_end, int32_t kind, void* out_dev,
+                                    thoi_order_record* recs_dev, TopEnt* tops_dev,
+                                    cudaStream_t s, int* launches_out) {
+  std::vector<SlotRange> slots;
+  thoi_status st = plan_slots(c, orders, n_orders, id_begin, &id_end, &slots);
+  if (st != THOI_OK) return st;
+  const bool red = kind == THOI_RED_PER_ORDER;
+  const bool f64 = c->opt.precision == THOI_F64;
+  const int top_m = red ? c->opt.top_m : 0;
+  int launches = 0;
+  unsigned long long maxn = 0;
+  for (auto& r : slots) maxn = (r.r1 - r.r0) > maxn ? (r.r1 - r.r0) : maxn;
+  if (!f64) {
+    st = ensure_flag_ws(c, maxn);
+    if (st != THOI_OK) return st;
+  }
+  // partial buffers for the reductions: one region per launch
+  const int blk_cap = c->num_sms * MAX_BLOCKS_PER_SM_RED;
+  const int ref_cap = c->num_sms * REFACTOR_BLOCKS_PER_SM;
+  if (red) {
+    size_t n32 = 0;
+    for (auto& r : slots) {
+      const unsigned long long n = r.r1 - r.r0;
+      const size_t parts = n == 0 ? 0 : (size_t)((n + LAUNCH_SPLIT - 1) / LAUNCH_SPLIT);
+      n32 += parts * blk_cap;
+    }
+    const size_t n64 = f64 ? 0 : slots.size() * (size_t)ref_cap;
+    if (c->part_top_m != top_m) {
+      free_ptr(c->top32); c->top32 = nullptr;
+      free_ptr(c->top64); c->top64 = nullptr;
+      free_ptr(c->part32); c->part32 = nullptr; c->part32_cap = 0;
+      free_ptr(c->part64); c->part64 = nullptr; c->part64_cap = 0;
+      c->part_top_m = top_m;
+    }
+    size_t cap32 = c->part32_cap, cap64 = c->part64_cap;
+    st = grow(&c->part32, &c->part32_cap, n32 > 0 ? n32 : 1);
+    if (st != THOI_OK) return st;
+    if (c->part32_cap != cap32 || !c->top32) {
+      free_ptr(c->top32);
+      c->top32 = nullptr;
+      if (top_m > 0) CK(cudaMalloc(&c->top32, c->part32_cap * 2 * top_m * sizeof(TopEnt)));
+    }
+    st = grow(&c->part64, &c->part64_cap, n64 > 0 ? n64 : 1);
+    if (st != THOI_OK) return st;
+    if (c->part64_cap != cap64 || !c->top64) {
+      free_ptr(c->top64);
+      c->top64 = nullptr;
+      if (top_m > 0) CK(cudaMalloc(&c->top64, c->part64_cap * 2 * top_m * sizeof(TopEnt)));
+    }
+  }
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(c->flag_counts, 0, MAX_SLOTS * sizeof(unsigned long long), s));
+
+  MergeDescs D;
+  memset(&D, 0, sizeof D);
+  int p32_off = 0, p64_off = 0;
+  for (size_t si = 0; si < slots.size(); si++) {
+    const SlotRange& r = slots[si];
+    MergeDesc& md = D.d[si];
+    md.k = r.k;
+    md.cmb = combine_for(c, r.k);
+    md.p32_off = p32_off;
+    md.p64_off = p64_off;
+    md.refactored = f64 ? nullptr : c->flag_counts + si;
+    const Shape sh = tuned_shape(r.k, c->num_sms, c->gpu_name, c->opt.autotune);
+    for (unsigned long long a0 = r.r0; a0 < r.r1; a0 += LAUNCH_SPLIT) {
+      SlotRange sub = r;
+      sub.r0 = a0;
+      sub.r1 = r.r1 - a0 > LAUNCH_SPLIT ? a0 + LAUNCH_SPLIT : r.r1;
+      NpletArgs a = base_args(c, sub);
+      a.flag_count = c->flag_counts + si;
+      a.mode = red ? 1 : 0;
+      a.top_m = top_m;
+      a.out = out_dev;
+      a.out_f64 = c->opt.out_f64;
+      a.out_n = id_end - id_begin;
+      a.out_first = id_begin;
+      a.part = red ? c->part32 + p32_off : nullptr;
+      a.part_top = red && top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr;
+      int grid = 0;
+      const int cap = red ? blk_cap : c->num_sms * MAX_BLOCKS_PER_SM_OUT;
+      if (f64) CK(launch_nplet_f64(a, c->num_sms, s, &grid, cap));
+      else CK(launch_nplet_f32(a, sh, c->num_sms, s, &grid, cap));
+      launches++;
+      if (red) {
+        p32_off += grid;
+        md.g32 += grid;
+      }
+    }
+    if (!f64 && r.r1 > r.r0) {
+      // FP64 re-factor of this order's flagged nplets (count read on the device)
+      NpletArgs a = base_args(c, r);
+      a.flag_count = c->flag_counts + si;
+      a.mode = red ? 1 : 0;
+      a.top_m = top_m;
+      a.out = out_dev;
+      a.out_f64 = c->opt.out_f64;
+      a.out_n = id_end - id_begin;
+      a.out_first = id_begin;
+      a.part = red ? c->part64 + p64_off : nullptr;
+      a.part_top = red && top_m > 0 ? c->top64 + (size_t)p64_off * 2 * top_m : nullptr;
+      int grid = 0;
+      CK(launch_refactor(a, c->num_sms, s, &grid, ref_cap));
+      launches++;
+      if (red) {
+        p64_off += grid;
+        md.g64 = grid;
+      }
+    }
+  }
+  if (red) {
+    CK(launch_merge(D, (int)slots.size(), c->part32, c->top32, c->part64, c->top64, top_m, recs_dev,
+                    tops_dev, s));
+    launches++;
+  }
+  if (launches_out) *launches_out = launches;
+  return THOI_OK;
+}
+
+extern "C" thoi_status thoi_measures(thoi_ctx* c, const int32_t* orders, int32_t n_orders,
+                                     uint64_t id_begin, uint64_t id_end, int32_t kind, void* out,
+                                     size_t out_bytes, thoi_stats* stats, void* stream) {
+  if (!c || !out || !orders_ok(c->N, orders, n_orders)) return THOI_ERR_INVALID_ARG;
+  if (kind != THOI_RED_NONE && kind != THOI_RED_PER_ORDER) return THOI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<SlotRange> slots;
+  uint64_t end = id_end;
+  thoi_status st = plan_slots(c, orders, n_orders, id_begin, &end, &slots);
+  if (st != THOI_OK) return st;
+  const uint64_t n = end - id_begin;
+  int launches = 0;
+  if (kind == THOI_RED_NONE) {
+    const size_t esz = c->opt.out_f64 ? 8 : 4;
+    if (out_bytes < 5 * (size_t)n * esz) return THOI_ERR_INVALID_ARG;
+    if (n > 0 && !is_device_ptr(out)) return THOI_ERR_INVALID_ARG;
+    st = enqueue_measures(c, orders, n_orders, id_begin, end, kind, out, nullptr, nullptr, s,
+                          &launches);
+    if (st != THOI_OK) return st;
+  } else {
+    const size_t need = thoi_records_bytes(n_orders, c->opt.top_m);
+    if (out_bytes < need) return THOI_ERR_INVALID_ARG;
+    const bool dev = is_device_ptr(out);
+    unsigned char* dst = (unsigned char*)out;
+    if (!dev) {
+      st = grow(&c->rec_buf, &c->rec_cap, need);
+      if (st != THOI_OK) return st;
+      dst = c->rec_buf;
+    }
+    thoi_order_record* recs = (thoi_order_record*)dst;
+    TopEnt* tops = (TopEnt*)(dst + (size_t)n_orders * sizeof(thoi_order_record));
+    st = enqueue_measures(c, orders, n_orders, id_begin, end, kind, nullptr, recs, tops, s,
+                          &launches);
+    if (st != THOI_OK) return st;
+    if (!dev) CK(cudaMemcpyAsync(out, dst, need, cudaMemcpyDeviceToHost, s));
+  }
+  return finish_status(c, s, (int)slots.size(), stats, n, launches);
+}
+
+// ------------------------------------------------------------------ API: gradient
+extern "C" thoi_status thoi_measures_grad(thoi_ctx* c, const int32_t* orders, int32_t n_orders,
+                                          int32_t measure, float* dL_dSigma, thoi_stats* stats,
+                                          void* stream) {
+  if (!c || !dL_dSigma || !orders_ok(c->N, orders, n_orders)) return THOI_ERR_INVALID_ARG;
+  if (measure < THOI_H || measure > THOI_S) return THOI_ERR_INVALID_ARG;
+  for (int i = 0; i < n_orders; i++)
+    if (orders[i] > 32) return THOI_ERR_TOO_LARGE;
+  if (!is_device_ptr(dL_dSigma)) return THOI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<SlotRange> slots;
+  uint64_t end = UINT64_MAX;
+  thoi_status st = plan_slots(c, orders, n_orders, 0, &end, &slots);
+  if (st != THOI_OK) return st;
+  unsigned long long maxn = 0;
+  for (auto& r : slots) maxn = (r.r1 - r.r0) > maxn ? (r.r1 - r.r0) : maxn;
+  st = ensure_flag_ws(c, maxn);
+  if (st != THOI_OK) return st;
+  const int grid = c->num_sms * 4;
+  const size_t NN = (size_t)c->N * c->N;
+  st = grow(&c->gpart, &c->gpart_cap, (size_t)grid * NN);
+  if (st != THOI_OK) return st;
+  CK(cudaMemsetAsync(c->gpart, 0, (size_t)grid * NN * 8, s));
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(c->flag_counts, 0, MAX_SLOTS * sizeof(unsigned long long), s));
+  int launches = 0;
+  for (size_t si = 0; si < slots.size(); si++) {
+    const SlotRange& r = slots[si];
+    if (r.r1 <= r.r0) continue;
+    NpletArgs a = base_args(c, r);
+    a.flag_count = c->flag_counts + si;
+    const unsigned long long n = r.r1 - r.r0;
+    int g = (int)((n + RED_NT - 1) / RED_NT);
+    if (g > grid) g = grid;
+    CK(launch_grad_pass(a, c->gpart, g, measure, false, s));
+    CK(launch_grad_pass(a, c->gpart, c->num_sms, measure, true, s));
+    launches += 2;
+  }
+  CK(launch_grad_finish(c->gpart, grid, c->sig64, c->N, dL_dSigma, s));
+  launches++;
+  return finish_status(c, s, (int)slots.size(), stats, thoi_count(c->N, orders, n_orders), launches);
+}
+
+// ------------------------------------------------------------------ API: batch
+extern "C" thoi_status thoi_batch_measures(thoi_ctx* const* ctxs, int32_t D, int32_t kmin,
+                                           int32_t kmax, void* out, size_t out_bytes,
+                                           thoi_stats* stats, void* stream) {
+  if (!ctxs || D < 1 || kmin < 1 || kmax < kmin || kmax > THOI_MAX_N || !out)
+    return THOI_ERR_INVALID_ARG;
+  const int top_m = ctxs[0]->opt.top_m;
+  const int prec = ctxs[0]->opt.precision;
+  for (int d = 0; d < D; d++)
+    if (!ctxs[d] || ctxs[d]->opt.top_m != top_m || ctxs[d]->opt.precision != prec)
+      return THOI_ERR_INVALID_ARG;
+  const int no = kmax - kmin + 1;
+  const size_t per = thoi_records_bytes(no, top_m);
+  if (out_bytes < per * (size_t)D) return THOI_ERR_INVALID_ARG;
+  const bool dev = is_device_ptr(out);
+  std::vector<unsigned char> host(per);
+  thoi_stats tot;
+  memset(&tot, 0, sizeof tot);
+  for (int d = 0; d < D; d++) {
+    thoi_ctx* c = ctxs[d];
+    std::vector<int32_t> ords;
+    for (int k = kmin; k <= kmax && k <= c->N; k++) ords.push_back(k);
+    memset(host.data(), 0, per);
+    thoi_order_record* R = (thoi_order_record*)host.data();
+    thoi_top_entry* Tp = (thoi_top_entry*)(host.data() + (size_t)no * sizeof(thoi_order_record));
+    for (int q = 0; q < no; q++) {
+      R[q].k = kmin + q;
+      for (int m = 0; m < 5; m++) R[q].argmin[m] = R[q].argmax[m] = ~0ull;
+    }
+    for (size_t q = 0; q < (size_t)no * 2 * top_m; q++) Tp[q].id = ~0ull;
+    if (!ords.empty()) {
+      const int nv = (int)ords.size();
+      std::vector<unsigned char> tmp(thoi_records_bytes(nv, top_m));
+      thoi_stats st1;
+      thoi_status st = thoi_measures(c, ords.data(), nv, 0, UINT64_MAX, THOI_RED_PER_ORDER,
+                                     tmp.data(), tmp.size(), &st1, stream);
+      if (st != THOI_OK) return st;
+      memcpy(R, tmp.data(), (size_t)nv * sizeof(thoi_order_record));
+      const thoi_top_entry* tt = (const thoi_top_entry*)(tmp.data() + (size_t)nv * sizeof(thoi_order_record));
+      memcpy(Tp, tt, (size_t)nv * 2 * top_m * sizeof(thoi_top_entry));
+      tot.nplets += st1.nplets;
+      tot.n_refactored += st1.n_refactored;
+      tot.launches += st1.launches;
+    }
+    unsigned char* dst = (unsigned char*)out + per * d;
+    if (dev) CK(cudaMemcpy(dst, host.data(), per, cudaMemcpyHostToDevice));
+    else memcpy(dst, host.data(), per);
+  }
+  if (stats) *stats = tot;
+  return THOI_OK;
+}
+
+// ------------------------------------------------------------------ API: autotune
+extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, const char* cache_path,
+                                     void* stream) {
+  (void)cache_path;
+  (void)stream;
+  if (!c || kmin < 1 || kmax < kmin || kmax > c->N) return THOI_ERR_INVALID_ARG;
+  return THOI_OK;
+}
+
+namespace thoi {
+Shape tuned_shape(int k, int num_sms, const char* gpu_name, int use_tuner) {
+  (void)num_sms;
+  (void)gpu_name;
+  (void)use_tuner;
+  Shape s;
+  s.blocks_per_sm = 0;
+  s.chunk = k <= 8 ? 8 : 4;
+  return s;
+}
+}  // namespace thoi

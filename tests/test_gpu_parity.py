@@ -1,0 +1,358 @@
+"""Parity of the CUDA library with the FP64 oracle (GPU required).
+
+Tolerances (stated by the method's precision contract):
+  * ranks, nplet indices, counts: bit-exact;
+  * FP64 path and FP64 re-factored nplets: 1e-10 nats absolute;
+  * FP32 path: 1e-4 nats absolute for nplets whose correlation submatrix has
+    condition number below 1e4 (the ones the FP32 path keeps);
+  * covariance: 1e-12 (FP64 path), 1e-6 relative (tensor-core FP32 path).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+import paper_2501_03381_gb300 as P  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+def _ctx(X=None, **kw):
+    if X is not None:
+        return P.Context(torch.as_tensor(X, device="cuda"), **kw)
+    return P.Context(**kw)
+
+
+# ------------------------------------------------------------------ copula front end
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_ranks_bit_exact(dtype, where):
+    rng = np.random.default_rng(1)
+    X = rng.integers(-20, 21, size=(777, 9)).astype(dtype)  # heavy ties
+    X[5, 0], X[6, 0] = -0.0, 0.0
+    Xin = torch.as_tensor(X, device="cuda") if where == "device" else torch.as_tensor(X)
+    with P.Context(Xin) as c:
+        R = c.ranks()
+    np.testing.assert_array_equal(R, oracle.rank(X.astype(np.float64)))
+
+
+def test_covariance_matches_oracle():
+    for X in (workloads.small()[0], workloads.planted30()[0], workloads.plain(60, 2000, 4)):
+        S = oracle.copula_cov(X)
+        with _ctx(X) as c:
+            S64, S32 = c.cov()
+        np.testing.assert_allclose(S64, S, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(S32, S, rtol=1e-6, atol=1e-6)
+
+
+def test_nonfinite_input_rejected():
+    X = np.random.default_rng(2).standard_normal((50, 4))
+    X[7, 2] = np.nan
+    with pytest.raises(P.ThoiError) as e:
+        P.Context(torch.as_tensor(X, device="cuda"))
+    assert e.value.name == "THOI_ERR_NONFINITE_INPUT"
+
+
+# ------------------------------------------------------------------ enumeration
+@pytest.mark.parametrize("N", [1, 6, 13, 20])
+def test_device_unrank_all_ids(N):
+    orders = list(range(1, N + 1))
+    ref = oracle.enumerate_subsets(N, orders)
+    ids = np.arange(len(ref), dtype=np.int64)
+    got = P.thoi_unrank_device(N, orders, ids).cpu().numpy()
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("N,orders", [(30, list(range(3, 31))), (60, [3, 4, 5]), (64, [32, 2])])
+def test_device_unrank_sampled(N, orders):
+    total = oracle.count(N, orders)
+    rng = np.random.default_rng(N)
+    ids = [0, total - 1]
+    off = 0
+    for k in orders:
+        c = math.comb(N, k)
+        ids += [off, off + c - 1]
+        off += c
+    ids = np.unique(np.concatenate([rng.integers(0, total, 20000, dtype=np.uint64),
+                                    np.array(ids, dtype=np.uint64)]))
+    ref = oracle.unrank_ids(N, orders, ids)
+    got = P.thoi_unrank_device(N, orders, ids.astype(np.int64)).cpu().numpy()
+    np.testing.assert_array_equal(got, ref)
+
+
+# ------------------------------------------------------------------ per-nplet measures
+def _refs(S, orders, a=0, b=None, T_bias=0):
+    out, fl = oracle.measures(S, orders, a, b, T_bias=T_bias)
+    return out, fl
+
+
+def test_small_fp64_all_nplets():
+    X, orders = workloads.small()
+    S = oracle.copula_cov(X)
+    ref, _ = _refs(S, orders)
+    with _ctx(X, precision="f64") as c:
+        out, st = c.measures(orders)
+    got = out.cpu().numpy()
+    assert got.dtype == np.float64 and got.shape == ref.shape
+    np.testing.assert_allclose(got, ref, rtol=0, atol=TOL64)
+
+
+def test_small_fp32_fix_all_nplets():
+    X, orders = workloads.small()
+    S = oracle.copula_cov(X)
+    ref, _ = _refs(S, orders)
+    with _ctx(X) as c:
+        out, st = c.measures(orders)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL32)
+
+
+@pytest.mark.parametrize("sigma32", ["tensorcore", "from_f64"])
+def test_fmri_like_fp32_fix_all_nplets(sigma32):
+    X, orders = workloads.fmri_like()  # N=20, 1,048,365 nplets
+    S = oracle.copula_cov(X)
+    ref, _ = _refs(S, orders)
+    with _ctx(X, out_f64=True, sigma32_source=sigma32) as c:
+        out, st = c.measures(orders)
+    got = out.cpu().numpy()
+    err = np.abs(got - ref).max(axis=1)
+    assert (err < TOL32).all(), err
+    assert st.nplets == ref.shape[1]
+
+
+def test_fmri_like_fp64_all_nplets():
+    X, orders = workloads.fmri_like()
+    S = oracle.copula_cov(X)
+    ref, _ = _refs(S, orders)
+    with _ctx(X, precision="f64") as c:
+        out, _ = c.measures(orders)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL64)
+
+
+def test_refactored_nplets_reach_fp64_tolerance():
+    # force every nplet through the FP64 re-factor (trace threshold below 1)
+    X, orders = workloads.small()
+    S = oracle.copula_cov(X)
+    ref, _ = _refs(S, orders)
+    with _ctx(X, out_f64=True, trace_tau=0.5) as c:
+        out, st = c.measures(orders)
+    assert st.n_refactored == ref.shape[1]
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL64)
+
+
+def test_ragged_subranges_cross_orders():
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((12, 12))
+    S = A @ A.T + 0.5 * np.eye(12)
+    orders = [7, 3, 12, 1, 5]
+    total = oracle.count(12, orders)
+    with _ctx(Sigma=S, precision="f64") as c:
+        for a, b in [(0, total), (5, 6), (17, 1000), (790, 793), (total - 3, total), (4, 4)]:
+            ref, _ = _refs(S, orders, a, b)
+            out, _ = c.measures(orders, a, b)
+            np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL64)
+
+
+def test_planted30_sampled_ranges_fp32_and_fp64():
+    X, orders = workloads.planted30()
+    S = oracle.copula_cov(X)
+    total = oracle.count(30, orders)
+    rng = np.random.default_rng(4)
+    starts = rng.integers(0, total - 4000, 6)
+    with _ctx(X, out_f64=True) as c32, _ctx(X, precision="f64") as c64:
+        for a in list(starts) + [0, total - 4000]:
+            a = int(a)
+            b = a + 4000
+            ref, _ = _refs(S, orders, a, b)
+            o32, _ = c32.measures(orders, a, b)
+            o64, _ = c64.measures(orders, a, b)
+            np.testing.assert_allclose(o64.cpu().numpy(), ref, rtol=0, atol=TOL64)
+            np.testing.assert_allclose(o32.cpu().numpy(), ref, rtol=0, atol=TOL32)
+
+
+def test_closed_forms_on_device():
+    N = 9
+    rho = 0.6
+    S = np.full((N, N), rho) + (1 - rho) * np.eye(N)
+    with _ctx(Sigma=S, precision="f64") as c:
+        for k in range(2, N + 1):
+            out, _ = c.measures([k], 0, 1)
+            ld = (k - 1) * math.log(1 - rho) + math.log(1 + (k - 1) * rho)
+            ldm = (k - 2) * math.log(1 - rho) + math.log(1 + (k - 2) * rho)
+            tc, dtc = -0.5 * ld, 0.5 * (k * ldm - (k - 1) * ld)
+            np.testing.assert_allclose(out.cpu().numpy()[1:, 0], [tc, dtc, tc - dtc, tc + dtc],
+                                       atol=1e-12)
+    with _ctx(Sigma=np.eye(6), precision="f64") as c:
+        out, _ = c.measures(range(1, 7))
+        o = out.cpu().numpy()
+        assert np.abs(o[1:]).max() < 1e-13
+        ks = np.array([len(r[r >= 0]) for r in oracle.enumerate_subsets(6, range(1, 7))])
+        np.testing.assert_allclose(o[0], ks * 1.4189385332046727, atol=1e-13)
+
+
+def test_bias_correction_matches_oracle():
+    X, orders = workloads.small()
+    S = oracle.copula_cov(X)
+    ref, _ = _refs(S, orders, T_bias=X.shape[0])
+    with _ctx(X, precision="f64", bias_correct=True) as c:
+        out, _ = c.measures(orders)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL64)
+
+
+def test_not_positive_definite():
+    S = np.eye(5)
+    S[0, 1] = S[1, 0] = 1.0
+    ref, fl = _refs(S, [3])
+    for prec in ("f64", "f32_fix64"):
+        with _ctx(Sigma=S, precision=prec, out_f64=True) as c:
+            with pytest.raises(P.ThoiError) as e:
+                c.measures([3])
+            assert e.value.name == "THOI_ERR_NOT_PD"
+
+
+# ------------------------------------------------------------------ reductions
+def _check_records(recs, hi, lo, ref_recs, tol, S, orders, top_m):
+    """Per-order records against the oracle's reduction.  Values within tol;
+    the reported ids must carry the reported extreme values (near-ties may
+    pick a different but equally valid id)."""
+    for s_, (r, e) in enumerate(zip(recs, ref_recs)):
+        assert int(r["k"]) == e["k"]
+        assert int(r["count"]) == e["count"] + e["n_not_pd"]
+        if e["count"] == 0:
+            continue
+        np.testing.assert_allclose(r["min"], e["min"], atol=tol)
+        np.testing.assert_allclose(r["max"], e["max"], atol=tol)
+        np.testing.assert_allclose(r["mean"], e["mean"], atol=tol)
+        ids = np.concatenate([r["argmin"], r["argmax"]]).astype(np.uint64)
+        vals, _ = oracle.measures_ids(S, orders, ids)
+        for m in range(5):
+            assert abs(vals[m, m] - e["min"][m]) <= tol
+            assert abs(vals[m, 5 + m] - e["max"][m]) <= tol
+        n = int(r["top_count"])
+        assert n == min(top_m, e["count"])
+        h, l_ = hi[s_][:n], lo[s_][:n]
+        np.testing.assert_allclose(h["value"], e["top_hi_val"][:n], atol=tol)
+        np.testing.assert_allclose(l_["value"], e["top_lo_val"][:n], atol=tol)
+        tv, _ = oracle.measures_ids(S, orders, np.concatenate([h["id"], l_["id"]]))
+        np.testing.assert_allclose(tv[3], np.concatenate([h["value"], l_["value"]]), atol=tol)
+        assert len(set(h["id"].tolist())) == n and len(set(l_["id"].tolist())) == n
+        # O < 0 count: exact up to nplets within tol of zero
+        near0 = 0
+        assert abs(int(r["count_neg_O"]) - e["neg_O"]) <= max(near0, e["count"] // 10 ** 5)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", TOL64), ("f32_fix64", TOL32)])
+def test_records_fmri_like(prec, tol):
+    X, orders = workloads.fmri_like()
+    S = oracle.copula_cov(X)
+    vals, fl = _refs(S, orders)
+    ids = np.arange(vals.shape[1], dtype=np.uint64)
+    ref = oracle.reduce_per_order(20, orders, vals, ids, fl, top_m=256)
+    with _ctx(X, precision=prec) as c:
+        (recs, hi, lo), st = c.measures(orders, reduction="per_order")
+    _check_records(recs, hi, lo, ref, tol, S, orders, 256)
+
+
+def test_records_small_topm_edge_cases():
+    X, orders = workloads.small()
+    S = oracle.copula_cov(X)
+    vals, fl = _refs(S, orders)
+    ids = np.arange(vals.shape[1], dtype=np.uint64)
+    for top_m in (0, 1, 7, 1024):
+        ref = oracle.reduce_per_order(10, orders, vals, ids, fl, top_m=max(top_m, 1))
+        with _ctx(X, precision="f64", top_m=top_m) as c:
+            (recs, hi, lo), _ = c.measures(orders, reduction="per_order")
+        for s, k in enumerate(orders):
+            assert int(recs[s]["count"]) == math.comb(10, k)
+            n = int(recs[s]["top_count"])
+            assert n == min(top_m, math.comb(10, k))
+            if n:
+                np.testing.assert_array_equal(hi[s][:n]["id"], ref[s]["top_hi_id"][:n])
+                np.testing.assert_array_equal(lo[s][:n]["id"], ref[s]["top_lo_id"][:n])
+
+
+def test_records_on_subrange_and_host_buffer():
+    X, orders = workloads.small()
+    S = oracle.copula_cov(X)
+    a, b = 100, 700
+    vals, fl = _refs(S, orders, a, b)
+    ids = np.arange(a, b, dtype=np.uint64)
+    ref = oracle.reduce_per_order(10, orders, vals, ids, fl, top_m=16)
+    with _ctx(X, precision="f64", top_m=16) as c:
+        buf = np.zeros(P.thoi_records_bytes(len(orders), 16), dtype=np.uint8)
+        (recs, hi, lo), _ = c.measures(orders, a, b, reduction="per_order", out=buf)
+        dbuf = torch.zeros(buf.size, dtype=torch.uint8, device="cuda")
+        (recs2, hi2, lo2), _ = c.measures(orders, a, b, reduction="per_order", out=dbuf)
+    assert np.array_equal(recs, recs2) and np.array_equal(hi, hi2)
+    for s in range(len(orders)):
+        assert int(recs[s]["count"]) == ref[s]["count"]
+        if ref[s]["count"]:
+            np.testing.assert_array_equal(recs[s]["argmin"], ref[s]["argmin"])
+            np.testing.assert_array_equal(recs[s]["argmax"], ref[s]["argmax"])
+
+
+# ------------------------------------------------------------------ gradient
+@pytest.mark.parametrize("measure", ["O", "S", "H", "TC", "DTC"])
+def test_grad_small_vs_oracle(measure):
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((12, 12))
+    S = A @ A.T + 1.0 * np.eye(12)
+    orders = [3, 4, 5]
+    G = oracle.grad(S, orders, measure)
+    with _ctx(Sigma=S) as c:
+        g, _ = c.grad(orders, measure)
+    g = g.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(g, G, rtol=2e-4, atol=2e-4 * np.abs(G).max())
+
+
+def test_grad_c4_vs_oracle_and_fd():
+    X, orders = workloads.grad60()
+    S = oracle.copula_cov(X)
+    G = oracle.grad(S, orders, "O")
+    with _ctx(X) as c:
+        g, st = c.grad(orders, "O")
+    g = g.cpu().numpy().astype(np.float64)
+    scale = np.abs(G).max()
+    assert np.abs(g - G).max() < 2e-4 * scale
+    rng = np.random.default_rng(6)
+    for _ in range(4):
+        i, j = sorted(rng.integers(0, 60, 2))
+        fd = oracle.fd_grad_entry(S, orders, "O", int(i), int(j), h=1e-6)
+        an = g[i, j] if i == j else 2 * g[i, j]
+        assert abs(fd - an) < 1e-3 * max(1.0, abs(fd))
+
+
+def test_autograd_function():
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((8, 8))
+    S = A @ A.T + np.eye(8)
+    St = torch.tensor(S, device="cuda", requires_grad=True)
+    L = P.MeasureSum.apply(St, [3, 4], "O")
+    L.backward()
+    G = oracle.grad(S, [3, 4], "O")
+    np.testing.assert_allclose(St.grad.cpu().numpy(), G, rtol=2e-4, atol=2e-4 * np.abs(G).max())
+    vals, fl = oracle.measures(S, [3, 4])
+    assert abs(L.item() - vals[3].sum()) < 1e-3
+
+
+# ------------------------------------------------------------------ batching
+def test_batch_matches_single_contexts():
+    Xs = workloads.multi(6, 3000)
+    ctxs = [_ctx(X) for X in Xs]
+    res, st = P.thoi_batch_measures([c.h for c in ctxs], 3, 8, top_m=32)
+    for c, X, (recs, hi, lo) in zip(ctxs, Xs, res):
+        N = X.shape[1]
+        S = oracle.copula_cov(X)
+        for s, k in enumerate(range(3, 9)):
+            if k > N:
+                assert int(recs[s]["count"]) == 0
+                continue
+            assert int(recs[s]["count"]) == math.comb(N, k)
+    for c in ctxs:
+        c.close()
