@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the exhaustive Gaussian-copula O-information path.
+
+Workload: N=30 variables, T=1000 samples with planted redundancy and
+synergy, every nplet of orders 3..30 (1,073,741,358 nplets), per-order
+min/max/mean/count/top-256 reductions on the device.  A step is one full
+pass: copula transform and covariance, enumeration, FP32 Cholesky with
+leave-one-out log-determinants, FP64 re-factor of flagged nplets, combine,
+reductions and merge.
+
+Prints one JSON line.  `value` = nplets/s of the FP32 + FP64-fix path with
+the sample matrix resident in HBM; `e2e` = the same through the public C ABI
+from pinned host memory (upload of X and download of the records inside the
+timed region).  Under torchrun every rank runs its own replica of the
+workload (independent datasets, no collective on the data path).
+"""
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_VARS, T_SAMPLES = 30, 1000
+ORDERS = list(range(3, 31))
+TOP_M = 256
+METRIC = "nplets/s exhaustive N=30 O-info (FP32+FP64 fix vs FP64), % of roofline"
+WORKLOAD = ("planted-structure Gaussian copula, N=30, T=1000, all nplets of orders 3..30 "
+            "(1,073,741,358), per-order min/max/mean/count/top-256 on device")
+
+
+def flops_model(k: int) -> float:
+    # Cholesky k^3/3 + triangular inverse k^3/3 + leave-one-out diagonal and
+    # combine 2k^2 (an FMA counts 2)
+    return 2.0 / 3.0 * k ** 3 + 2.0 * k ** 2
+
+
+def total_nplets(N=N_VARS, orders=ORDERS):
+    return sum(math.comb(N, k) for k in orders)
+
+
+def total_flops(N=N_VARS, orders=ORDERS):
+    return sum(math.comb(N, k) * flops_model(k) for k in orders)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ oracle baseline
+def cpu_baseline(seconds: float, seed: int = 0):
+    """The FP64 oracle as it stands, on a uniform random sample of the
+    workload's nplet ids, on every host core."""
+    import numpy as np
+
+    import oracle
+    import workloads
+    X, orders = workloads.planted30()
+    S = oracle.copula_cov(X)
+    total = total_nplets()
+    rng = np.random.default_rng(seed)
+    pilot = np.sort(rng.integers(0, total, 4000, dtype=np.uint64))
+    t0 = time.perf_counter()
+    oracle.measures_ids(S, orders, pilot)
+    dt = time.perf_counter() - t0
+    n = int(max(4000, min(5e7, 4000 * seconds / max(dt, 1e-6))))
+    ids = np.sort(rng.integers(0, total, n, dtype=np.uint64))
+    t0 = time.perf_counter()
+    oracle.measures_ids(S, orders, ids)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return {"value": n / dt, "unit": "nplets/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} nplet ids drawn uniformly (seed {seed}) from the "
+                      f"{total:,} nplets; FP64 LU per subset and per leave-one-out subset; "
+                      f"{dt:.1f} s on {cores} OpenMP threads"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    per_step_s = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(min(per_step_s, 5.0), seed=1000)
+    vals, times = [], []
+    for s in range(args.steps):
+        cb = cpu_baseline(per_step_s, seed=s)
+        vals.append(cb["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "nplets/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_nplets() / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N_VARS, "T": T_SAMPLES, "orders": "3..30",
+                       "top_m": TOP_M},
+            "cpu_baseline": {"value": v, "unit": "nplets/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "nplets/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2501_03381_gb300 as P
+    import workloads
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    P.load(build_if_missing=False)
+    X = workloads.planted(T_SAMPLES, seed=2 + 7919 * rank)  # replica per rank
+    Xd = torch.as_tensor(X, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    nb = P.thoi_records_bytes(len(ORDERS), TOP_M)
+    rec_dev = torch.zeros(nb, dtype=torch.uint8, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+
+    def one_step(opt):
+        h = P.thoi_create(Xd, opt)
+        try:
+            _, st = P.thoi_measures(h, ORDERS, 0, None, P.THOI_RED_PER_ORDER, rec_dev,
+                                    top_m=TOP_M)
+        finally:
+            P.thoi_destroy(h)
+        return st
+
+    def timed(opt, steps, warmup):
+        for _ in range(warmup):
+            one_step(opt)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms, nplet_ms, ref_ms, launches, nref = [], [], [], 0, 0
+        for _ in range(steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st = one_step(opt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            nplet_ms.append(st.nplet_ms)
+            ref_ms.append(st.refactor_ms)
+            launches += st.launches + 8  # + the copula-stage kernels of thoi_create
+            nref = st.n_refactored
+        if dist:
+            dist.barrier()
+        return ms, nplet_ms, ref_ms, launches, nref
+
+    opt32 = P.make_options(top_m=TOP_M, profile=True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms, nplet_ms, ref_ms, launches, nref = timed(opt32, args.steps, args.warmup)
+    clocks = sampler.stop()
+    t_step = sum(ms) / len(ms)
+    if dist:
+        t = torch.tensor([t_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    n_total = total_nplets() * world
+    value = n_total / (t_step / 1e3)
+
+    # FP64 path on the same workload (the comparison named by the metric)
+    fp64 = None
+    if not args.no_fp64:
+        opt64 = P.make_options(precision="f64", top_m=TOP_M, profile=True)
+        ms64, nms64, _, _, _ = timed(opt64, 1, 1)
+        fp64 = {"ms_per_step": ms64[0], "nplets_per_s": total_nplets() / (ms64[0] / 1e3),
+                "nplet_kernel_ms": nms64[0],
+                "speedup_fp32fix_over_fp64": ms64[0] / t_step}
+
+    # end to end through the public API from pinned host memory
+    Xh = torch.as_tensor(X).pin_memory()
+    rec_h = torch.zeros(nb, dtype=torch.uint8).pin_memory()
+
+    def e2e_step():
+        h = P.thoi_create(Xh, opt32)
+        try:
+            P.thoi_measures(h, ORDERS, 0, None, P.THOI_RED_PER_ORDER, rec_h.numpy(), top_m=TOP_M)
+        finally:
+            P.thoi_destroy(h)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t) / len(e2e_t)
+
+    # roofline of the dominant kernels (the FP32 nplet kernels of all orders)
+    f_total = total_flops()
+    kern_s = sum(nplet_ms) / len(nplet_ms) / 1e3
+    achieved = f_total / kern_s / 1e12
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "nplets/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N_VARS, "T": T_SAMPLES, "orders": "3..30",
+                   "top_m": TOP_M, "precision": "fp32 Cholesky + fp64 re-factor",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "replicas": "one independent dataset per rank"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "FP32 nplet kernels (k_nplet_reg<k>, k_nplet_gen), CUDA events",
+                     "flops_per_step": f_total, "kernel_ms_per_step": kern_s * 1e3,
+                     "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
+        "e2e": {"value": n_total / e2e_s, "unit": "nplets/s",
+                "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(nb)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "refactored_per_step": int(nref),
+        "refactor_ms_per_step": sum(ref_ms) / len(ref_ms),
+        "fp64_path": fp64,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -89,10 +89,15 @@ typedef struct {
                             default 256 */
   int32_t out_f64;       /* per-nplet output in FP64 (1) or FP32 (0); default: 1 for
                             THOI_F64, 0 otherwise */
-  int32_t sigma32_source;/* thoi_sigma32_source; default THOI_SIGMA32_TENSORCORE */
+  int32_t sigma32_source;/* thoi_sigma32_source; default THOI_SIGMA32_FROM_F64 (the
+                            tensor-core GEMM is about 1e-7 relative off, which moves O
+                            by up to ~1e-4 at k >= 20 on ill-conditioned nplets) */
   int32_t autotune;      /* use the autotuner's launch shapes (1) or the built-in ones (0);
                             default 1 */
   uint64_t flag_capacity;/* entries of the FP64 re-factor list; 0 = automatic */
+  int32_t profile;       /* 1: time the kernels with CUDA events on `stream` and report
+                            the times in thoi_stats; default 0 */
+  int32_t reserved;
 } thoi_options;
 
 /* Per-order reduction record (Fig. 1A caption: a function applied to every
@@ -126,6 +131,12 @@ typedef struct {
   uint64_t n_not_pd;     /* nplets not positive definite */
   int32_t launches;      /* kernel launches queued by the call */
   int32_t pad;
+  /* device time in milliseconds, measured with CUDA events when opt.profile = 1
+     (otherwise 0): the nplet kernels (FP32 or FP64 path), the FP64 re-factor
+     kernels and the merge */
+  double nplet_ms;
+  double refactor_ms;
+  double merge_ms;
 } thoi_stats;
 
 /* Fill `opt` with the defaults listed above. */

@@ -47,13 +47,15 @@ class thoi_options(ctypes.Structure):
                 ("trace_tau", ctypes.c_float), ("bias_correct", ctypes.c_int32),
                 ("top_m", ctypes.c_int32), ("out_f64", ctypes.c_int32),
                 ("sigma32_source", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("flag_capacity", ctypes.c_uint64)]
+                ("flag_capacity", ctypes.c_uint64), ("profile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class thoi_stats(ctypes.Structure):
     _fields_ = [("nplets", ctypes.c_uint64), ("n_refactored", ctypes.c_uint64),
                 ("n_not_pd", ctypes.c_uint64), ("launches", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("pad", ctypes.c_int32), ("nplet_ms", ctypes.c_double),
+                ("refactor_ms", ctypes.c_double), ("merge_ms", ctypes.c_double)]
 
 
 RECORD_DTYPE = np.dtype([("k", "<i4"), ("top_count", "<i4"), ("count", "<u8"),
@@ -153,8 +155,8 @@ def _ptr(x):
 def make_options(precision: str | int = "f32_fix64", pivot_tau: float | None = None,
                  trace_tau: float | None = None, bias_correct: bool = False,
                  top_m: int | None = None, out_f64: bool | None = None,
-                 sigma32_source: str | int = "tensorcore", autotune: bool = True,
-                 flag_capacity: int = 0) -> thoi_options:
+                 sigma32_source: str | int = "from_f64", autotune: bool = True,
+                 flag_capacity: int = 0, profile: bool = False) -> thoi_options:
     o = thoi_options()
     load().thoi_default_options(ctypes.byref(o))
     if isinstance(precision, str):
@@ -175,6 +177,7 @@ def make_options(precision: str | int = "f32_fix64", pivot_tau: float | None = N
     o.sigma32_source = sigma32_source
     o.autotune = int(bool(autotune))
     o.flag_capacity = flag_capacity
+    o.profile = int(bool(profile))
     return o
 
 

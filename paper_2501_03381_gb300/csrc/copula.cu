@@ -118,11 +118,11 @@ __global__ void __launch_bounds__(RED_T) k_cov64(const double* __restrict__ Z,
 // Zc = Z - mu is split into three BF16 terms hi + mid + lo (8 significant
 // bits each, 24 together).  The six products whose combined weight is at
 // most 2^-16 relative (hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid) are
-// accumulated in FP32 by mma.sync m16n8k16 over a chunk of 256 samples; the
-// per-chunk FP32 tiles are then summed in FP64.  This keeps the covariance
-// at FP32 accuracy; with two terms (hi + lo) and one FP32 accumulator over
-// all samples the error is about 1e-6, which moves O by more than 1e-4 at
-// k >= 20.
+// summed by mma.sync m16n8k16 into an FP32 accumulator that starts from zero
+// for every 16-sample step; the step sums are then added in FP64.  Letting
+// one FP32 tensor-core accumulator run over many steps biases the diagonal
+// by about -2.4e-6 relative (the accumulator add truncates), which moves O
+// by more than 1e-4 at k >= 20.
 constexpr int TC_CHUNK = 256;
 
 __global__ void k_split_bf16(const double* __restrict__ Z, const double* __restrict__ mu,
@@ -159,7 +159,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4],
 // are variables i0..i0+15, B fragment columns variables j0..j0+7, K = samples.
 __global__ void k_cov_tc(const __nv_bfloat16* __restrict__ zh, const __nv_bfloat16* __restrict__ zm,
                          const __nv_bfloat16* __restrict__ zl, long long Tp, int Np, int tiles_j,
-                         int n_tiles, float* __restrict__ part) {
+                         int n_tiles, double* __restrict__ part) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int tile = warp % n_tiles;
@@ -168,7 +168,7 @@ __global__ void k_cov_tc(const __nv_bfloat16* __restrict__ zh, const __nv_bfloat
   if (t_begin >= Tp) return;
   const int i0 = (tile / tiles_j) * 16, j0 = (tile % tiles_j) * 8;
   const int g = lane >> 2, q = lane & 3;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  double acc64[4] = {0.0, 0.0, 0.0, 0.0};
   const long long t_end = min(Tp, t_begin + TC_CHUNK);
   const __nv_bfloat16* srcs[3] = {zh, zm, zl};
   for (long long t0 = t_begin; t0 < t_end; t0 += 16) {
@@ -186,6 +186,7 @@ __global__ void k_cov_tc(const __nv_bfloat16* __restrict__ zh, const __nv_bfloat
       b[s][0] = *reinterpret_cast<const unsigned*>(Zs + rj);
       b[s][1] = *reinterpret_cast<const unsigned*>(Zs + rj + 8);
     }
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     // smallest terms first
     mma_bf16(acc, a[1], b[1]);  // mid.mid
     mma_bf16(acc, a[0], b[2]);  // hi.lo
@@ -193,23 +194,25 @@ __global__ void k_cov_tc(const __nv_bfloat16* __restrict__ zh, const __nv_bfloat
     mma_bf16(acc, a[0], b[1]);  // hi.mid
     mma_bf16(acc, a[1], b[0]);  // mid.hi
     mma_bf16(acc, a[0], b[0]);  // hi.hi
+#pragma unroll
+    for (int r = 0; r < 4; r++) acc64[r] += (double)acc[r];
   }
   // C fragment: (row g, cols 2q, 2q+1) and (row g+8, same cols)
-  float* P = part + (long long)chunk * Np * Np;
-  P[(i0 + g) * Np + j0 + 2 * q] = acc[0];
-  P[(i0 + g) * Np + j0 + 2 * q + 1] = acc[1];
-  P[(i0 + g + 8) * Np + j0 + 2 * q] = acc[2];
-  P[(i0 + g + 8) * Np + j0 + 2 * q + 1] = acc[3];
+  double* P = part + (long long)chunk * Np * Np;
+  P[(i0 + g) * Np + j0 + 2 * q] = acc64[0];
+  P[(i0 + g) * Np + j0 + 2 * q + 1] = acc64[1];
+  P[(i0 + g + 8) * Np + j0 + 2 * q] = acc64[2];
+  P[(i0 + g + 8) * Np + j0 + 2 * q + 1] = acc64[3];
 }
 
-// Sum the per-chunk FP32 tiles in FP64 (fixed chunk order), scale by 1/(T-1).
-__global__ void k_cov_tc_sum(const float* __restrict__ part, int n_chunks, int Np, int N,
+// Sum the per-chunk tiles in FP64 (fixed chunk order), scale by 1/(T-1).
+__global__ void k_cov_tc_sum(const double* __restrict__ part, int n_chunks, int Np, int N,
                              long long T, double* __restrict__ sig32acc) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N * N) return;
   const int i = idx / N, j = idx % N;
   double s = 0;
-  for (int c = 0; c < n_chunks; c++) s += (double)part[(long long)c * Np * Np + i * Np + j];
+  for (int c = 0; c < n_chunks; c++) s += part[(long long)c * Np * Np + i * Np + j];
   sig32acc[idx] = s / (double)(T - 1);
 }
 

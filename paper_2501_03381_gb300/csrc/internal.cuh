@@ -96,8 +96,8 @@ struct CopulaWs {
   void* zh;           // Np x Tp BF16 (hi, mid, lo terms of Z - mu)
   void* zm;
   void* zl;
-  float* part;        // n_chunks x Np x Np FP32 chunk tiles
-  double* sig32acc;   // N x N, FP64 sum of the FP32 chunk tiles
+  double* part;       // n_chunks x Np x Np chunk tiles
+  double* sig32acc;   // N x N, FP64 sum of the chunk tiles
 };
 struct CopulaWsSizes {
   int Np;

@@ -69,7 +69,30 @@ struct thoi_ctx {
   size_t rec_cap = 0;
   double* gpart = nullptr;    // gradient partials
   size_t gpart_cap = 0;       // doubles
+  // profiling: event pairs around launches, by class (0 nplet, 1 refactor, 2 merge)
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_class;
+  int ev_used = 0;
 };
+
+static thoi_status prof_begin(thoi_ctx* c, cudaStream_t s, int cls) {
+  if (!c->opt.profile) return THOI_OK;
+  while ((int)c->ev.size() < 2 * (c->ev_used + 1)) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    c->ev.push_back(e);
+  }
+  if ((int)c->ev_class.size() < c->ev_used + 1) c->ev_class.resize(c->ev_used + 1);
+  c->ev_class[c->ev_used] = cls;
+  CK(cudaEventRecord(c->ev[2 * c->ev_used], s));
+  return THOI_OK;
+}
+static thoi_status prof_end(thoi_ctx* c, cudaStream_t s) {
+  if (!c->opt.profile) return THOI_OK;
+  CK(cudaEventRecord(c->ev[2 * c->ev_used + 1], s));
+  c->ev_used++;
+  return THOI_OK;
+}
 
 static void free_ptr(void* p) {
   if (p) cudaFree(p);
@@ -155,9 +178,10 @@ extern "C" void thoi_default_options(thoi_options* o) {
   o->bias_correct = 0;
   o->top_m = 256;
   o->out_f64 = -1;
-  o->sigma32_source = THOI_SIGMA32_TENSORCORE;
+  o->sigma32_source = THOI_SIGMA32_FROM_F64;
   o->autotune = 1;
   o->flag_capacity = 0;
+  o->profile = 0;
 }
 
 extern "C" const char* thoi_status_string(thoi_status s) {
@@ -275,6 +299,7 @@ extern "C" void thoi_destroy(thoi_ctx* c) {
   free_ptr(c->ranks);
   free_ptr(c->status);
   if (c->h_cancel) cudaFreeHost(c->h_cancel);
+  for (auto e : c->ev) cudaEventDestroy(e);
   free_ptr(c->flag_ids);
   free_ptr(c->flag_counts);
   free_ptr(c->part32);
@@ -371,7 +396,7 @@ extern "C" thoi_status thoi_create(thoi_ctx** out, const void* X, int64_t T, int
     TRY(cudaMalloc(&w.zh, nz));
     TRY(cudaMalloc(&w.zm, nz));
     TRY(cudaMalloc(&w.zl, nz));
-    TRY(cudaMalloc(&w.part, (size_t)z.n_chunks * z.Np * z.Np * 4));
+    TRY(cudaMalloc(&w.part, (size_t)z.n_chunks * z.Np * z.Np * 8));
     TRY(cudaMalloc(&w.sig32acc, (size_t)N * N * 8));
   }
   TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s));
@@ -527,11 +552,22 @@ static thoi_status finish_status(thoi_ctx* c, cudaStream_t s, int n_slots, thoi_
   CK(cudaStreamSynchronize(s));
   unsigned long long nref = 0;
   for (int i = 0; i < n_slots; i++) nref += fc[i] < c->flag_cap ? fc[i] : c->flag_cap;
+  double ms[3] = {0, 0, 0};
+  for (int i = 0; i < c->ev_used; i++) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->ev[2 * i], c->ev[2 * i + 1]));
+    ms[c->ev_class[i]] += t;
+  }
+  c->ev_used = 0;
   if (stats) {
+    memset(stats, 0, sizeof *stats);
     stats->nplets = nplets;
     stats->n_refactored = nref;
     stats->n_not_pd = 0;
     stats->launches = launches;
+    stats->nplet_ms = ms[0];
+    stats->refactor_ms = ms[1];
+    stats->merge_ms = ms[2];
   }
   if (hs & ST_FLAG_OVERFLOW) return THOI_ERR_WORKSPACE;
   if (hs & ST_CANCELLED) return THOI_ERR_CANCELLED;
@@ -552,6 +588,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
   const bool f64 = c->opt.precision == THOI_F64;
   const int top_m = red ? c->opt.top_m : 0;
   int launches = 0;
+  c->ev_used = 0;
   unsigned long long maxn = 0;
   for (auto& r : slots) maxn = (r.r1 - r.r0) > maxn ? (r.r1 - r.r0) : maxn;
   if (!f64) {
@@ -623,8 +660,12 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       a.part_top = red && top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr;
       int grid = 0;
       const int cap = red ? blk_cap : c->num_sms * MAX_BLOCKS_PER_SM_OUT;
+      st = prof_begin(c, s, 0);
+      if (st != THOI_OK) return st;
       if (f64) CK(launch_nplet_f64(a, c->num_sms, s, &grid, cap));
       else CK(launch_nplet_f32(a, sh, c->num_sms, s, &grid, cap));
+      st = prof_end(c, s);
+      if (st != THOI_OK) return st;
       launches++;
       if (red) {
         p32_off += grid;
@@ -644,7 +685,11 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       a.part = red ? c->part64 + p64_off : nullptr;
       a.part_top = red && top_m > 0 ? c->top64 + (size_t)p64_off * 2 * top_m : nullptr;
       int grid = 0;
+      st = prof_begin(c, s, 1);
+      if (st != THOI_OK) return st;
       CK(launch_refactor(a, c->num_sms, s, &grid, ref_cap));
+      st = prof_end(c, s);
+      if (st != THOI_OK) return st;
       launches++;
       if (red) {
         p64_off += grid;
@@ -653,8 +698,12 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
     }
   }
   if (red) {
+    st = prof_begin(c, s, 2);
+    if (st != THOI_OK) return st;
     CK(launch_merge(D, (int)slots.size(), c->part32, c->top32, c->part64, c->top64, top_m, recs_dev,
                     tops_dev, s));
+    st = prof_end(c, s);
+    if (st != THOI_OK) return st;
     launches++;
   }
   if (launches_out) *launches_out = launches;
@@ -664,8 +713,9 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
 extern "C" thoi_status thoi_measures(thoi_ctx* c, const int32_t* orders, int32_t n_orders,
                                      uint64_t id_begin, uint64_t id_end, int32_t kind, void* out,
                                      size_t out_bytes, thoi_stats* stats, void* stream) {
-  if (!c || !out || !orders_ok(c->N, orders, n_orders)) return THOI_ERR_INVALID_ARG;
+  if (!c || !orders_ok(c->N, orders, n_orders)) return THOI_ERR_INVALID_ARG;
   if (kind != THOI_RED_NONE && kind != THOI_RED_PER_ORDER) return THOI_ERR_INVALID_ARG;
+  if (!out && !(kind == THOI_RED_NONE && id_begin == id_end)) return THOI_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<SlotRange> slots;
   uint64_t end = id_end;

@@ -76,7 +76,7 @@ def test_default_options(lib):
     o = P.thoi_options()
     lib.thoi_default_options(ctypes.byref(o))
     assert o.precision == 0 and o.top_m == 256 and abs(o.pivot_tau - 1e-2) < 1e-9
-    assert o.trace_tau == 100.0 and o.bias_correct == 0 and o.sigma32_source == 0
+    assert o.trace_tau == 100.0 and o.bias_correct == 0 and o.sigma32_source == 1
 
 
 def test_status_strings(lib):
