@@ -59,7 +59,31 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--only-order", type=int, default=0,
+                    help="profiling aid: run the per-order reduction of one order a few "
+                         "times and exit (for ncu captures of one kernel)")
+    ap.add_argument("--precision", default="f32_fix64", choices=["f32_fix64", "f64"],
+                    help="precision of the --only-order runs")
     return ap.parse_args()
+
+
+def run_only_order(args, local_rank):
+    import torch
+
+    import paper_2501_03381_gb300 as P
+    import workloads
+    torch.cuda.set_device(local_rank)
+    P.load(build_if_missing=False)
+    X, _ = workloads.planted30()
+    with P.Context(torch.as_tensor(X, device="cuda"), precision=args.precision, top_m=TOP_M,
+                   profile=True) as c:
+        for _ in range(max(1, args.steps)):
+            (recs, _, _), st = c.measures([args.only_order], reduction="per_order")
+    torch.cuda.synchronize()
+    print(json.dumps({"order": args.only_order, "precision": args.precision,
+                      "nplet_ms": st.nplet_ms, "refactor_ms": st.refactor_ms,
+                      "merge_ms": st.merge_ms, "count": int(recs[0]["count"])}))
+    return 0
 
 
 # ------------------------------------------------------------------ clocks
@@ -316,6 +340,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.only_order:
+        return run_only_order(args, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 
