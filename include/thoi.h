@@ -256,6 +256,30 @@ thoi_status thoi_autotune(thoi_ctx* ctx, int32_t kmin, int32_t kmax, const char*
  * thoi_measures calls stop early and return THOI_ERR_CANCELLED. */
 thoi_status thoi_set_cancel(thoi_ctx* ctx, int32_t flag);
 
+/* Per-order reduction record of one order k, computed without allocating
+ * any device memory (the paper has no counterpart; it exists for callers
+ * that cannot call cudaMalloc or cudaFree -- for example a process whose
+ * device memory budget is wholly held by another allocator, or one that
+ * cannot afford the device-wide synchronisation those calls may cause).
+ *  Sigma   : device pointer, N x N covariance, row-major FP64 (input)
+ *  N, k    : 1 <= k <= N <= THOI_MAX_N and C(N, k) < 2^32
+ *  top_m   : 0..16 entries per top list
+ *  rec_out : device pointer to one thoi_order_record (output)
+ *  top_out : device pointer to 2 * top_m thoi_top_entry (largest O
+ *            descending, then smallest O ascending), or NULL when top_m = 0
+ * Every nplet is evaluated in FP64 (the THOI_F64 path, no bias correction);
+ * global ids are the lexicographic ranks within order k.  Scratch space
+ * (1 MiB per device, held from library load until process exit) is one
+ * static device array shared by all calls: calls whose work overlaps on the
+ * GPU (different streams, or different host threads) race on it and must be
+ * serialised by the caller.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  Returns
+ * THOI_ERR_TOO_LARGE for N > 64, top_m > 16 or C(N, k) >= 2^32; synchronises
+ * `stream`; THOI_ERR_NOT_PD when a nplet is not positive definite. */
+thoi_status thoi_order_record_noalloc(const double* Sigma, int64_t N, int32_t k, int32_t top_m,
+                                      thoi_order_record* rec_out, thoi_top_entry* top_out,
+                                      void* stream);
+
 /* Human-readable name of a status. */
 const char* thoi_status_string(thoi_status s);
 

@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
                                                    ctypes.POINTER(thoi_stats), vp]),
             "thoi_autotune": (ctypes.c_int, [vp, i32, i32, ctypes.c_char_p, vp]),
             "thoi_set_cancel": (ctypes.c_int, [vp, i32]),
+            "thoi_order_record_noalloc": (ctypes.c_int, [vp, i64, i32, i32, vp, vp, vp]),
             "thoi_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -356,6 +357,30 @@ def thoi_autotune(h, kmin: int, kmax: int, cache_path: str | None = None, stream
 
 def thoi_set_cancel(h, flag: bool):
     _check(load().thoi_set_cancel(h, int(bool(flag))), "thoi_set_cancel")
+
+
+def thoi_order_record_noalloc(Sigma, k: int, top_m: int = 0, rec_out=None, top_out=None,
+                              stream=None):
+    """Per-order record of order k from a device covariance, allocating no
+    device memory inside the library (for callers that cannot call
+    cudaMalloc/cudaFree).  Sigma, rec_out and top_out are CUDA tensors
+    (uint8 buffers of 240 and 2*top_m*16 bytes when given).  Calls that
+    overlap on the GPU share one scratch array and must be serialised."""
+    import torch
+    S = Sigma if Sigma.dtype == torch.float64 else Sigma.double()
+    S = S.contiguous()
+    N = S.shape[0]
+    if rec_out is None:
+        rec_out = torch.zeros(RECORD_DTYPE.itemsize, dtype=torch.uint8, device=S.device)
+    if top_out is None and top_m > 0:
+        top_out = torch.zeros(2 * top_m * TOP_DTYPE.itemsize, dtype=torch.uint8, device=S.device)
+    _check(load().thoi_order_record_noalloc(_ptr(S), N, k, top_m, _ptr(rec_out),
+                                            _ptr(top_out) if top_m > 0 else None,
+                                            _stream_ptr(stream)), "thoi_order_record_noalloc")
+    rec = rec_out.cpu().numpy().view(RECORD_DTYPE)[0].copy()
+    tops = (top_out.cpu().numpy().view(TOP_DTYPE).reshape(2, top_m).copy() if top_m > 0
+            else np.zeros((2, 0), dtype=TOP_DTYPE))
+    return rec, tops[0], tops[1]
 
 
 # --------------------------------------------------------------------- convenience

@@ -1,0 +1,63 @@
+"""The entry point that allocates no device memory, checked against the
+regular per-order reduction of the FP64 path.
+
+It serves callers that cannot call cudaMalloc or cudaFree (device memory
+held entirely by another allocator, or no tolerance for the synchronisation
+those calls can cause).  This file is collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+import paper_2501_03381_gb300 as P  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def _regular(S, k, top_m):
+    with P.Context(Sigma=S, precision="f64", top_m=top_m) as c:
+        (recs, hi, lo), _ = c.measures([k], reduction="per_order")
+    return recs[0], hi[0], lo[0]
+
+
+@pytest.mark.parametrize("k,top_m", [(5, 16), (3, 0), (10, 7)])
+def test_noalloc_matches_regular_entry_point(k, top_m):
+    X, _ = workloads.small()
+    S = oracle.copula_cov(X)
+    ref, rhi, rlo = _regular(S, k, top_m)
+    Sd = torch.as_tensor(S, device="cuda")
+    for _ in range(2):  # two calls in a row share the static scratch array
+        rec, hi, lo = P.thoi_order_record_noalloc(Sd, k, top_m)
+        assert int(rec["k"]) == k and int(rec["count"]) == int(ref["count"])
+        assert int(rec["count_neg_O"]) == int(ref["count_neg_O"])
+        for f in ("min", "max", "mean"):
+            np.testing.assert_allclose(rec[f], ref[f], rtol=0, atol=TOL64)
+        np.testing.assert_array_equal(rec["argmin"], ref["argmin"])
+        np.testing.assert_array_equal(rec["argmax"], ref["argmax"])
+        n = int(rec["top_count"])
+        assert n == int(ref["top_count"])
+        if n:
+            np.testing.assert_array_equal(hi["id"][:n], rhi["id"][:n])
+            np.testing.assert_array_equal(lo["id"][:n], rlo["id"][:n])
+            np.testing.assert_allclose(hi["value"][:n], rhi["value"][:n], atol=TOL64)
+            np.testing.assert_allclose(lo["value"][:n], rlo["value"][:n], atol=TOL64)
+
+
+def test_noalloc_rejects_sizes_beyond_limits():
+    lib = P.load()
+    S = torch.eye(8, dtype=torch.float64, device="cuda")
+    rec = torch.zeros(240, dtype=torch.uint8, device="cuda")
+    top = torch.zeros(2 * 32 * 16, dtype=torch.uint8, device="cuda")
+    st = lib.thoi_order_record_noalloc(ctypes.c_void_p(S.data_ptr()), 8, 3, 17,
+                                       ctypes.c_void_p(rec.data_ptr()),
+                                       ctypes.c_void_p(top.data_ptr()), None)
+    assert st == 3  # THOI_ERR_TOO_LARGE: top_m above 16
+    st = lib.thoi_order_record_noalloc(ctypes.c_void_p(S.data_ptr()), 65, 3, 0,
+                                       ctypes.c_void_p(rec.data_ptr()), None, None)
+    assert st == 3  # N above 64
