@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_gen(const NpletArgs a) {
 // block order), merge the sorted top lists pairwise by (value, id), and
 // write the final record and top lists.
 constexpr int MERGE_NT = 128;
+constexpr int MERGE_SURV_CAP = 4096;  // survivors sorted in shared memory
 
 __device__ __forceinline__ bool ent_before(int side, const TopEnt& a, const TopEnt& b) {
   if (a.v != b.v) return side == 0 ? (a.v > b.v) : (a.v < b.v);
@@ -320,7 +321,114 @@ __global__ void __launch_bounds__(MERGE_NT) k_merge(const MergeDescs D,
   TopEnt* bufA = reinterpret_cast<TopEnt*>(smem);
   TopEnt* bufB = bufA + top_m;
   TopEnt* stage = bufB + top_m;
+  TopEnt* surv = stage + top_m;                              // MERGE_SURV_CAP entries
+  int* offs = reinterpret_cast<int*>(surv + MERGE_SURV_CAP);  // G + 1 entries
+  __shared__ TopEnt s_best[MERGE_NT];
+  __shared__ int s_have[MERGE_NT];
+  __shared__ int s_total;
   for (int side = 0; side < 2; side++) {
+    // (a) threshold: the best M-th entry among the blocks with a full list.
+    // Such a block alone holds M entries at least that good, so the global
+    // top M is among the entries of all lists that are at least that good.
+    {
+      TopEnt best;
+      best.v = 0.0;
+      best.id = ~0ull;
+      int have = 0;
+      for (int b = threadIdx.x; b < G; b += MERGE_NT) {
+        const PartRec& P = b < g32 ? p32[b] : p64[b - g32];
+        const int nl = side == 0 ? P.top_hi : P.top_lo;
+        if (nl < top_m) continue;
+        const TopEnt* Lst = (b < g32 ? t32 + (size_t)b * 2 * top_m
+                                     : t64 + (size_t)(b - g32) * 2 * top_m) + (size_t)side * top_m;
+        const TopEnt e = Lst[top_m - 1];
+        if (!have || ent_before(side, e, best)) { best = e; have = 1; }
+      }
+      s_best[threadIdx.x] = best;
+      s_have[threadIdx.x] = have;
+      __syncthreads();
+      for (int h = MERGE_NT / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+          const int o = threadIdx.x + h;
+          if (s_have[o] && (!s_have[threadIdx.x] || ent_before(side, s_best[o], s_best[threadIdx.x]))) {
+            s_best[threadIdx.x] = s_best[o];
+            s_have[threadIdx.x] = 1;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    const bool have = s_have[0] != 0;
+    const TopEnt thr = s_best[0];
+    bool done = false;
+    if (have) {
+      // (b) survivors per list (binary search for the entries at least as good)
+      for (int b = threadIdx.x; b < G; b += MERGE_NT) {
+        const PartRec& P = b < g32 ? p32[b] : p64[b - g32];
+        const int nl = side == 0 ? P.top_hi : P.top_lo;
+        const TopEnt* Lst = (b < g32 ? t32 + (size_t)b * 2 * top_m
+                                     : t64 + (size_t)(b - g32) * 2 * top_m) + (size_t)side * top_m;
+        int lo = 0, hi = nl > 0 ? nl : 0;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          const TopEnt e = Lst[mid];
+          const bool keep = ent_before(side, e, thr) || (e.v == thr.v && e.id == thr.id);
+          if (keep) lo = mid + 1;
+          else hi = mid;
+        }
+        offs[b + 1] = lo;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        offs[0] = 0;
+        for (int b = 0; b < G; b++) offs[b + 1] += offs[b];
+        s_total = offs[G];
+      }
+      __syncthreads();
+      const int S = s_total;
+      if (S <= MERGE_SURV_CAP) {
+        // (c) gather the survivors, sort them (bitonic), keep the first M
+        for (int b = 0; b < G; b++) {
+          const int n0 = offs[b], nb = offs[b + 1] - n0;
+          if (nb == 0) continue;
+          const TopEnt* Lst = (b < g32 ? t32 + (size_t)b * 2 * top_m
+                                       : t64 + (size_t)(b - g32) * 2 * top_m) + (size_t)side * top_m;
+          for (int q = threadIdx.x; q < nb; q += MERGE_NT) surv[n0 + q] = Lst[q];
+        }
+        int P2 = 2;
+        while (P2 < S) P2 <<= 1;
+        for (int q = S + threadIdx.x; q < P2; q += MERGE_NT) {
+          surv[q].v = side == 0 ? -pinf<double>() : pinf<double>();
+          surv[q].id = ~0ull;
+        }
+        __syncthreads();
+        for (int kk = 2; kk <= P2; kk <<= 1) {
+          for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P2; i += MERGE_NT) {
+              const int ixj = i ^ j;
+              if (ixj > i) {
+                const bool up = (i & kk) == 0;
+                const TopEnt x = surv[i], y = surv[ixj];
+                const bool sw = up ? ent_before(side, y, x) : ent_before(side, x, y);
+                if (sw) { surv[i] = y; surv[ixj] = x; }
+              }
+            }
+            __syncthreads();
+          }
+        }
+        const int nout = S < top_m ? S : top_m;
+        for (int q = threadIdx.x; q < top_m; q += MERGE_NT) {
+          TopEnt e;
+          if (q < nout) e = surv[q];
+          else { e.v = 0.0; e.id = ~0ull; }
+          top_out[(size_t)side * top_m + q] = e;
+        }
+        __syncthreads();
+        done = true;
+      }
+    }
+    if (done) continue;
+    // fallback: pairwise merge of the sorted lists
     int ncur = 0;
     TopEnt* cur = bufA;
     TopEnt* nxt = bufB;
@@ -446,7 +554,11 @@ cudaError_t launch_nplet_f32_gen(const NpletArgs& a, int num_sms, cudaStream_t s
 cudaError_t launch_merge(const MergeDescs& D, int n_slots, const PartRec* p32, const TopEnt* t32,
                          const PartRec* p64, const TopEnt* t64, int top_m, thoi_order_record* recs,
                          TopEnt* tops, cudaStream_t s) {
-  const size_t sm = top_m > 0 ? (size_t)3 * top_m * sizeof(TopEnt) : 0;
+  int gmax = 0;
+  for (int i = 0; i < n_slots; i++) gmax = D.d[i].g32 + D.d[i].g64 > gmax ? D.d[i].g32 + D.d[i].g64 : gmax;
+  const size_t sm = top_m > 0 ? (size_t)3 * top_m * sizeof(TopEnt) + MERGE_SURV_CAP * sizeof(TopEnt) +
+                                    (size_t)(gmax + 1) * sizeof(int)
+                              : 0;
   cudaError_t e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   if (n_slots <= 0) return cudaSuccess;

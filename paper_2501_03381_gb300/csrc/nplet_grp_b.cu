@@ -1,0 +1,7 @@
+// Instantiations of the lane-group FP32 nplet kernel for orders 23..24.
+#include "nplet_grp.cuh"
+
+namespace thoi {
+template cudaError_t launch_grp_k<23, 2>(const NpletArgs&, const Shape&, int, cudaStream_t, int*, int);
+template cudaError_t launch_grp_k<24, 2>(const NpletArgs&, const Shape&, int, cudaStream_t, int*, int);
+}  // namespace thoi

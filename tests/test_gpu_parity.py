@@ -361,3 +361,50 @@ def test_batch_matches_single_contexts():
             assert int(recs[s]["count"]) == math.comb(N, k)
     for c in ctxs:
         c.close()
+
+
+# ------------------------------------------------------------------ large orders
+def _wellcond(N, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((N, N))
+    S = A @ A.T + N * np.eye(N)
+    d = np.sqrt(np.diag(S))
+    return S / np.outer(d, d)
+
+
+@pytest.mark.parametrize("N,orders", [(32, list(range(21, 33))), (40, [24, 25, 33, 36])])
+def test_large_orders_lane_group_and_generic(N, orders):
+    # orders 21..32 run on the lane-group kernels (2 or 4 lanes per nplet),
+    # above 32 on the generic kernel; 32-bit and 64-bit masks
+    S = _wellcond(N, 8)
+    total = oracle.count(N, orders)
+    rng = np.random.default_rng(9)
+    offs = np.cumsum([0] + [math.comb(N, k) for k in orders])
+    ranges = []
+    for s_ in range(len(orders)):
+        a0, b0 = int(offs[s_]), int(offs[s_ + 1])
+        for _ in range(2):
+            a = int(rng.integers(a0, max(a0 + 1, b0 - 700)))
+            ranges.append((a, min(b0, a + 700)))
+        ranges.append((max(a0, b0 - 300), b0))
+    with _ctx(Sigma=S, out_f64=True) as c32, _ctx(Sigma=S, precision="f64") as c64:
+        for a, b in ranges:
+            ref, _ = _refs(S, orders, a, b)
+            o32, _ = c32.measures(orders, a, b)
+            np.testing.assert_allclose(o32.cpu().numpy(), ref, rtol=0, atol=TOL32)
+            o64, _ = c64.measures(orders, a, b)
+            np.testing.assert_allclose(o64.cpu().numpy(), ref, rtol=0, atol=TOL64)
+    if N != 32:
+        return
+    # per-order records of two large orders (10.7M nplets) against the FP64 path
+    rec_orders = [24, 27]
+    with _ctx(Sigma=S, top_m=64) as c32, _ctx(Sigma=S, precision="f64", top_m=64) as c64:
+        (r32, h32, l32), _ = c32.measures(rec_orders, reduction="per_order")
+        (r64, h64, l64), _ = c64.measures(rec_orders, reduction="per_order")
+    for s_ in range(2):
+        assert int(r32[s_]["count"]) == int(r64[s_]["count"])
+        np.testing.assert_allclose(r32[s_]["min"], r64[s_]["min"], atol=TOL32)
+        np.testing.assert_allclose(r32[s_]["max"], r64[s_]["max"], atol=TOL32)
+        np.testing.assert_allclose(r32[s_]["mean"], r64[s_]["mean"], atol=TOL32)
+        np.testing.assert_allclose(h32[s_]["value"], h64[s_]["value"], atol=TOL32)
+        np.testing.assert_allclose(l32[s_]["value"], l64[s_]["value"], atol=TOL32)
