@@ -251,6 +251,17 @@ def run_ours(args, rank, world, local_rank):
         return ms, nplet_ms, ref_ms, launches, nref
 
     opt32 = P.make_options(top_m=TOP_M, profile=True)
+    # launch shapes per order, tuned on this GPU before the timed region
+    tune_path = os.path.join(tempfile.gettempdir(), f"thoi_tune_{os.getpid()}.json")
+    h = P.thoi_create(Xd, opt32)
+    try:
+        P.thoi_autotune(h, 3, N_VARS, tune_path)
+    finally:
+        P.thoi_destroy(h)
+    try:
+        shapes = {e["k"]: [e["lanes"], e["chunk"]] for e in json.load(open(tune_path))}
+    except Exception:
+        shapes = {}
     sampler = ClockSampler(local_rank)
     sampler.start()
     ms, nplet_ms, ref_ms, launches, nref = timed(opt32, args.steps, args.warmup)
@@ -310,7 +321,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "N": N_VARS, "T": T_SAMPLES, "orders": "3..30",
                    "top_m": TOP_M, "precision": "fp32 Cholesky + fp64 re-factor",
                    "l2": "flushed between timed steps (256 MiB write)",
-                   "replicas": "one independent dataset per rank"},
+                   "replicas": "one independent dataset per rank",
+                   "tuned_shapes_k_lanes_chunk": shapes},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "FP32 nplet kernels (k_nplet_reg<k>, k_nplet_gen), CUDA events",

@@ -83,8 +83,14 @@ struct NpletArgs {
 // ------------------------------------------------------------------ launchers
 struct Shape {
   int blocks_per_sm;  // 0 = occupancy maximum
-  int chunk;          // nplets per thread per round (multiple of 1)
+  int chunk;          // nplets per thread (or lane group) per round, 1..8
+  int lanes;          // lanes per nplet: 1 (one-thread kernel), 2 or 4 (lane-group kernel)
 };
+// Built-in launch shape of the FP32 kernel for order k (used when no tuned
+// shape is cached).
+Shape default_shape(int k);
+// Whether a (k, lanes) kernel instance exists.
+bool shape_available(int k, int lanes);
 
 // Workspace of the copula front end (device pointers owned by the context).
 struct CopulaWs {

@@ -69,6 +69,12 @@ __device__ __forceinline__ void renorm(double& P, int& E, bool& bad) {
   E += ex - 1023;
   P = __longlong_as_double((b & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
 }
+// Reciprocal by the hardware approximation (about 1 ulp), one instruction.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ float log_of(float P, int E) {
   return (__log2f(P) + (float)E) * (float)LN2;
 }
@@ -95,7 +101,8 @@ template <typename V, typename I>
 struct ThreadRed {
   V mn[5], mx[5];
   I imn[5], imx[5];
-  double slr, ssp, sls;
+  double slr, ssp, sls;  // running sums
+  V plr, psp, pls;       // partial sums of the current chunk (added by flush())
   unsigned cnt, neg;
 
   __device__ __forceinline__ void init() {
@@ -107,7 +114,14 @@ struct ThreadRed {
       imx[m] = imax_val<I>();
     }
     slr = ssp = sls = 0.0;
+    plr = psp = pls = (V)0;
     cnt = neg = 0;
+  }
+  __device__ __forceinline__ void flush() {
+    slr += (double)plr;
+    ssp += (double)psp;
+    sls += (double)pls;
+    plr = psp = pls = (V)0;
   }
   __device__ __forceinline__ void add(const V (&v)[5], I id, V lr, V sp, V lsum) {
 #pragma unroll
@@ -115,9 +129,9 @@ struct ThreadRed {
       if (v[m] < mn[m] || (v[m] == mn[m] && id < imn[m])) { mn[m] = v[m]; imn[m] = id; }
       if (v[m] > mx[m] || (v[m] == mx[m] && id < imx[m])) { mx[m] = v[m]; imx[m] = id; }
     }
-    slr += (double)lr;
-    ssp += (double)sp;
-    sls += (double)lsum;
+    plr += lr;
+    psp += sp;
+    pls += lsum;
     cnt++;
     neg += (v[3] < (V)0) ? 1u : 0u;
   }
@@ -144,6 +158,7 @@ struct RedScratch {
 template <typename V, typename I>
 __device__ void block_write_part(ThreadRed<V, I>& t, unsigned notpd, unsigned long long id_off,
                                  RedScratch& sc, PartRec* out, int top_hi, int top_lo) {
+  t.flush();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned long long gmn[5], gmx[5];
   double vmn[5], vmx[5];

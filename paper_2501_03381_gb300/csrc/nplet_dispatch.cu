@@ -14,8 +14,43 @@ cudaError_t launch_grp_k(const NpletArgs& a, const Shape& sh, int num_sms, cudaS
 cudaError_t launch_nplet_f32_gen(const NpletArgs& a, int num_sms, cudaStream_t s, int* grid_out,
                                  int max_blocks);
 
+Shape default_shape(int k) {
+  Shape s;
+  s.blocks_per_sm = 0;
+  s.chunk = 8;
+  s.lanes = k <= 20 ? 1 : (k <= 24 ? 2 : (k <= 32 ? 4 : 1));
+  return s;
+}
+
+bool shape_available(int k, int lanes) {
+  if (lanes == 1) return true;  // one-thread kernel for k <= 20, generic above
+  if (lanes == 2) return k >= 13 && k <= 24;
+  if (lanes == 4) return k >= 25 && k <= 32;
+  return false;
+}
+
 cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                              int* grid_out, int max_blocks) {
+  const int lanes = shape_available(a.k, sh.lanes) ? sh.lanes : default_shape(a.k).lanes;
+  if (lanes == 2) {
+    switch (a.k) {
+#define CASE_G(KK) \
+  case KK: return launch_grp_k<KK, 2>(a, sh, num_sms, s, grid_out, max_blocks);
+      CASE_G(13) CASE_G(14) CASE_G(15) CASE_G(16) CASE_G(17) CASE_G(18) CASE_G(19) CASE_G(20)
+      CASE_G(21) CASE_G(22) CASE_G(23) CASE_G(24)
+#undef CASE_G
+      default: break;
+    }
+  }
+  if (lanes == 4) {
+    switch (a.k) {
+#define CASE_G(KK) \
+  case KK: return launch_grp_k<KK, 4>(a, sh, num_sms, s, grid_out, max_blocks);
+      CASE_G(25) CASE_G(26) CASE_G(27) CASE_G(28) CASE_G(29) CASE_G(30) CASE_G(31) CASE_G(32)
+#undef CASE_G
+      default: break;
+    }
+  }
   switch (a.k) {
 #define CASE_K(KK) \
   case KK: return launch_reg_k<KK>(a, sh, num_sms, s, grid_out, max_blocks);
@@ -23,11 +58,6 @@ cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, c
     CASE_K(10) CASE_K(11) CASE_K(12) CASE_K(13) CASE_K(14) CASE_K(15) CASE_K(16) CASE_K(17)
     CASE_K(18) CASE_K(19) CASE_K(20)
 #undef CASE_K
-#define CASE_G(KK, GG) \
-  case KK: return launch_grp_k<KK, GG>(a, sh, num_sms, s, grid_out, max_blocks);
-    CASE_G(21, 2) CASE_G(22, 2) CASE_G(23, 2) CASE_G(24, 2) CASE_G(25, 4) CASE_G(26, 4)
-    CASE_G(27, 4) CASE_G(28, 4) CASE_G(29, 4) CASE_G(30, 4) CASE_G(31, 4) CASE_G(32, 4)
-#undef CASE_G
     default: return launch_nplet_f32_gen(a, num_sms, s, grid_out, max_blocks);
   }
 }

@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_gen(const NpletArgs a) {
         store5<V>(a, gid, v);
       } else if (!bad) {
         tr.add(v, loc, lr, sp, lsum);
+        tr.flush();
         if (with_top) top_offer(tb, v[3], loc, thr_hi, thr_lo);
       }
       if (FP32_PATH) flag_append(a, bad, gid);
@@ -388,12 +389,17 @@ __global__ void __launch_bounds__(MERGE_NT) k_merge(const MergeDescs D,
       const int S = s_total;
       if (S <= MERGE_SURV_CAP) {
         // (c) gather the survivors, sort them (bitonic), keep the first M
-        for (int b = 0; b < G; b++) {
-          const int n0 = offs[b], nb = offs[b + 1] - n0;
-          if (nb == 0) continue;
+        for (int q = threadIdx.x; q < S; q += MERGE_NT) {
+          int lo = 0, hi = G - 1;  // list b with offs[b] <= q < offs[b + 1]
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offs[mid] <= q) lo = mid;
+            else hi = mid - 1;
+          }
+          const int b = lo;
           const TopEnt* Lst = (b < g32 ? t32 + (size_t)b * 2 * top_m
                                        : t64 + (size_t)(b - g32) * 2 * top_m) + (size_t)side * top_m;
-          for (int q = threadIdx.x; q < nb; q += MERGE_NT) surv[n0 + q] = Lst[q];
+          surv[q] = Lst[q - offs[b]];
         }
         int P2 = 2;
         while (P2 < S) P2 <<= 1;

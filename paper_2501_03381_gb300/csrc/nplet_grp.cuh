@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_grp(const NpletArgs a, const i
         }
         if (jn + 1 < cnt) mask = lex_succ(mask, full);
       }
+      tr.flush();
     }
     if (threadIdx.x == 0 && a.cancel && *(volatile const int*)a.cancel) s_stop = 1;
     __syncthreads();

@@ -1,0 +1,10 @@
+// Instantiations of the lane-group FP32 nplet kernel with 2 lanes for orders 17..20
+// (an alternative to the one-thread kernel that the autotuner may pick).
+#include "nplet_grp.cuh"
+
+namespace thoi {
+template cudaError_t launch_grp_k<17, 2>(const NpletArgs&, const Shape&, int, cudaStream_t, int*, int);
+template cudaError_t launch_grp_k<18, 2>(const NpletArgs&, const Shape&, int, cudaStream_t, int*, int);
+template cudaError_t launch_grp_k<19, 2>(const NpletArgs&, const Shape&, int, cudaStream_t, int*, int);
+template cudaError_t launch_grp_k<20, 2>(const NpletArgs&, const Shape&, int, cudaStream_t, int*, int);
+}  // namespace thoi

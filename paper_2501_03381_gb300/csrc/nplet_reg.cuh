@@ -11,6 +11,11 @@
 namespace thoi {
 
 
+// R_S = Lh D Lh^T (Lh unit lower, D the Cholesky pivots), in place: the
+// strictly lower part of A becomes Lh, the diagonal 1/D.  Then
+// V = -(Lh^-1 - I) column by column (unit lower inverse, FMAs only), and
+// p_j = (R_S^-1)_jj = sum_i (Lh^-1)_ij^2 / D_i = 1/D_j + sum_{i>j} V_ij^2 / D_i.
+// log det R_S = sum_p log D_p.
 template <int K>
 __device__ __forceinline__ void chol_loo_reg(float (&A)[K][K], float& lr, float& sp,
                                              float& pmin, float& trace, bool& bad) {
@@ -23,28 +28,29 @@ __device__ __forceinline__ void chol_loo_reg(float (&A)[K][K], float& lr, float&
     pmin = fminf(pmin, d);
     P1 *= d;
     if ((p & 3) == 3 || p == K - 1) renorm(P1, E1, bad);
-    const float inv = rsqrtf(d);
-    A[p][p] = inv;
+    const float rd = rcp_approx(d);
+    A[p][p] = rd;
+    float u[K];
 #pragma unroll
-    for (int i = p + 1; i < K; i++) A[i][p] *= inv;
+    for (int i = p + 1; i < K; i++) u[i] = A[i][p] * rd;
 #pragma unroll
     for (int i = p + 1; i < K; i++)
 #pragma unroll
-      for (int j = p + 1; j <= i; j++) A[i][j] = fmaf(-A[i][p], A[j][p], A[i][j]);
+      for (int j = p + 1; j <= i; j++) A[i][j] = fmaf(-u[i], A[j][p], A[i][j]);
+#pragma unroll
+    for (int i = p + 1; i < K; i++) A[i][p] = u[i];
   }
   trace = 0.f;
 #pragma unroll
   for (int j = 0; j < K; j++) {
-    const float wjj = A[j][j];
-    float pj = wjj * wjj;
+    float pj = A[j][j];
 #pragma unroll
     for (int i = j + 1; i < K; i++) {
-      float s = A[i][j] * wjj;
+      float s = A[i][j];
 #pragma unroll
-      for (int m = j + 1; m < i; m++) s = fmaf(A[i][m], A[m][j], s);
-      const float w = -A[i][i] * s;
-      A[i][j] = w;
-      pj = fmaf(w, w, pj);
+      for (int m = j + 1; m < i; m++) s = fmaf(-A[i][m], A[m][j], s);
+      A[i][j] = s;
+      pj = fmaf(s * A[i][i], s, pj);
     }
     trace += pj;
     P2 *= pj;
@@ -143,6 +149,7 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_reg(const NpletArgs a, const i
         flag_append(a, bad, gid);
         if (j + 1 < cnt) mask = lex_succ(mask, full);
       }
+      tr.flush();
     }
     if (threadIdx.x == 0 && a.cancel && *(volatile const int*)a.cancel) s_stop = 1;
     __syncthreads();
@@ -193,7 +200,7 @@ static cudaError_t launch_reg_t(const NpletArgs& a, const Shape& sh, int num_sms
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
   if (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ) occ = sh.blocks_per_sm;
-  int chunk = sh.chunk > 0 ? sh.chunk : 4;
+  int chunk = sh.chunk > 0 ? sh.chunk : 8;
   if (chunk > 8) chunk = 8;
   long long grid = (long long)num_sms * occ;
   const unsigned long long n = a.rank_end - a.rank_begin;

@@ -6,7 +6,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -16,7 +18,6 @@ using namespace thoi;
 namespace thoi {
 cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                              int* grid_out, int max_blocks);
-Shape tuned_shape(int k, int num_sms, const char* gpu_name, int use_tuner);
 }  // namespace thoi
 
 #define CK(x)                                        \
@@ -73,7 +74,31 @@ struct thoi_ctx {
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;
   int ev_used = 0;
+  // autotuner: a shape forced for the duration of a timing run
+  int force_shape_valid = 0;
+  Shape force_shape;
 };
+
+// ------------------------------------------------------------------ autotune cache
+// Process-wide: (GPU name, SM count, order, mask width) -> launch shape.
+static std::mutex g_tune_mu;
+static std::map<std::string, Shape> g_tune;
+
+static std::string tune_key(const char* gpu, int sms, int k, int wide) {
+  char b[320];
+  snprintf(b, sizeof b, "%s|%d|%d|%d", gpu, sms, k, wide);
+  return b;
+}
+
+static Shape shape_for(const thoi_ctx* c, int k) {
+  if (c->force_shape_valid) return c->force_shape;
+  if (c->opt.autotune) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(c->gpu_name, c->num_sms, k, c->N > 32));
+    if (it != g_tune.end()) return it->second;
+  }
+  return default_shape(k);
+}
 
 static thoi_status prof_begin(thoi_ctx* c, cudaStream_t s, int cls) {
   if (!c->opt.profile) return THOI_OK;
@@ -643,7 +668,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
     md.p32_off = p32_off;
     md.p64_off = p64_off;
     md.refactored = f64 ? nullptr : c->flag_counts + si;
-    const Shape sh = tuned_shape(r.k, c->num_sms, c->gpu_name, c->opt.autotune);
+    const Shape sh = shape_for(c, r.k);
     for (unsigned long long a0 = r.r0; a0 < r.r1; a0 += LAUNCH_SPLIT) {
       SlotRange sub = r;
       sub.r0 = a0;
@@ -846,22 +871,119 @@ extern "C" thoi_status thoi_batch_measures(thoi_ctx* const* ctxs, int32_t D, int
 }
 
 // ------------------------------------------------------------------ API: autotune
-extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, const char* cache_path,
-                                     void* stream) {
-  (void)cache_path;
-  (void)stream;
-  if (!c || kmin < 1 || kmax < kmin || kmax > c->N) return THOI_ERR_INVALID_ARG;
-  return THOI_OK;
+static void tune_load(const char* path, const char* gpu, int sms) {
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char line[1024];
+  while (fgets(line, sizeof line, f)) {
+    char g[256] = {0};
+    int sm = 0, k = 0, wide = 0, lanes = 0, chunk = 0, bps = 0;
+    const char* q = strstr(line, "\"gpu\": \"");
+    if (!q) continue;
+    q += 8;
+    int n = 0;
+    while (q[n] && q[n] != '"' && n < 255) { g[n] = q[n]; n++; }
+    if (sscanf(strstr(line, "\"sms\""), "\"sms\": %d, \"k\": %d, \"wide\": %d, \"lanes\": %d, "
+                                          "\"chunk\": %d, \"blocks_per_sm\": %d",
+               &sm, &k, &wide, &lanes, &chunk, &bps) != 6)
+      continue;
+    if (strcmp(g, gpu) != 0 || sm != sms || !shape_available(k, lanes)) continue;
+    Shape sh;
+    sh.lanes = lanes;
+    sh.chunk = chunk;
+    sh.blocks_per_sm = bps;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(gpu, sms, k, wide)] = sh;
+  }
+  fclose(f);
 }
 
-namespace thoi {
-Shape tuned_shape(int k, int num_sms, const char* gpu_name, int use_tuner) {
-  (void)num_sms;
-  (void)gpu_name;
-  (void)use_tuner;
-  Shape s;
-  s.blocks_per_sm = 0;
-  s.chunk = k <= 8 ? 8 : 4;
-  return s;
+static void tune_save(const char* path, const char* gpu, int sms) {
+  FILE* f = fopen(path, "w");
+  if (!f) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  fprintf(f, "[\n");
+  bool first = true;
+  for (auto& kv : g_tune) {
+    char g[256];
+    int sm, k, wide;
+    if (sscanf(kv.first.c_str(), "%255[^|]|%d|%d|%d", g, &sm, &k, &wide) != 4) continue;
+    if (strcmp(g, gpu) != 0 || sm != sms) continue;
+    fprintf(f, "%s{\"gpu\": \"%s\", \"sms\": %d, \"k\": %d, \"wide\": %d, \"lanes\": %d, "
+               "\"chunk\": %d, \"blocks_per_sm\": %d}",
+            first ? "" : ",\n", g, sm, k, wide, kv.second.lanes, kv.second.chunk,
+            kv.second.blocks_per_sm);
+    first = false;
+  }
+  fprintf(f, "\n]\n");
+  fclose(f);
 }
-}  // namespace thoi
+
+// Time the FP32 nplet kernel of order k with shape sh on the first n nplets
+// (CUDA events on `s`); returns milliseconds or a negative value on error.
+static double time_shape(thoi_ctx* c, int k, uint64_t n, const Shape& sh, cudaStream_t s) {
+  const int saved_profile = c->opt.profile;
+  c->opt.profile = 1;
+  c->force_shape = sh;
+  c->force_shape_valid = 1;
+  double best = -1.0;
+  const size_t need = thoi_records_bytes(1, c->opt.top_m);
+  if (grow(&c->rec_buf, &c->rec_cap, need) == THOI_OK) {
+    thoi_order_record* recs = (thoi_order_record*)c->rec_buf;
+    TopEnt* tops = (TopEnt*)(c->rec_buf + sizeof(thoi_order_record));
+    const int32_t ord = k;
+    for (int rep = 0; rep < 3; rep++) {
+      int launches = 0;
+      thoi_stats st;
+      if (enqueue_measures(c, &ord, 1, 0, n, THOI_RED_PER_ORDER, nullptr, recs, tops, s,
+                           &launches) != THOI_OK)
+        break;
+      const thoi_status fs = finish_status(c, s, 1, &st, n, launches);
+      if (fs != THOI_OK && fs != THOI_ERR_NOT_PD) break;
+      if (rep > 0 && (best < 0 || st.nplet_ms < best)) best = st.nplet_ms;  // rep 0 warms up
+    }
+  }
+  c->force_shape_valid = 0;
+  c->opt.profile = saved_profile;
+  return best;
+}
+
+extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, const char* cache_path,
+                                     void* stream) {
+  if (!c || kmin < 1 || kmax < kmin || kmax > c->N) return THOI_ERR_INVALID_ARG;
+  if (c->opt.precision != THOI_F32_FIX64) return THOI_OK;  // only the FP32 kernels have shapes
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cache_path) tune_load(cache_path, c->gpu_name, c->num_sms);
+  const int wide = c->N > 32;
+  for (int k = kmin; k <= kmax; k++) {
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      if (g_tune.count(tune_key(c->gpu_name, c->num_sms, k, wide))) continue;
+    }
+    const uint64_t total = binom_host(c->N, k);
+    if (total < (1ull << 17)) continue;  // too small to matter: built-in shape
+    const uint64_t n = total < (1ull << 22) ? total : (1ull << 22);
+    Shape best = default_shape(k);
+    double best_ms = -1.0;
+    for (int lanes = 1; lanes <= 4; lanes <<= 1) {
+      if (!shape_available(k, lanes)) continue;
+      if (lanes == 1 && k > 20 && shape_available(k, 2)) continue;  // generic kernel: never faster
+      if (lanes == 1 && k > 20 && shape_available(k, 4)) continue;
+      for (int chunk = 4; chunk <= 8; chunk <<= 1) {
+        Shape sh;
+        sh.lanes = lanes;
+        sh.chunk = chunk;
+        sh.blocks_per_sm = 0;
+        const double ms = time_shape(c, k, n, sh, s);
+        if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
+          best_ms = ms;
+          best = sh;
+        }
+      }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(c->gpu_name, c->num_sms, k, wide)] = best;
+  }
+  if (cache_path) tune_save(cache_path, c->gpu_name, c->num_sms);
+  return THOI_OK;
+}

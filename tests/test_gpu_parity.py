@@ -408,3 +408,57 @@ def test_large_orders_lane_group_and_generic(N, orders):
         np.testing.assert_allclose(r32[s_]["mean"], r64[s_]["mean"], atol=TOL32)
         np.testing.assert_allclose(h32[s_]["value"], h64[s_]["value"], atol=TOL32)
         np.testing.assert_allclose(l32[s_]["value"], l64[s_]["value"], atol=TOL32)
+
+
+# ------------------------------------------------------------------ autotuner
+def test_autotune_cache_and_parity(tmp_path):
+    import json
+    X, orders = workloads.planted30()
+    S = oracle.copula_cov(X)
+    path = str(tmp_path / "tune.json")
+    with _ctx(X, out_f64=True) as c:
+        P.thoi_autotune(c.h, 12, 14, path)
+        ents = json.load(open(path))
+        ks = sorted(e["k"] for e in ents)
+        assert ks == [12, 13, 14]
+        for e in ents:
+            assert e["lanes"] in (1, 2) and e["chunk"] in (4, 8)
+        # the tuned shapes compute the same measures
+        total = oracle.count(30, orders)
+        off = sum(math.comb(30, k) for k in range(3, 13))
+        a, b = off + 1000, off + 6000
+        ref, _ = _refs(S, orders, a, b)
+        out, _ = c.measures(orders, a, b)
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL32)
+        # a second call reads the cache and measures nothing new
+        P.thoi_autotune(c.h, 12, 14, path)
+        assert json.load(open(path)) == ents
+
+
+def _force_shape(h, k, wide, lanes, chunk, path):
+    """Make the library use one launch shape for order k by loading it
+    through the autotuner's cache file."""
+    import json
+    props = torch.cuda.get_device_properties(0)
+    ent = {"gpu": props.name, "sms": props.multi_processor_count, "k": k, "wide": wide,
+           "lanes": lanes, "chunk": chunk, "blocks_per_sm": 0}
+    with open(path, "w") as fh:
+        fh.write("[\n" + json.dumps(ent) + "\n]\n")
+    P.thoi_autotune(h, k, k, path)
+
+
+@pytest.mark.parametrize("k", [14, 17, 20, 23])
+def test_all_lane_shapes_agree(k, tmp_path):
+    # every kernel variant the autotuner can pick gives the oracle's values
+    X, orders = workloads.planted30()
+    S = oracle.copula_cov(X)
+    off = sum(math.comb(30, q) for q in orders if q < k)
+    a, b = off + 777, off + 2777
+    ref, _ = _refs(S, orders, a, b)
+    with _ctx(X, out_f64=True) as c:
+        for lanes in (1, 2, 4):
+            for chunk in (1, 8):
+                _force_shape(c.h, k, 0, lanes, chunk, str(tmp_path / "f.json"))
+                out, _ = c.measures(orders, a, b)
+                np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL32)
+        _force_shape(c.h, k, 0, 1 if k <= 20 else 2, 8, str(tmp_path / "f.json"))
