@@ -133,10 +133,11 @@ typedef struct {
   int32_t pad;
   /* device time in milliseconds, measured with CUDA events when opt.profile = 1
      (otherwise 0): the nplet kernels (FP32 or FP64 path), the FP64 re-factor
-     kernels and the merge */
+     kernels, the merge, and the streaming reduction */
   double nplet_ms;
   double refactor_ms;
   double merge_ms;
+  double reduce_ms;      /* the streaming per-order reduction of the FP32 path */
 } thoi_stats;
 
 /* Fill `opt` with the defaults listed above. */

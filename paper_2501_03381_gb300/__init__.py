@@ -55,7 +55,8 @@ class thoi_stats(ctypes.Structure):
     _fields_ = [("nplets", ctypes.c_uint64), ("n_refactored", ctypes.c_uint64),
                 ("n_not_pd", ctypes.c_uint64), ("launches", ctypes.c_int32),
                 ("pad", ctypes.c_int32), ("nplet_ms", ctypes.c_double),
-                ("refactor_ms", ctypes.c_double), ("merge_ms", ctypes.c_double)]
+                ("refactor_ms", ctypes.c_double), ("merge_ms", ctypes.c_double),
+                ("reduce_ms", ctypes.c_double)]
 
 
 RECORD_DTYPE = np.dtype([("k", "<i4"), ("top_count", "<i4"), ("count", "<u8"),

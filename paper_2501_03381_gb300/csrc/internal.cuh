@@ -118,6 +118,12 @@ cudaError_t launch_normalise(const double* sig64, const double* sig32acc, int N,
                              cudaStream_t s);
 cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                              int* grid_out, int max_blocks);
+// Per-block reduction of n basis triples stored at basis[m * stride_elems + e]
+// (element e has global id id0 + e); writes `grid` partials.
+cudaError_t launch_reduce_basis(const float* basis, unsigned long long stride_elems,
+                                unsigned long long n, unsigned long long id0, Combine cmb,
+                                int top_m, PartRec* part, TopEnt* part_top, int num_sms,
+                                int max_blocks, cudaStream_t s, int* grid_out);
 cudaError_t launch_nplet_f64(const NpletArgs& a, int num_sms, cudaStream_t s, int* grid_out,
                              int max_blocks);
 cudaError_t launch_refactor(const NpletArgs& a, int num_sms, cudaStream_t s, int* grid_out,

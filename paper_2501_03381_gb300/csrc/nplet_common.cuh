@@ -386,6 +386,18 @@ __device__ __forceinline__ void flag_append(const NpletArgs& a, bool flag, unsig
   }
 }
 
+// Basis store (mode 2): log det R_S, sum_j log p_j and sum_i log Sigma_ii of
+// one nplet at out[m * out_n + (gid - out_first)], m = 0, 1, 2, FP32.  A
+// flagged nplet (re-factored in FP64 later) stores NaN as its log det.
+__device__ __forceinline__ void store_basis(const NpletArgs& a, unsigned long long gid, float lr,
+                                            float sp, float lsum, bool flagged) {
+  const unsigned long long o = gid - a.out_first;
+  float* O = reinterpret_cast<float*>(a.out);
+  O[o] = flagged ? __int_as_float(0x7fc00000) : lr;
+  O[a.out_n + o] = sp;
+  O[2 * a.out_n + o] = lsum;
+}
+
 // Per-nplet SoA store.
 template <typename V>
 __device__ __forceinline__ void store5(const NpletArgs& a, unsigned long long gid, const V (&v)[5]) {

@@ -141,7 +141,9 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_gen(const NpletArgs a) {
         for (int m = 0; m < 5; m++) v[m] = pinf<V>() - pinf<V>();  // NaN
       }
       const I loc = LIST ? (I)gid : (I)(r - a.rank_begin);
-      if (!red) {
+      if (FP32_PATH && a.mode == 2) {
+        store_basis(a, gid, (float)lr, (float)sp, (float)lsum, bad);
+      } else if (!red) {
         store5<V>(a, gid, v);
       } else if (!bad) {
         tr.add(v, loc, lr, sp, lsum);

@@ -112,27 +112,13 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_grp(const NpletArgs a, const i
   constexpr int R = (K + G - 1) / G;
   constexpr int GPB = RED_NT / G;  // groups per block
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ RedScratch sc;
-  __shared__ int s_tcnt[2];
-  __shared__ int s_stop;
   const int N = a.N, ldr = row_stride(N);
-  const bool red = a.mode == 1;
-  const bool with_top = red && a.top_m > 0;
-  const SmemLayout L = smem_layout(N, K, ldr, sizeof(float), sizeof(unsigned), with_top);
-  if (threadIdx.x == 0) { s_tcnt[0] = s_tcnt[1] = 0; s_stop = 0; }
+  const SmemLayout L = smem_layout(N, K, ldr, sizeof(float), sizeof(unsigned), 0);
   load_tables<float>(a, smem, L, a.R32);
   const unsigned long long* sb = reinterpret_cast<const unsigned long long*>(smem + L.binom);
   const float* sR = reinterpret_cast<const float*>(smem + L.R);
   const float* sls = reinterpret_cast<const float*>(smem + L.ls);
-  TopBuf<float, unsigned> tb;
-  tb.val[0] = reinterpret_cast<float*>(smem + L.tv0);
-  tb.val[1] = reinterpret_cast<float*>(smem + L.tv1);
-  tb.idx[0] = reinterpret_cast<unsigned*>(smem + L.ti0);
-  tb.idx[1] = reinterpret_cast<unsigned*>(smem + L.ti1);
-  tb.cnt = s_tcnt;
-  float thr_hi = -pinf<float>(), thr_lo = pinf<float>();
-  ThreadRed<float, unsigned> tr;
-  tr.init();
+  const bool basis = a.mode == 2;
   const int lane = threadIdx.x & 31;
   const int g = lane % G;
   const int gbase = lane - g;
@@ -142,98 +128,70 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_grp(const NpletArgs a, const i
   const unsigned long long n = a.rank_end - a.rank_begin;
   const unsigned long long nch = (n + chunk - 1) / chunk;
   const unsigned long long stride = (unsigned long long)gridDim.x * GPB;
-  const unsigned long long rounds = (nch + stride - 1) / stride;
-  const int trigger = TOP_CAP - GPB * chunk;
   const float tau_piv = a.tau_piv, tau_tr = a.tau_tr;
 
-  for (unsigned long long rd = 0; rd < rounds; rd++) {
-    const unsigned long long ch = rd * stride + (unsigned long long)blockIdx.x * GPB + threadIdx.x / G;
-    if (ch < nch) {
-      const unsigned long long r0 = a.rank_begin + ch * chunk;
-      const unsigned long long left = a.rank_end - r0;
-      const int cnt = left < (unsigned long long)chunk ? (int)left : chunk;
-      M mask = unrank_s<M>(r0, K, N, sb, K + 1);
-      for (int jn = 0; jn < cnt; jn++) {
-        // indices of the nplet; row offsets of the lane's own rows
-        int c[K];
-        int ro[R];
-        {
-          M m = mask;
+  for (unsigned long long ch = (unsigned long long)blockIdx.x * GPB + threadIdx.x / G; ch < nch;
+       ch += stride) {
+    // the cancel flag lives in host memory: the leader reads it once every
+    // 64 rounds and the whole group follows its answer
+    if (((ch / stride) & 63) == 0 && a.cancel) {
+      int stop = leader ? *(volatile const int*)a.cancel : 0;
+      stop = __shfl_sync(gmask, stop, gbase);
+      if (stop) {
+        if (leader) atomicOr(a.status, ST_CANCELLED);
+        break;
+      }
+    }
+    const unsigned long long r0 = a.rank_begin + ch * chunk;
+    const unsigned long long left = a.rank_end - r0;
+    const int cnt = left < (unsigned long long)chunk ? (int)left : chunk;
+    M mask = unrank_s<M>(r0, K, N, sb, K + 1);
+    for (int jn = 0; jn < cnt; jn++) {
+      // indices of the nplet; row offsets of the lane's own rows
+      int c[K];
+      int ro[R];
+      {
+        M m = mask;
 #pragma unroll
-          for (int q = 0; q < K; q++) {
-            const int hb = hibit(m);
-            m ^= (M)1 << hb;
-            c[q] = N - 1 - hb;
-          }
-#pragma unroll
-          for (int r = 0; r < R; r++) ro[r] = 0;
-#pragma unroll
-          for (int q = 0; q < K; q++)
-            if (q % G == g) ro[q / G] = c[q] * ldr;
+        for (int q = 0; q < K; q++) {
+          const int hb = hibit(m);
+          m ^= (M)1 << hb;
+          c[q] = N - 1 - hb;
         }
-        float A[R][K];
-        float lsum = 0.f;
 #pragma unroll
-        for (int q = 0; q < K; q++) lsum += sls[c[q]];
+        for (int r = 0; r < R; r++) ro[r] = 0;
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-          const int i = r * G + g;
+        for (int q = 0; q < K; q++)
+          if (q % G == g) ro[q / G] = c[q] * ldr;
+      }
+      float A[R][K];
+      float lsum = 0.f;
 #pragma unroll
-          for (int j = 0; j < K && j <= r * G + G - 1; j++)
-            A[r][j] = (j <= i && i < K) ? sR[ro[r] + c[j]] : 0.f;
-        }
-        float lr, sp, pmin, trace;
-        bool bad = false;
-        chol_loo_grp<K, G>(A, g, gbase, gmask, lr, sp, pmin, trace, bad);
-        bad |= !(pmin >= tau_piv) | !(trace <= tau_tr);
-        if (leader) {
+      for (int q = 0; q < K; q++) lsum += sls[c[q]];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const int i = r * G + g;
+#pragma unroll
+        for (int j = 0; j < K && j <= r * G + G - 1; j++)
+          A[r][j] = (j <= i && i < K) ? sR[ro[r] + c[j]] : 0.f;
+      }
+      float lr, sp, pmin, trace;
+      bool bad = false;
+      chol_loo_grp<K, G>(A, g, gbase, gmask, lr, sp, pmin, trace, bad);
+      bad |= !(pmin >= tau_piv) | !(trace <= tau_tr);
+      if (leader) {
+        const unsigned long long gid = a.id_base + r0 + jn;
+        if (basis) {
+          store_basis(a, gid, lr, sp, lsum, bad);
+        } else {
           float v[5];
           combine5<float>(lr, sp, lsum, a.cmb, v);
-          const unsigned long long r = r0 + jn;
-          const unsigned long long gid = a.id_base + r;
-          if (!red) {
-            store5<float>(a, gid, v);
-          } else if (!bad) {
-            const unsigned loc = (unsigned)(r - a.rank_begin);
-            tr.add(v, loc, lr, sp, lsum);
-            if (with_top) top_offer(tb, v[3], loc, thr_hi, thr_lo);
-          }
-          flag_append(a, bad, gid);
+          store5<float>(a, gid, v);
         }
-        if (jn + 1 < cnt) mask = lex_succ(mask, full);
+        flag_append(a, bad, gid);
       }
-      tr.flush();
+      if (jn + 1 < cnt) mask = lex_succ(mask, full);
     }
-    if (threadIdx.x == 0 && a.cancel && *(volatile const int*)a.cancel) s_stop = 1;
-    __syncthreads();
-    if (with_top) {
-      const bool c0 = tb.cnt[0] > trigger, c1 = tb.cnt[1] > trigger;
-      if (c0) {
-        top_sort_cut(tb, 0, a.top_m);
-        thr_hi = top_threshold(tb, 0, a.top_m);
-      }
-      if (c1) {
-        top_sort_cut(tb, 1, a.top_m);
-        thr_lo = top_threshold(tb, 1, a.top_m);
-      }
-      __syncthreads();
-    }
-    if (s_stop) {
-      if (threadIdx.x == 0) atomicOr(a.status, ST_CANCELLED);
-      break;
-    }
-  }
-  if (red) {
-    int th = 0, tl = 0;
-    const unsigned long long id_off = a.id_base + a.rank_begin;
-    if (with_top) {
-      top_sort_cut(tb, 0, a.top_m);
-      top_sort_cut(tb, 1, a.top_m);
-      th = tb.cnt[0];
-      tl = tb.cnt[1];
-      top_write(tb, a.top_m, id_off, a.part_top + (size_t)blockIdx.x * 2 * a.top_m);
-    }
-    block_write_part<float, unsigned>(tr, 0u, id_off, sc, a.part + blockIdx.x, th, tl);
   }
 }
 
@@ -241,9 +199,7 @@ template <int K, int G, typename M>
 static cudaError_t launch_grp_t(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                                 int* grid_out, int max_blocks) {
   constexpr int GPB = RED_NT / G;
-  const bool red = a.mode == 1;
-  const SmemLayout L = smem_layout(a.N, K, row_stride(a.N), sizeof(float), sizeof(unsigned),
-                                   red && a.top_m > 0);
+  const SmemLayout L = smem_layout(a.N, K, row_stride(a.N), sizeof(float), sizeof(unsigned), 0);
   void (*fn)(const NpletArgs, const int) = k_nplet_grp<K, G, M>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
   if (e != cudaSuccess) return e;

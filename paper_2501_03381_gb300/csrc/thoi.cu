@@ -70,7 +70,9 @@ struct thoi_ctx {
   size_t rec_cap = 0;
   double* gpart = nullptr;    // gradient partials
   size_t gpart_cap = 0;       // doubles
-  // profiling: event pairs around launches, by class (0 nplet, 1 refactor, 2 merge)
+  float* basis = nullptr;     // FP32 path: three basis values per nplet of one piece
+  size_t basis_cap = 0;       // floats
+  // profiling: event pairs around launches, by class (0 nplet, 1 refactor, 2 merge, 3 reduce)
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;
   int ev_used = 0;
@@ -333,6 +335,7 @@ extern "C" void thoi_destroy(thoi_ctx* c) {
   free_ptr(c->top64);
   free_ptr(c->rec_buf);
   free_ptr(c->gpart);
+  free_ptr(c->basis);
   delete c;
 }
 
@@ -507,6 +510,14 @@ constexpr int MAX_BLOCKS_PER_SM_RED = 4;   // cap for reduction launches (partia
 constexpr int MAX_BLOCKS_PER_SM_OUT = 8;
 constexpr int REFACTOR_BLOCKS_PER_SM = 2;
 constexpr unsigned long long LAUNCH_SPLIT = 0xffffffffull;  // ranks per launch (u32 local ids)
+constexpr unsigned long long PIECE = 1ull << 28;  // FP32 records path: nplets per basis piece
+
+// Elements between the three basis arrays: the piece length rounded up to a
+// multiple of 64, so that every array is 256-byte aligned.
+unsigned long long basis_stride(unsigned long long max_slot_nplets) {
+  const unsigned long long piece = max_slot_nplets < PIECE ? max_slot_nplets : PIECE;
+  return ((piece > 0 ? piece : 1) + 63) / 64 * 64;
+}
 
 }  // namespace
 
@@ -577,7 +588,7 @@ static thoi_status finish_status(thoi_ctx* c, cudaStream_t s, int n_slots, thoi_
   CK(cudaStreamSynchronize(s));
   unsigned long long nref = 0;
   for (int i = 0; i < n_slots; i++) nref += fc[i] < c->flag_cap ? fc[i] : c->flag_cap;
-  double ms[3] = {0, 0, 0};
+  double ms[4] = {0, 0, 0, 0};
   for (int i = 0; i < c->ev_used; i++) {
     float t = 0.f;
     CK(cudaEventElapsedTime(&t, c->ev[2 * i], c->ev[2 * i + 1]));
@@ -593,6 +604,7 @@ static thoi_status finish_status(thoi_ctx* c, cudaStream_t s, int n_slots, thoi_
     stats->nplet_ms = ms[0];
     stats->refactor_ms = ms[1];
     stats->merge_ms = ms[2];
+    stats->reduce_ms = ms[3];
   }
   if (hs & ST_FLAG_OVERFLOW) return THOI_ERR_WORKSPACE;
   if (hs & ST_CANCELLED) return THOI_ERR_CANCELLED;
@@ -625,10 +637,15 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
   const int ref_cap = c->num_sms * REFACTOR_BLOCKS_PER_SM;
   if (red) {
     size_t n32 = 0;
+    const unsigned long long split = f64 ? LAUNCH_SPLIT : PIECE;
     for (auto& r : slots) {
       const unsigned long long n = r.r1 - r.r0;
-      const size_t parts = n == 0 ? 0 : (size_t)((n + LAUNCH_SPLIT - 1) / LAUNCH_SPLIT);
+      const size_t parts = n == 0 ? 0 : (size_t)((n + split - 1) / split);
       n32 += parts * blk_cap;
+    }
+    if (!f64) {
+      st = grow(&c->basis, &c->basis_cap, (size_t)3 * basis_stride(maxn));
+      if (st != THOI_OK) return st;
     }
     const size_t n64 = f64 ? 0 : slots.size() * (size_t)ref_cap;
     if (c->part_top_m != top_m) {
@@ -669,7 +686,41 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
     md.p64_off = p64_off;
     md.refactored = f64 ? nullptr : c->flag_counts + si;
     const Shape sh = shape_for(c, r.k);
-    for (unsigned long long a0 = r.r0; a0 < r.r1; a0 += LAUNCH_SPLIT) {
+    if (red && !f64) {
+      // FP32 records: basis values per piece, then the streaming reduction
+      // each of the three arrays starts on a 256-byte boundary (16-byte loads)
+      const unsigned long long bstride = basis_stride(maxn);
+      for (unsigned long long a0 = r.r0; a0 < r.r1; a0 += PIECE) {
+        SlotRange sub = r;
+        sub.r0 = a0;
+        sub.r1 = r.r1 - a0 > PIECE ? a0 + PIECE : r.r1;
+        NpletArgs a = base_args(c, sub);
+        a.flag_count = c->flag_counts + si;
+        a.mode = 2;
+        a.out = c->basis;
+        a.out_f64 = 0;
+        a.out_n = bstride;
+        a.out_first = r.off + sub.r0;
+        int grid = 0;
+        st = prof_begin(c, s, 0);
+        if (st != THOI_OK) return st;
+        CK(launch_nplet_f32(a, sh, c->num_sms, s, &grid, c->num_sms * MAX_BLOCKS_PER_SM_OUT));
+        st = prof_end(c, s);
+        if (st != THOI_OK) return st;
+        st = prof_begin(c, s, 3);
+        if (st != THOI_OK) return st;
+        CK(launch_reduce_basis(c->basis, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb, top_m,
+                               c->part32 + p32_off,
+                               top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
+                               c->num_sms, blk_cap, s, &grid));
+        st = prof_end(c, s);
+        if (st != THOI_OK) return st;
+        launches += 2;
+        p32_off += grid;
+        md.g32 += grid;
+      }
+    }
+    for (unsigned long long a0 = r.r0; a0 < r.r1 && !(red && !f64); a0 += LAUNCH_SPLIT) {
       SlotRange sub = r;
       sub.r0 = a0;
       sub.r1 = r.r1 - a0 > LAUNCH_SPLIT ? a0 + LAUNCH_SPLIT : r.r1;
