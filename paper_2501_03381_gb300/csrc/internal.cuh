@@ -81,6 +81,10 @@ struct NpletArgs {
 };
 
 // ------------------------------------------------------------------ launchers
+// Maximum resident blocks per SM of a kernel at a dynamic shared-memory size,
+// with the shared-memory attribute set; cached per (kernel, size) so that
+// repeated launches do not pay for the occupancy query.
+cudaError_t occupancy_cached(const void* fn, int block, size_t smem, int* occ);
 struct Shape {
   int blocks_per_sm;  // 0 = occupancy maximum
   int chunk;          // nplets per thread (or lane group) per round, 1..8
@@ -120,10 +124,25 @@ cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, c
                              int* grid_out, int max_blocks);
 // Per-block reduction of n basis triples stored at basis[m * stride_elems + e]
 // (element e has global id id0 + e); writes `grid` partials.
+// seed_thr: device scratch for 2 floats (starting top-M thresholds), or null.
 cudaError_t launch_reduce_basis(const float* basis, unsigned long long stride_elems,
                                 unsigned long long n, unsigned long long id0, Combine cmb,
-                                int top_m, PartRec* part, TopEnt* part_top, int num_sms,
-                                int max_blocks, cudaStream_t s, int* grid_out);
+                                int top_m, float* seed_thr, PartRec* part, TopEnt* part_top,
+                                int num_sms, int max_blocks, cudaStream_t s, int* grid_out);
+cudaError_t launch_reduce_basis64(const double* basis, unsigned long long stride_elems,
+                                  unsigned long long n, unsigned long long id0, Combine cmb,
+                                  int top_m, PartRec* part, TopEnt* part_top, int num_sms,
+                                  int max_blocks, cudaStream_t s, int* grid_out);
+cudaError_t launch_reduce_list64(const double* basis, unsigned long long stride_elems,
+                                 const unsigned long long* ids, const unsigned long long* count,
+                                 unsigned long long cap, Combine cmb, int top_m, PartRec* part,
+                                 TopEnt* part_top, int num_sms, int max_blocks, cudaStream_t s,
+                                 int* grid_out);
+// FP64 kernel with shared-memory matrices; threads per block that fit (0: none)
+int f64s_threads(int N, int k, size_t* smem_out);
+cudaError_t launch_nplet_f64s(const NpletArgs& a, bool list, double* b64,
+                              unsigned long long bstride, int num_sms, cudaStream_t s,
+                              int* grid_out, int max_blocks);
 cudaError_t launch_nplet_f64(const NpletArgs& a, int num_sms, cudaStream_t s, int* grid_out,
                              int max_blocks);
 cudaError_t launch_refactor(const NpletArgs& a, int num_sms, cudaStream_t s, int* grid_out,

@@ -83,11 +83,29 @@ __device__ __forceinline__ double log_of(double P, int E) { return log(P) + (dou
 // The five measures from the three per-nplet quantities (Methods eqs. TC,
 // DTC, O-info, S-info with H from Supp. eq. gaussian_differential_entropy):
 // Lr = log det R_S, Sp = sum_j log (R_S^-1)_jj, Ls = sum_{i in S} log Sigma_ii.
+// Unsigned key with the numeric order of a double (zeros of both signs map to
+// one key).  Double compares run on the narrow FP64 pipe of this GPU; the
+// reductions and sorts order doubles through these integer keys instead.
+__device__ __forceinline__ unsigned long long okey(double v) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  if ((u << 1) == 0) u = 0;
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// The combine constants in the working precision, converted once per kernel
+// (a double-to-float conversion runs on the FP64 pipe).
 template <typename V>
-__device__ __forceinline__ void combine5(V lr, V sp, V lsum, const Combine& c, V (&v)[5]) {
-  const V tc = (V)(-0.5) * lr + (V)c.tc_c;
-  const V dtc = (V)0.5 * (lr + sp) + (V)c.dtc_c;
-  v[0] = (V)c.h_c + (V)0.5 * (lr + lsum);
+struct CombineV {
+  V h_c, tc_c, dtc_c;
+  __device__ __forceinline__ explicit CombineV(const Combine& c)
+      : h_c((V)c.h_c), tc_c((V)c.tc_c), dtc_c((V)c.dtc_c) {}
+};
+
+template <typename V>
+__device__ __forceinline__ void combine5(V lr, V sp, V lsum, const CombineV<V>& c, V (&v)[5]) {
+  const V tc = (V)(-0.5) * lr + c.tc_c;
+  const V dtc = (V)0.5 * (lr + sp) + c.dtc_c;
+  v[0] = c.h_c + (V)0.5 * (lr + lsum);
   v[1] = tc;
   v[2] = dtc;
   v[3] = tc - dtc;
@@ -101,8 +119,12 @@ template <typename V, typename I>
 struct ThreadRed {
   V mn[5], mx[5];
   I imn[5], imx[5];
-  double slr, ssp, sls;  // running sums
-  V plr, psp, pls;       // partial sums of the current chunk (added by flush())
+  // Running sums in the working precision; in FP32 with Kahan compensation
+  // (c*), so that no double arithmetic runs per element: on this GPU the FP64
+  // pipe is narrow enough that even one double add per few elements bounds a
+  // streaming kernel.
+  V plr, psp, pls;
+  V clr, csp, cls;
   unsigned cnt, neg;
 
   __device__ __forceinline__ void init() {
@@ -113,25 +135,71 @@ struct ThreadRed {
       imn[m] = imax_val<I>();
       imx[m] = imax_val<I>();
     }
-    slr = ssp = sls = 0.0;
     plr = psp = pls = (V)0;
+    clr = csp = cls = (V)0;
     cnt = neg = 0;
   }
-  __device__ __forceinline__ void flush() {
-    slr += (double)plr;
-    ssp += (double)psp;
-    sls += (double)pls;
-    plr = psp = pls = (V)0;
+  // (kept for the call sites; the compensated sums need no periodic flush)
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ static void kahan(V& s, V& c, V x) {
+    if (sizeof(V) == 4) {
+      const V y = x - c;
+      const V t = s + y;
+      c = (t - s) - y;
+      s = t;
+    } else {
+      s += x;
+    }
   }
+  __device__ __forceinline__ double total_lr() const { return (double)plr - (double)clr; }
+  __device__ __forceinline__ double total_sp() const { return (double)psp - (double)csp; }
+  __device__ __forceinline__ double total_ls() const { return (double)pls - (double)cls; }
+  // ids in any order: ties go to the smaller id (branch-free selects; doubles
+  // are compared through their integer keys)
   __device__ __forceinline__ void add(const V (&v)[5], I id, V lr, V sp, V lsum) {
+    if (sizeof(V) == 8) {
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        const unsigned long long kv = okey((double)v[m]), kn = okey((double)mn[m]),
+                                 kx = okey((double)mx[m]);
+        const bool lt = (kv < kn) | ((kv == kn) & (id < imn[m]));
+        const bool gt = (kv > kx) | ((kv == kx) & (id < imx[m]));
+        mn[m] = lt ? v[m] : mn[m];
+        imn[m] = lt ? id : imn[m];
+        mx[m] = gt ? v[m] : mx[m];
+        imx[m] = gt ? id : imx[m];
+      }
+      accumulate(v, lr, sp, lsum);
+      return;
+    }
 #pragma unroll
     for (int m = 0; m < 5; m++) {
-      if (v[m] < mn[m] || (v[m] == mn[m] && id < imn[m])) { mn[m] = v[m]; imn[m] = id; }
-      if (v[m] > mx[m] || (v[m] == mx[m] && id < imx[m])) { mx[m] = v[m]; imx[m] = id; }
+      const bool lt = (v[m] < mn[m]) | ((v[m] == mn[m]) & (id < imn[m]));
+      const bool gt = (v[m] > mx[m]) | ((v[m] == mx[m]) & (id < imx[m]));
+      mn[m] = lt ? v[m] : mn[m];
+      imn[m] = lt ? id : imn[m];
+      mx[m] = gt ? v[m] : mx[m];
+      imx[m] = gt ? id : imx[m];
     }
-    plr += lr;
-    psp += sp;
-    pls += lsum;
+    accumulate(v, lr, sp, lsum);
+  }
+  // ids strictly increasing in this thread: a later equal value never wins
+  __device__ __forceinline__ void add_mono(const V (&v)[5], I id, V lr, V sp, V lsum) {
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+      const bool lt = v[m] < mn[m];
+      const bool gt = v[m] > mx[m];
+      mn[m] = lt ? v[m] : mn[m];
+      imn[m] = lt ? id : imn[m];
+      mx[m] = gt ? v[m] : mx[m];
+      imx[m] = gt ? id : imx[m];
+    }
+    accumulate(v, lr, sp, lsum);
+  }
+  __device__ __forceinline__ void accumulate(const V (&v)[5], V lr, V sp, V lsum) {
+    kahan(plr, clr, lr);
+    kahan(psp, csp, sp);
+    kahan(pls, cls, lsum);
     cnt++;
     neg += (v[3] < (V)0) ? 1u : 0u;
   }
@@ -144,6 +212,16 @@ __device__ __forceinline__ void pick_min(V& v, I& i, V ov, I oi) {
 template <typename V, typename I>
 __device__ __forceinline__ void pick_max(V& v, I& i, V ov, I oi) {
   if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+}
+template <typename I>
+__device__ __forceinline__ void pick_min(double& v, I& i, double ov, I oi) {
+  const unsigned long long k = okey(v), ko = okey(ov);
+  if (ko < k || (ko == k && oi < i)) { v = ov; i = oi; }
+}
+template <typename I>
+__device__ __forceinline__ void pick_max(double& v, I& i, double ov, I oi) {
+  const unsigned long long k = okey(v), ko = okey(ov);
+  if (ko > k || (ko == k && oi < i)) { v = ov; i = oi; }
 }
 
 struct RedScratch {
@@ -169,7 +247,7 @@ __device__ void block_write_part(ThreadRed<V, I>& t, unsigned notpd, unsigned lo
     gmn[m] = (t.imn[m] == imax_val<I>()) ? ~0ull : (unsigned long long)t.imn[m] + id_off;
     gmx[m] = (t.imx[m] == imax_val<I>()) ? ~0ull : (unsigned long long)t.imx[m] + id_off;
   }
-  double slr = t.slr, ssp = t.ssp, sls = t.sls;
+  double slr = t.total_lr(), ssp = t.total_sp(), sls = t.total_ls();
   unsigned long long cnt = t.cnt, neg = t.neg, npd = notpd;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -250,6 +328,12 @@ struct TopBuf {
 template <typename V, typename I>
 __device__ __forceinline__ bool top_before(int side, V va, I ia, V vb, I ib) {
   if (va != vb) return side == 0 ? (va > vb) : (va < vb);
+  return ia < ib;
+}
+template <typename I>
+__device__ __forceinline__ bool top_before(int side, double va, I ia, double vb, I ib) {
+  const unsigned long long ka = okey(va), kb = okey(vb);
+  if (ka != kb) return side == 0 ? (ka > kb) : (ka < kb);
   return ia < ib;
 }
 

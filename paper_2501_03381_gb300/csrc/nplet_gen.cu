@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_gen(const NpletArgs a) {
   const unsigned long long rounds = (n + stride - 1) / stride;
   const int trigger = TOP_CAP - RED_NT;
   const unsigned long long id_off = LIST ? 0ull : a.id_base + a.rank_begin;
+  const CombineV<V> cmbv(a.cmb);
 
   for (unsigned long long rd = 0; rd < rounds; rd++) {
     const unsigned long long e = rd * stride + (unsigned long long)blockIdx.x * RED_NT + threadIdx.x;
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_gen(const NpletArgs a) {
       gather_gen<V, M>(mask, k, N, sR, ldr, sls, A, lsum);
       chol_loo_gen<V>(A, k, lr, sp, pmin, trace, bad);
       V v[5];
-      combine5<V>(lr, sp, lsum, a.cmb, v);
+      combine5<V>(lr, sp, lsum, cmbv, v);
       if (FP32_PATH) {
         bad |= !(pmin >= (V)a.tau_piv) | !(trace <= (V)a.tau_tr);
       } else if (bad) {
@@ -193,9 +194,31 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_gen(const NpletArgs a) {
 constexpr int MERGE_NT = 128;
 constexpr int MERGE_SURV_CAP = 4096;  // survivors sorted in shared memory
 
+// Unsigned key with the numeric order of a double (sign-magnitude to offset
+// binary), so the merge orders entries with integer compares: on this GPU a
+// double compare runs on the narrow FP64 pipe.
+__device__ __forceinline__ unsigned long long dkey(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
 __device__ __forceinline__ bool ent_before(int side, const TopEnt& a, const TopEnt& b) {
-  if (a.v != b.v) return side == 0 ? (a.v > b.v) : (a.v < b.v);
+  const unsigned long long ka = dkey(a.v), kb = dkey(b.v);
+  if (ka != kb) return side == 0 ? (ka > kb) : (ka < kb);
   return a.id < b.id;
+}
+__device__ __forceinline__ bool ent_same(const TopEnt& a, const TopEnt& b) {
+  return dkey(a.v) == dkey(b.v) && a.id == b.id;
+}
+__device__ __forceinline__ void kpick_min(double& v, unsigned long long& i, double ov,
+                                          unsigned long long oi) {
+  const unsigned long long k = dkey(v), ko = dkey(ov);
+  if (ko < k || (ko == k && oi < i)) { v = ov; i = oi; }
+}
+__device__ __forceinline__ void kpick_max(double& v, unsigned long long& i, double ov,
+                                          unsigned long long oi) {
+  const unsigned long long k = dkey(v), ko = dkey(ov);
+  if (ko > k || (ko == k && oi < i)) { v = ov; i = oi; }
 }
 
 // Merge sorted lists X (nx) and Y (ny), keep the first `keep` into Z.
@@ -257,8 +280,8 @@ __global__ void __launch_bounds__(MERGE_NT) k_merge(const MergeDescs D,
     npd += P.notpd;
     if (P.count == 0) continue;
     for (int m = 0; m < 5; m++) {
-      pick_min(vmn[m], imn[m], P.vmin[m], P.imin[m]);
-      pick_max(vmx[m], imx[m], P.vmax[m], P.imax[m]);
+      kpick_min(vmn[m], imn[m], P.vmin[m], P.imin[m]);
+      kpick_max(vmx[m], imx[m], P.vmax[m], P.imax[m]);
     }
     sum[0] += P.s_lr;
     sum[1] += P.s_sp;
@@ -283,8 +306,8 @@ __global__ void __launch_bounds__(MERGE_NT) k_merge(const MergeDescs D,
     if (threadIdx.x < h) {
       const int o = threadIdx.x + h;
       for (int m = 0; m < 5; m++) {
-        pick_min(s_vmin[threadIdx.x][m], s_imin[threadIdx.x][m], s_vmin[o][m], s_imin[o][m]);
-        pick_max(s_vmax[threadIdx.x][m], s_imax[threadIdx.x][m], s_vmax[o][m], s_imax[o][m]);
+        kpick_min(s_vmin[threadIdx.x][m], s_imin[threadIdx.x][m], s_vmin[o][m], s_imin[o][m]);
+        kpick_max(s_vmax[threadIdx.x][m], s_imax[threadIdx.x][m], s_vmax[o][m], s_imax[o][m]);
       }
       for (int q = 0; q < 3; q++) {
         s_sum[threadIdx.x][q] += s_sum[o][q];
@@ -375,7 +398,7 @@ __global__ void __launch_bounds__(MERGE_NT) k_merge(const MergeDescs D,
         while (lo < hi) {
           const int mid = (lo + hi) >> 1;
           const TopEnt e = Lst[mid];
-          const bool keep = ent_before(side, e, thr) || (e.v == thr.v && e.id == thr.id);
+          const bool keep = ent_before(side, e, thr) || ent_same(e, thr);
           if (keep) lo = mid + 1;
           else hi = mid;
         }
@@ -509,12 +532,9 @@ static cudaError_t launch_gen_t(const NpletArgs& a, int num_sms, cudaStream_t s,
   void (*fn)(const NpletArgs);
   if (wide) fn = k_nplet_gen<V, KMAX, LIST, FP32_PATH, unsigned long long>;
   else fn = k_nplet_gen<V, KMAX, LIST, FP32_PATH, unsigned>;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-  if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, RED_NT, L.total);
+  e = occupancy_cached((const void*)fn, RED_NT, L.total, &occ);
   if (e != cudaSuccess) return e;
-  if (occ < 1) occ = 1;
   long long grid = (long long)num_sms * occ;
   if (!LIST) {
     const unsigned long long n = a.rank_end - a.rank_begin;

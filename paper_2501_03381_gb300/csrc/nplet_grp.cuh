@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_grp(const NpletArgs a, const i
   const unsigned long long nch = (n + chunk - 1) / chunk;
   const unsigned long long stride = (unsigned long long)gridDim.x * GPB;
   const float tau_piv = a.tau_piv, tau_tr = a.tau_tr;
+  const CombineV<float> cmbv(a.cmb);
 
   for (unsigned long long ch = (unsigned long long)blockIdx.x * GPB + threadIdx.x / G; ch < nch;
        ch += stride) {
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_grp(const NpletArgs a, const i
           store_basis(a, gid, lr, sp, lsum, bad);
         } else {
           float v[5];
-          combine5<float>(lr, sp, lsum, a.cmb, v);
+          combine5<float>(lr, sp, lsum, cmbv, v);
           store5<float>(a, gid, v);
         }
         flag_append(a, bad, gid);
@@ -201,12 +202,9 @@ static cudaError_t launch_grp_t(const NpletArgs& a, const Shape& sh, int num_sms
   constexpr int GPB = RED_NT / G;
   const SmemLayout L = smem_layout(a.N, K, row_stride(a.N), sizeof(float), sizeof(unsigned), 0);
   void (*fn)(const NpletArgs, const int) = k_nplet_grp<K, G, M>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-  if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, RED_NT, L.total);
+  cudaError_t e = occupancy_cached((const void*)fn, RED_NT, L.total, &occ);
   if (e != cudaSuccess) return e;
-  if (occ < 1) occ = 1;
   if (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ) occ = sh.blocks_per_sm;
   int chunk = sh.chunk > 0 ? sh.chunk : 4;
   if (chunk > 8) chunk = 8;

@@ -1,72 +1,182 @@
-// Streaming per-order reduction of the FP32 path.  The nplet kernels write
-// three basis values per nplet (log det R_S, sum_j log p_j, sum_i log
-// Sigma_ii; NaN log det = re-factored in FP64); this kernel reads them
-// back (coalesced, 16-byte loads), forms the five measures and reduces them
-// per block: min/max with the smallest id on ties, sums, counts, count of
-// O < 0 and the top-M lists (Fig. 1A caption: a function applied to every
-// batch, here a fixed reduction set).  Keeping the reduction out of the
-// compute kernels frees their registers and removes their barriers.
+// Streaming per-order reduction.  The nplet kernels write three basis values
+// per nplet (log det R_S, sum_j log p_j, sum_i log Sigma_ii; a NaN log det
+// marks a nplet that is reduced elsewhere or is not positive definite); this
+// kernel reads them back, forms the five measures and reduces them per block:
+// min/max with the smallest id on ties, sums, counts, count of O < 0 and the
+// top-M lists (Fig. 1A caption: a function applied to every batch, here a
+// fixed reduction set).  Keeping the reduction out of the compute kernels
+// frees their registers and removes their barriers.
+//
+// Instances: FP32 values with dense ids (the FP32 path; NaN = re-factored in
+// FP64, skipped), FP64 values with dense ids (the FP64 path; NaN = not
+// positive definite) and FP64 values with ids from the re-factor list.
+#include <type_traits>
+
 #include "nplet_common.cuh"
 
 namespace thoi {
 
-constexpr int RB_PER_THREAD = 4;  // elements per thread per round (one float4 of each array)
+constexpr int RB_VEC = 1;                     // 16-byte groups per array per thread per round
+constexpr int RB_PER_THREAD = 4 * RB_VEC;     // elements per thread per round
+constexpr int RTOP_CAP = 2048;                // candidate buffer per side (>= M + NT * RB)
+static_assert(RTOP_CAP >= THOI_MAX_TOP_M + RED_NT * RB_PER_THREAD, "top-M buffer too small");
 
-__global__ void __launch_bounds__(RED_NT) k_reduce_basis(const float* __restrict__ blr,
-                                                         const float* __restrict__ bsp,
-                                                         const float* __restrict__ bls,
-                                                         unsigned long long n,
+// Starting thresholds of the top-M buffers: the M-th largest and M-th
+// smallest O among a sample of the elements (SEED_CHUNKS runs of SEED_RUN
+// consecutive elements spread over the range).  The M-th best of any subset
+// is no better than the M-th best of the whole set, so every element of the
+// true top-M still passes; with the thresholds starting near their final
+// values, the blocks see few candidates and rarely compact.
+constexpr int SEED_NT = 1024;
+constexpr int SEED_CHUNKS = 128;
+constexpr int SEED_RUN = 256;
+constexpr int SEED_S = SEED_CHUNKS * SEED_RUN;  // 32768 sampled elements
+
+__global__ void __launch_bounds__(SEED_NT) k_seed_thresholds(const float* __restrict__ blr,
+                                                             const float* __restrict__ bsp,
+                                                             unsigned long long n, Combine cmb,
+                                                             int top_m, float* __restrict__ thr) {
+  extern __shared__ __align__(16) float sv[];  // SEED_S values
+  __shared__ int s_valid;
+  const CombineV<float> c(cmb);
+  if (threadIdx.x == 0) s_valid = 0;
+  __syncthreads();
+  const unsigned long long S = n < (unsigned long long)SEED_S ? n : (unsigned long long)SEED_S;
+  int valid = 0;
+  for (int q = threadIdx.x; q < SEED_S; q += SEED_NT) {
+    float o = pinf<float>();
+    if ((unsigned long long)q < S) {
+      unsigned long long e;
+      if (n <= (unsigned long long)SEED_S) {
+        e = q;
+      } else {
+        const int ch = q / SEED_RUN, off = q % SEED_RUN;
+        e = (unsigned long long)ch * (n - SEED_RUN) / (SEED_CHUNKS - 1) + off;
+      }
+      const float lr = blr[e];
+      if (!isnan(lr)) {
+        const float sp = bsp[e];
+        const float tc = -0.5f * lr + c.tc_c, dtc = 0.5f * (lr + sp) + c.dtc_c;
+        o = tc - dtc;
+        valid++;
+      }
+    }
+    sv[q] = o;  // invalid -> +inf, sorted to the end
+  }
+  atomicAdd(&s_valid, valid);
+  __syncthreads();
+  for (int kk = 2; kk <= SEED_S; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < SEED_S; i += SEED_NT) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & kk) == 0;
+          const float x = sv[i], y = sv[ixj];
+          if (up ? (y < x) : (x < y)) { sv[i] = y; sv[ixj] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    // widened by a relative 1e-6 so that a rounding difference between this
+    // kernel's O and the reduction's O can never reject a top-M element
+    const int V = s_valid;
+    const float hi = sv[V >= top_m ? V - top_m : 0], lo = sv[top_m - 1 < SEED_S ? top_m - 1 : 0];
+    thr[0] = V >= top_m ? hi - 1e-6f * fabsf(hi) - 1e-30f : -pinf<float>();  // M-th largest
+    thr[1] = V >= top_m ? lo + 1e-6f * fabsf(lo) + 1e-30f : pinf<float>();   // M-th smallest
+  }
+}
+
+template <typename V, bool LIST>
+__global__ void __launch_bounds__(RED_NT, 6) k_reduce_basis(const V* __restrict__ blr,
+                                                         const V* __restrict__ bsp,
+                                                         const V* __restrict__ bls,
+                                                         unsigned long long n_dense,
+                                                         const unsigned long long* __restrict__ ids,
+                                                         const unsigned long long* list_count,
+                                                         unsigned long long list_cap,
                                                          unsigned long long id0, Combine cmb,
-                                                         int top_m, PartRec* __restrict__ part,
+                                                         int top_m, int nan_is_notpd,
+                                                         const float* __restrict__ seed_thr,
+                                                         PartRec* __restrict__ part,
                                                          TopEnt* __restrict__ part_top) {
+  using I = typename std::conditional<LIST, unsigned long long, unsigned>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ RedScratch sc;
   __shared__ int s_tcnt[2];
   const bool with_top = top_m > 0;
-  TopBuf<float, unsigned> tb;
-  tb.val[0] = reinterpret_cast<float*>(smem);
-  tb.val[1] = tb.val[0] + TOP_CAP;
-  tb.idx[0] = reinterpret_cast<unsigned*>(tb.val[1] + TOP_CAP);
-  tb.idx[1] = tb.idx[0] + TOP_CAP;
+  TopBuf<V, I> tb;
+  tb.val[0] = reinterpret_cast<V*>(smem);
+  tb.val[1] = tb.val[0] + RTOP_CAP;
+  tb.idx[0] = reinterpret_cast<I*>(tb.val[1] + RTOP_CAP);
+  tb.idx[1] = tb.idx[0] + RTOP_CAP;
   tb.cnt = s_tcnt;
   if (threadIdx.x == 0) s_tcnt[0] = s_tcnt[1] = 0;
   __syncthreads();
-  float thr_hi = -pinf<float>(), thr_lo = pinf<float>();
-  ThreadRed<float, unsigned> tr;
+  V thr_hi = -pinf<V>(), thr_lo = pinf<V>();
+  if (seed_thr) {
+    thr_hi = (V)seed_thr[0];
+    thr_lo = (V)seed_thr[1];
+  }
+  ThreadRed<V, I> tr;
   tr.init();
+  unsigned notpd = 0;
+  unsigned long long n = n_dense;
+  if (LIST) {
+    const unsigned long long c = *list_count;
+    n = c < list_cap ? c : list_cap;
+  }
   const unsigned long long nq = (n + RB_PER_THREAD - 1) / RB_PER_THREAD;
   const unsigned long long stride = (unsigned long long)gridDim.x * RED_NT;
   const unsigned long long rounds = (nq + stride - 1) / stride;
-  const int trigger = TOP_CAP - RED_NT * RB_PER_THREAD;
+  const int trigger = RTOP_CAP - RED_NT * RB_PER_THREAD;
+  const CombineV<V> cmbv(cmb);
+  // one round = RB_PER_THREAD elements per thread, loaded as RB_VEC groups of
+  // four (all loads of a round are issued together)
   for (unsigned long long rd = 0; rd < rounds; rd++) {
     const unsigned long long q = rd * stride + (unsigned long long)blockIdx.x * RED_NT + threadIdx.x;
     if (q < nq) {
       const unsigned long long e0 = q * RB_PER_THREAD;
-      float lr[4], sp[4], ls[4];
-      if (e0 + 4 <= n) {
-        const float4 x = reinterpret_cast<const float4*>(blr)[q];
-        const float4 y = reinterpret_cast<const float4*>(bsp)[q];
-        const float4 z = reinterpret_cast<const float4*>(bls)[q];
-        lr[0] = x.x; lr[1] = x.y; lr[2] = x.z; lr[3] = x.w;
-        sp[0] = y.x; sp[1] = y.y; sp[2] = y.z; sp[3] = y.w;
-        ls[0] = z.x; ls[1] = z.y; ls[2] = z.z; ls[3] = z.w;
+      V lr[RB_PER_THREAD], sp[RB_PER_THREAD], ls[RB_PER_THREAD];
+      if (sizeof(V) == 4 && e0 + RB_PER_THREAD <= n) {
+#pragma unroll
+        for (int g = 0; g < RB_VEC; g++) {
+          const float4 fx = reinterpret_cast<const float4*>(blr)[q * RB_VEC + g];
+          const float4 fy = reinterpret_cast<const float4*>(bsp)[q * RB_VEC + g];
+          const float4 fz = reinterpret_cast<const float4*>(bls)[q * RB_VEC + g];
+          lr[4 * g] = fx.x; lr[4 * g + 1] = fx.y; lr[4 * g + 2] = fx.z; lr[4 * g + 3] = fx.w;
+          sp[4 * g] = fy.x; sp[4 * g + 1] = fy.y; sp[4 * g + 2] = fy.z; sp[4 * g + 3] = fy.w;
+          ls[4 * g] = fz.x; ls[4 * g + 1] = fz.y; ls[4 * g + 2] = fz.z; ls[4 * g + 3] = fz.w;
+        }
       } else {
 #pragma unroll
-        for (int t = 0; t < 4; t++) {
+        for (int t = 0; t < RB_PER_THREAD; t++) {
           const bool ok = e0 + t < n;
-          lr[t] = ok ? blr[e0 + t] : __int_as_float(0x7fc00000);
-          sp[t] = ok ? bsp[e0 + t] : 0.f;
-          ls[t] = ok ? bls[e0 + t] : 0.f;
+          lr[t] = ok ? blr[e0 + t] : pinf<V>() - pinf<V>();
+          sp[t] = ok ? bsp[e0 + t] : (V)0;
+          ls[t] = ok ? bls[e0 + t] : (V)0;
         }
       }
 #pragma unroll
-      for (int t = 0; t < 4; t++) {
-        if (isnan(lr[t])) continue;  // re-factored in FP64, or past the end
-        float v[5];
-        combine5<float>(lr[t], sp[t], ls[t], cmb, v);
-        const unsigned loc = (unsigned)(e0 + t);
-        tr.add(v, loc, lr[t], sp[t], ls[t]);
-        if (with_top) top_offer(tb, v[3], loc, thr_hi, thr_lo);
+      for (int t = 0; t < RB_PER_THREAD; t++) {
+        if (e0 + t >= n) continue;
+        if (isnan(lr[t])) {
+          notpd += nan_is_notpd ? 1u : 0u;
+          continue;
+        }
+        V v[5];
+        combine5<V>(lr[t], sp[t], ls[t], cmbv, v);
+        if (LIST) {
+          const I id = (I)ids[e0 + t];
+          tr.add(v, id, lr[t], sp[t], ls[t]);
+          if (with_top) top_offer(tb, v[3], id, thr_hi, thr_lo);
+        } else {
+          const I loc = (I)(e0 + t);
+          tr.add_mono(v, loc, lr[t], sp[t], ls[t]);
+          if (with_top) top_offer(tb, v[3], loc, thr_hi, thr_lo);
+        }
+        if ((t & 3) == 3) tr.flush();
       }
       tr.flush();
     }
@@ -81,41 +191,85 @@ __global__ void __launch_bounds__(RED_NT) k_reduce_basis(const float* __restrict
         top_sort_cut(tb, 1, top_m);
         thr_lo = top_threshold(tb, 1, top_m);
       }
+      // every thread has read the counts before anyone appends again
       __syncthreads();
     }
   }
   int th = 0, tl = 0;
+  const unsigned long long id_off = LIST ? 0ull : id0;
   if (with_top) {
     top_sort_cut(tb, 0, top_m);
     top_sort_cut(tb, 1, top_m);
     th = tb.cnt[0];
     tl = tb.cnt[1];
-    top_write(tb, top_m, id0, part_top + (size_t)blockIdx.x * 2 * top_m);
+    top_write(tb, top_m, id_off, part_top + (size_t)blockIdx.x * 2 * top_m);
   }
-  block_write_part<float, unsigned>(tr, 0u, id0, sc, part + blockIdx.x, th, tl);
+  block_write_part<V, I>(tr, notpd, id_off, sc, part + blockIdx.x, th, tl);
+}
+
+template <typename V, bool LIST>
+static cudaError_t launch_reduce_t(const V* basis, unsigned long long stride_elems,
+                                   unsigned long long n, const unsigned long long* ids,
+                                   const unsigned long long* list_count,
+                                   unsigned long long list_cap, unsigned long long id0, Combine cmb,
+                                   int top_m, int nan_is_notpd, const float* seed_thr,
+                                   PartRec* part, TopEnt* part_top, int num_sms, int max_blocks,
+                                   cudaStream_t s, int* grid_out) {
+  using I = typename std::conditional<LIST, unsigned long long, unsigned>::type;
+  const size_t sm = top_m > 0 ? (size_t)RTOP_CAP * 2 * (sizeof(V) + sizeof(I)) : 0;
+  void (*fn)(const V*, const V*, const V*, unsigned long long, const unsigned long long*,
+             const unsigned long long*, unsigned long long, unsigned long long, Combine, int, int,
+             const float*, PartRec*, TopEnt*) = k_reduce_basis<V, LIST>;
+  int occ = 0;
+  cudaError_t e = occupancy_cached((const void*)fn, RED_NT, sm, &occ);
+  if (e != cudaSuccess) return e;
+  long long grid = (long long)num_sms * occ;
+  if (!LIST) {
+    const long long need =
+        (long long)((n + RED_NT * RB_PER_THREAD - 1) / (RED_NT * RB_PER_THREAD));
+    if (need < grid) grid = need > 0 ? need : 1;
+  }
+  if (grid > max_blocks) grid = max_blocks;
+  fn<<<(unsigned)grid, RED_NT, sm, s>>>(basis, basis + stride_elems, basis + 2 * stride_elems, n,
+                                        ids, list_count, list_cap, id0, cmb, top_m, nan_is_notpd,
+                                        seed_thr, part, part_top);
+  if (grid_out) *grid_out = (int)grid;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_basis(const float* basis, unsigned long long stride_elems,
                                 unsigned long long n, unsigned long long id0, Combine cmb,
-                                int top_m, PartRec* part, TopEnt* part_top, int num_sms,
-                                int max_blocks, cudaStream_t s, int* grid_out) {
-  const size_t sm = top_m > 0 ? (size_t)TOP_CAP * 2 * (sizeof(float) + sizeof(unsigned)) : 0;
-  cudaError_t e = cudaFuncSetAttribute(k_reduce_basis, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_reduce_basis, RED_NT, sm);
-  if (e != cudaSuccess) return e;
-  if (occ < 1) occ = 1;
-  long long grid = (long long)num_sms * occ;
-  const long long need = (long long)((n + RED_NT * RB_PER_THREAD - 1) / (RED_NT * RB_PER_THREAD));
-  if (need < grid) grid = need > 0 ? need : 1;
-  if (grid > max_blocks) grid = max_blocks;
-  k_reduce_basis<<<(unsigned)grid, RED_NT, sm, s>>>(basis, basis + stride_elems,
-                                                    basis + 2 * stride_elems, n, id0, cmb, top_m,
-                                                    part, part_top);
-  if (grid_out) *grid_out = (int)grid;
-  return cudaGetLastError();
+                                int top_m, float* seed_thr, PartRec* part, TopEnt* part_top,
+                                int num_sms, int max_blocks, cudaStream_t s, int* grid_out) {
+  const float* thr = nullptr;
+  if (top_m > 0 && seed_thr && n > (unsigned long long)4 * SEED_S) {
+    const size_t sm = (size_t)SEED_S * sizeof(float);
+    int occ = 0;
+    cudaError_t e = occupancy_cached((const void*)k_seed_thresholds, SEED_NT, sm, &occ);
+    if (e != cudaSuccess) return e;
+    k_seed_thresholds<<<1, SEED_NT, sm, s>>>(basis, basis + stride_elems, n, cmb, top_m, seed_thr);
+    thr = seed_thr;
+  }
+  return launch_reduce_t<float, false>(basis, stride_elems, n, nullptr, nullptr, 0, id0, cmb, top_m,
+                                       0, thr, part, part_top, num_sms, max_blocks, s, grid_out);
+}
+
+cudaError_t launch_reduce_basis64(const double* basis, unsigned long long stride_elems,
+                                  unsigned long long n, unsigned long long id0, Combine cmb,
+                                  int top_m, PartRec* part, TopEnt* part_top, int num_sms,
+                                  int max_blocks, cudaStream_t s, int* grid_out) {
+  return launch_reduce_t<double, false>(basis, stride_elems, n, nullptr, nullptr, 0, id0, cmb,
+                                        top_m, 1, nullptr, part, part_top, num_sms, max_blocks, s,
+                                        grid_out);
+}
+
+cudaError_t launch_reduce_list64(const double* basis, unsigned long long stride_elems,
+                                 const unsigned long long* ids, const unsigned long long* count,
+                                 unsigned long long cap, Combine cmb, int top_m, PartRec* part,
+                                 TopEnt* part_top, int num_sms, int max_blocks, cudaStream_t s,
+                                 int* grid_out) {
+  return launch_reduce_t<double, true>(basis, stride_elems, 0, ids, count, cap, 0, cmb, top_m, 1,
+                                       nullptr, part, part_top, num_sms, max_blocks, s, grid_out);
 }
 
 }  // namespace thoi

@@ -72,6 +72,9 @@ struct thoi_ctx {
   size_t gpart_cap = 0;       // doubles
   float* basis = nullptr;     // FP32 path: three basis values per nplet of one piece
   size_t basis_cap = 0;       // floats
+  double* b64 = nullptr;      // FP64 basis values (FP64 path pieces, re-factor list)
+  size_t b64_cap = 0;         // doubles
+  float* seed_thr = nullptr;  // starting top-M thresholds of the streaming reduction (2 floats)
   // profiling: event pairs around launches, by class (0 nplet, 1 refactor, 2 merge, 3 reduce)
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;
@@ -80,6 +83,41 @@ struct thoi_ctx {
   int force_shape_valid = 0;
   Shape force_shape;
 };
+
+// ------------------------------------------------------------------ occupancy cache
+namespace thoi {
+static std::mutex g_occ_mu;
+static std::map<std::pair<const void*, size_t>, int> g_occ;   // (kernel, smem, device) -> blocks/SM
+static std::map<std::pair<const void*, int>, size_t> g_attr;  // (kernel, device) -> smem limit set
+cudaError_t occupancy_cached(const void* fn, int block, size_t smem, int* occ) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  // the kernel's dynamic shared-memory limit only ever grows, so every size
+  // launched before stays valid
+  const std::pair<const void*, int> akey(fn, dev);
+  auto at = g_attr.find(akey);
+  if (at == g_attr.end() || at->second < smem) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    g_attr[akey] = smem;
+  }
+  const std::pair<const void*, size_t> key(fn, smem * 64 + (size_t)dev);
+  auto it = g_occ.find(key);
+  if (it != g_occ.end()) {
+    *occ = it->second;
+    return cudaSuccess;
+  }
+  int o = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, block, smem);
+  if (e != cudaSuccess) return e;
+  if (o < 1) o = 1;
+  g_occ[key] = o;
+  *occ = o;
+  return cudaSuccess;
+}
+}  // namespace thoi
 
 // ------------------------------------------------------------------ autotune cache
 // Process-wide: (GPU name, SM count, order, mask width) -> launch shape.
@@ -336,6 +374,8 @@ extern "C" void thoi_destroy(thoi_ctx* c) {
   free_ptr(c->rec_buf);
   free_ptr(c->gpart);
   free_ptr(c->basis);
+  free_ptr(c->b64);
+  free_ptr(c->seed_thr);
   delete c;
 }
 
@@ -364,6 +404,7 @@ static thoi_status ctx_common(thoi_ctx* c, int N, const thoi_options* opt) {
   CK(cudaMalloc(&c->binom, (size_t)NB * NB * 8));
   CK(cudaMalloc(&c->status, sizeof(int)));
   CK(cudaMalloc(&c->flag_counts, MAX_SLOTS * sizeof(unsigned long long)));
+  CK(cudaMalloc(&c->seed_thr, 2 * sizeof(float)));
   CK(cudaHostAlloc(&c->h_cancel, sizeof(int), cudaHostAllocMapped));
   *c->h_cancel = 0;
   CK(cudaHostGetDevicePointer((void**)&c->d_cancel, c->h_cancel, 0));
@@ -506,7 +547,7 @@ struct SlotRange {
   unsigned long long r0, r1;  // rank range inside [id_begin, id_end)
 };
 
-constexpr int MAX_BLOCKS_PER_SM_RED = 4;   // cap for reduction launches (partials per block)
+constexpr int MAX_BLOCKS_PER_SM_RED = 8;   // cap for reduction launches (partials per block)
 constexpr int MAX_BLOCKS_PER_SM_OUT = 8;
 constexpr int REFACTOR_BLOCKS_PER_SM = 2;
 constexpr unsigned long long LAUNCH_SPLIT = 0xffffffffull;  // ranks per launch (u32 local ids)
@@ -647,6 +688,13 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       st = grow(&c->basis, &c->basis_cap, (size_t)3 * basis_stride(maxn));
       if (st != THOI_OK) return st;
     }
+    {
+      // FP64 basis scratch: pieces of the FP64 path, or the re-factor list
+      const size_t need = f64 ? (size_t)3 * basis_stride(maxn)
+                              : (size_t)3 * (((size_t)c->flag_cap + 63) / 64 * 64);
+      st = grow(&c->b64, &c->b64_cap, need);
+      if (st != THOI_OK) return st;
+    }
     const size_t n64 = f64 ? 0 : slots.size() * (size_t)ref_cap;
     if (c->part_top_m != top_m) {
       free_ptr(c->top32); c->top32 = nullptr;
@@ -710,7 +758,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         st = prof_begin(c, s, 3);
         if (st != THOI_OK) return st;
         CK(launch_reduce_basis(c->basis, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb, top_m,
-                               c->part32 + p32_off,
+                               c->seed_thr, c->part32 + p32_off,
                                top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
                                c->num_sms, blk_cap, s, &grid));
         st = prof_end(c, s);
@@ -720,7 +768,37 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         md.g32 += grid;
       }
     }
-    for (unsigned long long a0 = r.r0; a0 < r.r1 && !(red && !f64); a0 += LAUNCH_SPLIT) {
+    if (red && f64 && f64s_threads(c->N, r.k, nullptr) > 0) {
+      // FP64 records: basis values per piece, then the streaming reduction
+      const unsigned long long bstride = basis_stride(maxn);
+      for (unsigned long long a0 = r.r0; a0 < r.r1; a0 += PIECE) {
+        SlotRange sub = r;
+        sub.r0 = a0;
+        sub.r1 = r.r1 - a0 > PIECE ? a0 + PIECE : r.r1;
+        NpletArgs a = base_args(c, sub);
+        a.mode = 2;
+        int grid = 0;
+        st = prof_begin(c, s, 0);
+        if (st != THOI_OK) return st;
+        CK(launch_nplet_f64s(a, false, c->b64, bstride, c->num_sms, s, &grid,
+                             c->num_sms * MAX_BLOCKS_PER_SM_OUT));
+        st = prof_end(c, s);
+        if (st != THOI_OK) return st;
+        st = prof_begin(c, s, 3);
+        if (st != THOI_OK) return st;
+        CK(launch_reduce_basis64(c->b64, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb, top_m,
+                                 c->part32 + p32_off,
+                                 top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
+                                 c->num_sms, blk_cap, s, &grid));
+        st = prof_end(c, s);
+        if (st != THOI_OK) return st;
+        launches += 2;
+        p32_off += grid;
+        md.g32 += grid;
+      }
+    }
+    const bool done_red = red && (!f64 || f64s_threads(c->N, r.k, nullptr) > 0);
+    for (unsigned long long a0 = r.r0; a0 < r.r1 && !done_red; a0 += LAUNCH_SPLIT) {
       SlotRange sub = r;
       sub.r0 = a0;
       sub.r1 = r.r1 - a0 > LAUNCH_SPLIT ? a0 + LAUNCH_SPLIT : r.r1;
@@ -738,7 +816,9 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       const int cap = red ? blk_cap : c->num_sms * MAX_BLOCKS_PER_SM_OUT;
       st = prof_begin(c, s, 0);
       if (st != THOI_OK) return st;
-      if (f64) CK(launch_nplet_f64(a, c->num_sms, s, &grid, cap));
+      if (f64 && !red && f64s_threads(c->N, r.k, nullptr) > 0)
+        CK(launch_nplet_f64s(a, false, nullptr, 0, c->num_sms, s, &grid, cap));
+      else if (f64) CK(launch_nplet_f64(a, c->num_sms, s, &grid, cap));
       else CK(launch_nplet_f32(a, sh, c->num_sms, s, &grid, cap));
       st = prof_end(c, s);
       if (st != THOI_OK) return st;
@@ -761,12 +841,37 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       a.part = red ? c->part64 + p64_off : nullptr;
       a.part_top = red && top_m > 0 ? c->top64 + (size_t)p64_off * 2 * top_m : nullptr;
       int grid = 0;
-      st = prof_begin(c, s, 1);
-      if (st != THOI_OK) return st;
-      CK(launch_refactor(a, c->num_sms, s, &grid, ref_cap));
-      st = prof_end(c, s);
-      if (st != THOI_OK) return st;
-      launches++;
+      const bool smem_ok = f64s_threads(c->N, r.k, nullptr) > 0;
+      if (smem_ok) {
+        // FP64 kernel over the list, then (records) the list reduction
+        const unsigned long long lstride = ((unsigned long long)c->flag_cap + 63) / 64 * 64;
+        a.mode = red ? 2 : 0;
+        st = prof_begin(c, s, 1);
+        if (st != THOI_OK) return st;
+        CK(launch_nplet_f64s(a, true, c->b64, lstride, c->num_sms, s, &grid,
+                             c->num_sms * MAX_BLOCKS_PER_SM_OUT));
+        st = prof_end(c, s);
+        if (st != THOI_OK) return st;
+        launches++;
+        if (red) {
+          st = prof_begin(c, s, 3);
+          if (st != THOI_OK) return st;
+          CK(launch_reduce_list64(c->b64, lstride, c->flag_ids, c->flag_counts + si, c->flag_cap,
+                                  md.cmb, top_m, c->part64 + p64_off,
+                                  top_m > 0 ? c->top64 + (size_t)p64_off * 2 * top_m : nullptr,
+                                  c->num_sms, ref_cap, s, &grid));
+          st = prof_end(c, s);
+          if (st != THOI_OK) return st;
+          launches++;
+        }
+      } else {
+        st = prof_begin(c, s, 1);
+        if (st != THOI_OK) return st;
+        CK(launch_refactor(a, c->num_sms, s, &grid, ref_cap));
+        st = prof_end(c, s);
+        if (st != THOI_OK) return st;
+        launches++;
+      }
       if (red) {
         p64_off += grid;
         md.g64 = grid;
