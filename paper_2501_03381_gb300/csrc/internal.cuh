@@ -160,6 +160,12 @@ constexpr int MAX_SLOTS = 64;
 struct MergeDescs {
   MergeDesc d[MAX_SLOTS];
 };
+// Batched merge: descriptors and per-slot output places in device memory;
+// gmax = the largest g32 + g64 of any slot.
+cudaError_t launch_merge_arr(const MergeDesc* D, int n_slots, int gmax, const PartRec* p32,
+                             const TopEnt* t32, const PartRec* p64, const TopEnt* t64, int top_m,
+                             thoi_order_record* const* recp, TopEnt* const* topp,
+                             cudaStream_t s);
 cudaError_t launch_merge(const MergeDescs& D, int n_slots, const PartRec* p32, const TopEnt* t32,
                          const PartRec* p64, const TopEnt* t64, int top_m, thoi_order_record* recs,
                          TopEnt* tops, cudaStream_t s);

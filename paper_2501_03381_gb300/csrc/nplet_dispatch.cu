@@ -25,7 +25,7 @@ Shape default_shape(int k) {
 bool shape_available(int k, int lanes) {
   if (lanes == 1) return true;  // one-thread kernel for k <= 20, generic above
   if (lanes == 2) return k >= 13 && k <= 24;
-  if (lanes == 4) return k >= 25 && k <= 32;
+  if (lanes == 4) return k >= 21 && k <= 32;
   return false;
 }
 
@@ -46,6 +46,7 @@ cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, c
     switch (a.k) {
 #define CASE_G(KK) \
   case KK: return launch_grp_k<KK, 4>(a, sh, num_sms, s, grid_out, max_blocks);
+      CASE_G(21) CASE_G(22) CASE_G(23) CASE_G(24)
       CASE_G(25) CASE_G(26) CASE_G(27) CASE_G(28) CASE_G(29) CASE_G(30) CASE_G(31) CASE_G(32)
 #undef CASE_G
       default: break;

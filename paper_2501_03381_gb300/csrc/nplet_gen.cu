@@ -242,6 +242,12 @@ __device__ void merge_path(int side, const TopEnt* X, int nx, const TopEnt* Y, i
   }
 }
 
+__device__ void merge_slot(const MergeDesc& d, const PartRec* __restrict__ p32base,
+                           const TopEnt* __restrict__ t32base, const PartRec* __restrict__ p64base,
+                           const TopEnt* __restrict__ t64base, int top_m,
+                           thoi_order_record* __restrict__ rec, TopEnt* __restrict__ top_out,
+                           unsigned char* smem);
+
 __global__ void __launch_bounds__(MERGE_NT) k_merge(const MergeDescs D,
                                                     const PartRec* __restrict__ p32base,
                                                     const TopEnt* __restrict__ t32base,
@@ -249,7 +255,31 @@ __global__ void __launch_bounds__(MERGE_NT) k_merge(const MergeDescs D,
                                                     const TopEnt* __restrict__ t64base, int top_m,
                                                     thoi_order_record* __restrict__ recs,
                                                     TopEnt* __restrict__ tops) {
-  const MergeDesc& d = D.d[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smem[];
+  merge_slot(D.d[blockIdx.x], p32base, t32base, p64base, t64base, top_m, recs + blockIdx.x,
+             tops + (size_t)blockIdx.x * 2 * top_m, smem);
+}
+
+// Batched form: one block per slot, descriptors and output places in device
+// memory (any number of slots).
+__global__ void __launch_bounds__(MERGE_NT) k_merge_arr(const MergeDesc* __restrict__ D,
+                                                        const PartRec* __restrict__ p32base,
+                                                        const TopEnt* __restrict__ t32base,
+                                                        const PartRec* __restrict__ p64base,
+                                                        const TopEnt* __restrict__ t64base,
+                                                        int top_m,
+                                                        thoi_order_record* const* __restrict__ recp,
+                                                        TopEnt* const* __restrict__ topp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  merge_slot(D[blockIdx.x], p32base, t32base, p64base, t64base, top_m, recp[blockIdx.x],
+             topp[blockIdx.x], smem);
+}
+
+__device__ void merge_slot(const MergeDesc& d, const PartRec* __restrict__ p32base,
+                           const TopEnt* __restrict__ t32base, const PartRec* __restrict__ p64base,
+                           const TopEnt* __restrict__ t64base, int top_m,
+                           thoi_order_record* __restrict__ rec, TopEnt* __restrict__ top_out,
+                           unsigned char* smem) {
   const PartRec* p32 = p32base + d.p32_off;
   const TopEnt* t32 = t32base + (size_t)d.p32_off * 2 * top_m;
   const PartRec* p64 = p64base + d.p64_off;
@@ -257,9 +287,6 @@ __global__ void __launch_bounds__(MERGE_NT) k_merge(const MergeDescs D,
   const int g32 = d.g32, g64 = d.g64, k = d.k;
   const Combine cmb = d.cmb;
   const unsigned long long* refactored = d.refactored;
-  thoi_order_record* rec = recs + blockIdx.x;
-  TopEnt* top_out = tops + (size_t)blockIdx.x * 2 * top_m;
-  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double s_vmin[MERGE_NT][5];
   __shared__ unsigned long long s_imin[MERGE_NT][5];
   __shared__ double s_vmax[MERGE_NT][5];
@@ -591,6 +618,21 @@ cudaError_t launch_merge(const MergeDescs& D, int n_slots, const PartRec* p32, c
   if (e != cudaSuccess) return e;
   if (n_slots <= 0) return cudaSuccess;
   k_merge<<<n_slots, MERGE_NT, sm, s>>>(D, p32, t32, p64, t64, top_m, recs, tops);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_arr(const MergeDesc* D, int n_slots, int gmax, const PartRec* p32,
+                             const TopEnt* t32, const PartRec* p64, const TopEnt* t64, int top_m,
+                             thoi_order_record* const* recp, TopEnt* const* topp,
+                             cudaStream_t s) {
+  const size_t sm = top_m > 0 ? (size_t)3 * top_m * sizeof(TopEnt) + MERGE_SURV_CAP * sizeof(TopEnt) +
+                                    (size_t)(gmax + 1) * sizeof(int)
+                              : 0;
+  int occ = 0;
+  cudaError_t e = occupancy_cached((const void*)k_merge_arr, MERGE_NT, sm, &occ);
+  if (e != cudaSuccess) return e;
+  if (n_slots <= 0) return cudaSuccess;
+  k_merge_arr<<<n_slots, MERGE_NT, sm, s>>>(D, p32, t32, p64, t64, top_m, recp, topp);
   return cudaGetLastError();
 }
 

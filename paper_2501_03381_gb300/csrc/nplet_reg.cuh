@@ -93,8 +93,18 @@ __device__ __forceinline__ void nplet_reg_one(M mask, int N, const float* sR, in
 // so their shared-memory gathers mostly hit the same words.  Output: mode 0
 // writes the five measures per nplet, mode 2 the three basis values that the
 // streaming reduction consumes; flagged nplets go to the FP64 re-factor list.
+// Minimum resident blocks per SM, picked per order by timing: orders up to
+// 16 are held to three blocks (at most 168 registers a thread), 18..20 to two;
+// order 17 keeps the allocation the compiler picks on its own (three blocks
+// spill there, two are slower than one).
+template <int K>
+struct RegBlocks {
+  static constexpr int value = K <= 16 ? 3 : (K == 17 ? 1 : 2);
+};
+
 template <int K, typename M>
-__global__ void __launch_bounds__(RED_NT) k_nplet_reg(const NpletArgs a, const int chunk) {
+__global__ void __launch_bounds__(RED_NT, RegBlocks<K>::value) k_nplet_reg(const NpletArgs a,
+                                                                          const int chunk) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N, ldr = row_stride(N);
   const SmemLayout L = smem_layout(N, K, ldr, sizeof(float), sizeof(unsigned), 0);
