@@ -1,0 +1,207 @@
+// Multi-dataset batch: dispatch of the batched FP32 nplet kernel by order,
+// and the batched reduction, FP64 re-factor and list-reduction kernels.  The
+// bodies are those of the single-dataset kernels (reduce_core, f64s_body);
+// here a block finds its dataset, order and range from descriptors in device
+// memory instead of from launch arguments, so that one launch covers every
+// dataset of the batch.
+#include <type_traits>
+
+#include "nplet_f64.cuh"
+#include "reduce.cuh"
+
+namespace thoi {
+
+template <int K>
+cudaError_t batch_occ_k(bool wide, int maxN, size_t* smem, int* occ);
+template <int K>
+cudaError_t batch_launch_k(bool wide, const BatchArgs& b, size_t smem, int grid, int chunk,
+                           cudaStream_t s);
+
+#define THOI_BATCH_CASES(CALL)                                                              \
+  switch (k) {                                                                              \
+    case 1: return CALL(1); case 2: return CALL(2); case 3: return CALL(3);                 \
+    case 4: return CALL(4); case 5: return CALL(5); case 6: return CALL(6);                 \
+    case 7: return CALL(7); case 8: return CALL(8); case 9: return CALL(9);                 \
+    case 10: return CALL(10); case 11: return CALL(11); case 12: return CALL(12);           \
+    case 13: return CALL(13); case 14: return CALL(14); case 15: return CALL(15);           \
+    case 16: return CALL(16); case 17: return CALL(17); case 18: return CALL(18);           \
+    case 19: return CALL(19); case 20: return CALL(20);                                     \
+    default: return cudaErrorInvalidValue;                                                  \
+  }
+
+cudaError_t batch_nplet_occupancy(int k, bool wide, int maxN, size_t* smem, int* occ) {
+#define OCC(KK) batch_occ_k<KK>(wide, maxN, smem, occ)
+  THOI_BATCH_CASES(OCC)
+#undef OCC
+}
+
+cudaError_t launch_nplet_batch(int k, bool wide, const BatchArgs& b, size_t smem, int grid,
+                               int chunk, cudaStream_t s) {
+  if (grid < 1 || chunk < 1 || chunk > 8) return cudaErrorInvalidValue;
+#define LAUNCH(KK) batch_launch_k<KK>(wide, b, smem, grid, chunk, s)
+  THOI_BATCH_CASES(LAUNCH)
+#undef LAUNCH
+}
+#undef THOI_BATCH_CASES
+
+// ------------------------------------------------------------------ reduction tiles
+// One block per reduction tile: the streaming reduction of the tile's basis
+// triples into partial blockIdx.x.
+__global__ void __launch_bounds__(RED_NT, 6) k_reduce_batch(const float* __restrict__ basis,
+                                                          unsigned long long bstride,
+                                                          const BatchRTile* __restrict__ rt,
+                                                          const BatchSlot* __restrict__ slots,
+                                                          int top_m, PartRec* __restrict__ part,
+                                                          TopEnt* __restrict__ part_top) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ RedScratch sc;
+  __shared__ int s_tcnt[2];
+  const BatchRTile t = rt[blockIdx.x];
+  const Combine cmb = slots[t.slot].cmb;
+  const float* B = basis + t.boff;
+  reduce_core<float, false>(threadIdx.x, RED_NT, B, B + bstride, B + 2 * bstride, t.n, nullptr,
+                            nullptr, 0, t.id0, cmb, top_m, 0, nullptr, part + blockIdx.x,
+                            part_top + (size_t)blockIdx.x * 2 * top_m, smem, sc, s_tcnt);
+}
+
+static size_t reduce_smem(int top_m, size_t vsz, size_t isz) {
+  return top_m > 0 ? (size_t)RTOP_CAP * 2 * (vsz + isz) : 0;
+}
+
+cudaError_t batch_reduce_occupancy(int top_m, size_t* smem, int* occ) {
+  *smem = reduce_smem(top_m, sizeof(float), sizeof(unsigned));
+  return occupancy_cached((const void*)k_reduce_batch, RED_NT, *smem, occ);
+}
+
+cudaError_t launch_reduce_batch(const float* basis, unsigned long long bstride,
+                                const BatchRTile* rt, int n_rt, const BatchSlot* slots, int top_m,
+                                PartRec* part, TopEnt* part_top, cudaStream_t s) {
+  if (n_rt <= 0) return cudaSuccess;
+  const size_t sm = reduce_smem(top_m, sizeof(float), sizeof(unsigned));
+  k_reduce_batch<<<n_rt, RED_NT, sm, s>>>(basis, bstride, rt, slots, top_m, part, part_top);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FP64 re-factor
+// Block (x, y) re-factors list entries x, x + gridDim.x, ... (times NT) of
+// slot slot0 + y in FP64 and writes their basis triples.
+template <int NT, typename M>
+__global__ void __launch_bounds__(NT) k_refactor_batch(
+    const BatchDataset* __restrict__ ds, const BatchSlot* __restrict__ slots, int slot0,
+    const unsigned long long* __restrict__ binom, const unsigned long long* flag_ids,
+    unsigned long long* flag_counts, double* __restrict__ b64, unsigned long long lstride,
+    int* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int si = slot0 + blockIdx.y;
+  const BatchSlot sl = slots[si];
+  const BatchDataset D = ds[sl.d];
+  NpletArgs a;
+  a.N = D.N;
+  a.k = sl.k;
+  a.R32 = D.R32;
+  a.R64 = D.R64;
+  a.ls = D.ls;
+  a.binom = binom;
+  a.rank_begin = 0;
+  a.rank_end = sl.n;
+  a.id_base = sl.id_base;
+  a.cmb = sl.cmb;
+  a.tau_piv = D.tau_piv;
+  a.tau_tr = D.tau_tr;
+  a.mode = 2;
+  a.out = nullptr;
+  a.out_f64 = 1;
+  a.out_n = 0;
+  a.out_first = 0;
+  a.part = nullptr;
+  a.part_top = nullptr;
+  a.top_m = 0;
+  a.flag_ids = const_cast<unsigned long long*>(flag_ids) + sl.flag_off;
+  a.flag_count = flag_counts + si;
+  a.flag_cap = sl.flag_cap;
+  a.status = status;
+  a.cancel = nullptr;
+  f64s_body<NT, true, M>(a, b64 + sl.flag_off, lstride, smem);
+}
+
+template <int NT, typename M>
+static cudaError_t refactor_batch_t(const BatchDataset* ds, const BatchSlot* slots, int slot0,
+                                    int n_slots, const unsigned long long* binom,
+                                    const unsigned long long* flag_ids,
+                                    unsigned long long* flag_counts, double* b64,
+                                    unsigned long long lstride, int* status, int bx, size_t sm,
+                                    cudaStream_t s) {
+  int occ = 0;
+  cudaError_t e = occupancy_cached((const void*)k_refactor_batch<NT, M>, NT, sm, &occ);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)bx, (unsigned)n_slots);
+  k_refactor_batch<NT, M><<<grid, NT, sm, s>>>(ds, slots, slot0, binom, flag_ids, flag_counts,
+                                               b64, lstride, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refactor_batch(const BatchDataset* ds, const BatchSlot* slots, int slot0,
+                                  int n_slots, int maxN, int k, bool wide,
+                                  const unsigned long long* binom,
+                                  const unsigned long long* flag_ids,
+                                  unsigned long long* flag_counts, double* b64,
+                                  unsigned long long lstride, int* status, int bx,
+                                  cudaStream_t s) {
+  if (n_slots <= 0) return cudaSuccess;
+  if (bx < 1 || n_slots > 65535) return cudaErrorInvalidValue;
+  size_t sm = 0;
+  const int nt = f64s_threads(maxN, k, &sm);
+  if (nt == 0) return cudaErrorInvalidValue;
+#define RB(NTV)                                                                                \
+  (wide ? refactor_batch_t<NTV, unsigned long long>(ds, slots, slot0, n_slots, binom, flag_ids, \
+                                                    flag_counts, b64, lstride, status, bx, sm,   \
+                                                    s)                                           \
+        : refactor_batch_t<NTV, unsigned>(ds, slots, slot0, n_slots, binom, flag_ids,            \
+                                          flag_counts, b64, lstride, status, bx, sm, s))
+  if (nt == 128) return RB(128);
+  if (nt == 64) return RB(64);
+  return RB(32);
+#undef RB
+}
+
+// ------------------------------------------------------------------ list reduction
+// Block (x, y) reduces list entries of slot slot0 + y into partial
+// (slot0 + y) * gridDim.x + x.
+__global__ void __launch_bounds__(RED_NT, 6) k_reduce_list_batch(
+    const double* __restrict__ b64, unsigned long long lstride, const BatchSlot* __restrict__ slots,
+    int slot0, const unsigned long long* __restrict__ flag_ids,
+    const unsigned long long* flag_counts, int top_m, PartRec* __restrict__ part,
+    TopEnt* __restrict__ part_top) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ RedScratch sc;
+  __shared__ int s_tcnt[2];
+  const int si = slot0 + blockIdx.y;
+  const BatchSlot sl = slots[si];
+  const double* B = b64 + sl.flag_off;
+  const size_t pi = (size_t)si * gridDim.x + blockIdx.x;
+  reduce_core<double, true>((unsigned long long)blockIdx.x * RED_NT + threadIdx.x,
+                            (unsigned long long)gridDim.x * RED_NT, B, B + lstride, B + 2 * lstride,
+                            0, flag_ids + sl.flag_off, flag_counts + si, sl.flag_cap, 0, sl.cmb,
+                            top_m, 1, nullptr, part + pi, part_top + pi * 2 * top_m, smem, sc,
+                            s_tcnt);
+}
+
+cudaError_t launch_reduce_list_batch(const double* b64, unsigned long long lstride,
+                                     const BatchSlot* slots, int slot0, int n_slots,
+                                     const unsigned long long* flag_ids,
+                                     const unsigned long long* flag_counts, int top_m,
+                                     PartRec* part, TopEnt* part_top, int bx, cudaStream_t s) {
+  if (n_slots <= 0) return cudaSuccess;
+  if (bx < 1 || n_slots > 65535) return cudaErrorInvalidValue;
+  const size_t sm = reduce_smem(top_m, sizeof(double), sizeof(unsigned long long));
+  int occ = 0;
+  cudaError_t e = occupancy_cached((const void*)k_reduce_list_batch, RED_NT, sm, &occ);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)bx, (unsigned)n_slots);
+  k_reduce_list_batch<<<grid, RED_NT, sm, s>>>(b64, lstride, slots, slot0, flag_ids, flag_counts,
+                                               top_m, part, part_top);
+  return cudaGetLastError();
+}
+
+}  // namespace thoi

@@ -178,6 +178,78 @@ cudaError_t launch_grad_pass(const NpletArgs& a, double* Gpart, int grid, int me
 cudaError_t launch_grad_finish(const double* Gpart, int nblk, const double* sig64, int N, float* out,
                                cudaStream_t s);
 
+// ------------------------------------------------------------------ multi-dataset batch
+// Many datasets of uneven (N, T) in one graph: per order k one persistent
+// nplet launch walks a list of tiles (dataset, rank range) of every dataset,
+// one reduction launch walks a list of reduction tiles, then one FP64
+// re-factor launch and one list-reduction launch cover every dataset's
+// flagged nplets (grid.y = slot), and one merge launch writes every record.
+struct BatchDataset {
+  const float* R32;   // N x N correlation, FP32
+  const double* R64;  // N x N correlation, FP64
+  const double* ls;   // log Sigma_ii
+  int N;
+  float tau_piv, tau_tr;
+  int pad;
+};
+// One (dataset, order) pair with at least one nplet.
+struct BatchSlot {
+  int d, k;
+  unsigned long long n;        // C(N_d, k)
+  unsigned long long id_base;  // global id of rank 0 within dataset d's enumeration
+  unsigned long long flag_off, flag_cap;  // region of the flag list (and FP64 basis)
+  Combine cmb;
+};
+// Nplet tile: ranks [r0, r0 + n) of a slot; basis values at boff of the piece.
+struct BatchTile {
+  unsigned long long r0, boff;
+  unsigned n;
+  int slot;
+};
+// Reduction tile: n basis triples at boff of the piece, global ids id0 + e.
+struct BatchRTile {
+  unsigned long long boff, n, id0;
+  int slot, pad;
+};
+struct BatchArgs {
+  const BatchDataset* ds;
+  const BatchSlot* slots;
+  const BatchTile* tiles;
+  int n_tiles;
+  int pad;
+  const unsigned long long* binom;  // NB x NB
+  float* basis;                     // three arrays of bstride floats
+  unsigned long long bstride;
+  unsigned long long* flag_ids;
+  unsigned long long* flag_counts;  // one counter per slot
+  int* status;
+  const int* cancel;
+};
+// Dynamic shared memory and blocks per SM of the batched FP32 nplet kernel
+// for order k (maxN = the largest N of the batch; wide = 64-bit masks).
+cudaError_t batch_nplet_occupancy(int k, bool wide, int maxN, size_t* smem, int* occ);
+cudaError_t launch_nplet_batch(int k, bool wide, const BatchArgs& b, size_t smem, int grid,
+                               int chunk, cudaStream_t s);
+cudaError_t batch_reduce_occupancy(int top_m, size_t* smem, int* occ);
+cudaError_t launch_reduce_batch(const float* basis, unsigned long long bstride,
+                                const BatchRTile* rt, int n_rt, const BatchSlot* slots, int top_m,
+                                PartRec* part, TopEnt* part_top, cudaStream_t s);
+// FP64 re-factor of the flagged nplets of slots [slot0, slot0 + n_slots),
+// grid (bx, n_slots); basis values at b64[m * lstride + flag_off + e].
+cudaError_t launch_refactor_batch(const BatchDataset* ds, const BatchSlot* slots, int slot0,
+                                  int n_slots, int maxN, int k, bool wide,
+                                  const unsigned long long* binom,
+                                  const unsigned long long* flag_ids,
+                                  unsigned long long* flag_counts, double* b64,
+                                  unsigned long long lstride, int* status, int bx,
+                                  cudaStream_t s);
+// Reduction of those lists: partial (slot, x) at part[(slot) * bx + x].
+cudaError_t launch_reduce_list_batch(const double* b64, unsigned long long lstride,
+                                     const BatchSlot* slots, int slot0, int n_slots,
+                                     const unsigned long long* flag_ids,
+                                     const unsigned long long* flag_counts, int top_m,
+                                     PartRec* part, TopEnt* part_top, int bx, cudaStream_t s);
+
 // ------------------------------------------------------------------ device helpers
 #ifdef __CUDACC__
 

@@ -453,21 +453,27 @@ __device__ void load_tables(const NpletArgs& a, unsigned char* smem, const SmemL
   __syncthreads();
 }
 
-// Warp-aggregated append of a global id to the FP64 re-factor list.
-__device__ __forceinline__ void flag_append(const NpletArgs& a, bool flag, unsigned long long id) {
+// Warp-aggregated append of a global id to an FP64 re-factor list (every
+// active lane of the warp appends to the same list).
+__device__ __forceinline__ void flag_append_to(unsigned long long* ids, unsigned long long* count,
+                                               unsigned long long cap, int* status, bool flag,
+                                               unsigned long long id) {
   const unsigned act = __activemask();
   const unsigned fl = __ballot_sync(act, flag);
   if (!fl) return;
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(fl) - 1;
   unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(a.flag_count, (unsigned long long)__popc(fl));
+  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(fl));
   if (flag) {
     base = __shfl_sync(fl, base, leader);
     const unsigned long long pos = base + __popc(fl & ((1u << lane) - 1u));
-    if (pos < a.flag_cap) a.flag_ids[pos] = id;
-    else atomicOr(a.status, ST_FLAG_OVERFLOW);
+    if (pos < cap) ids[pos] = id;
+    else atomicOr(status, ST_FLAG_OVERFLOW);
   }
+}
+__device__ __forceinline__ void flag_append(const NpletArgs& a, bool flag, unsigned long long id) {
+  flag_append_to(a.flag_ids, a.flag_count, a.flag_cap, a.status, flag, id);
 }
 
 // Basis store (mode 2): log det R_S, sum_j log p_j and sum_i log Sigma_ii of

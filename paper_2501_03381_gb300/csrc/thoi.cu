@@ -82,6 +82,7 @@ struct thoi_ctx {
   // autotuner: a shape forced for the duration of a timing run
   int force_shape_valid = 0;
   Shape force_shape;
+  unsigned long long serial = 0;  // unique per context (keys the batch graph cache)
 };
 
 // ------------------------------------------------------------------ occupancy cache
@@ -123,6 +124,7 @@ cudaError_t occupancy_cached(const void* fn, int block, size_t smem, int* occ) {
 // Process-wide: (GPU name, SM count, order, mask width) -> launch shape.
 static std::mutex g_tune_mu;
 static std::map<std::string, Shape> g_tune;
+static unsigned long long g_tune_gen = 0;  // bumped whenever g_tune changes
 
 static std::string tune_key(const char* gpu, int sms, int k, int wide) {
   char b[320];
@@ -353,8 +355,12 @@ extern "C" thoi_status thoi_set_cancel(thoi_ctx* c, int32_t flag) {
   return THOI_OK;
 }
 
+static void batch_forget(unsigned long long serial);
+static unsigned long long next_serial();
+
 extern "C" void thoi_destroy(thoi_ctx* c) {
   if (!c) return;
+  batch_forget(c->serial);
   free_ptr(c->sig64);
   free_ptr(c->sig32);
   free_ptr(c->R64);
@@ -391,6 +397,7 @@ static thoi_status ctx_common(thoi_ctx* c, int N, const thoi_options* opt) {
       c->opt.sigma32_source != THOI_SIGMA32_FROM_F64)
     return THOI_ERR_INVALID_ARG;
   c->N = N;
+  c->serial = next_serial();
   CK(cudaGetDevice(&c->device));
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, c->device));
@@ -975,19 +982,462 @@ extern "C" thoi_status thoi_measures_grad(thoi_ctx* c, const int32_t* orders, in
 }
 
 // ------------------------------------------------------------------ API: batch
-extern "C" thoi_status thoi_batch_measures(thoi_ctx* const* ctxs, int32_t D, int32_t kmin,
-                                           int32_t kmax, void* out, size_t out_bytes,
-                                           thoi_stats* stats, void* stream) {
-  if (!ctxs || D < 1 || kmin < 1 || kmax < kmin || kmax > THOI_MAX_N || !out)
-    return THOI_ERR_INVALID_ARG;
-  const int top_m = ctxs[0]->opt.top_m;
-  const int prec = ctxs[0]->opt.precision;
+// Multi-dataset batch plan: descriptors, workspace and the CUDA graph of one
+// (contexts, kmin, kmax) combination.  Per order k, the slots (dataset d
+// with k <= N_d) are cut into nplet tiles of BATCH_TILE ranks; tiles are
+// grouped into pieces of at most BATCH_PIECE nplets (the basis buffer holds
+// one piece), and runs of BATCH_RTILE ranks of one slot inside one piece
+// form the reduction tiles.  Graph per order and piece: the batched nplet
+// launch, then the batched reduction; per order: the batched FP64 re-factor
+// of the flagged nplets and its list reduction; at the end one merge over
+// every (dataset, order) pair.  Plans are cached by context serial numbers,
+// so a repeated call replays the graph.
+namespace {
+
+constexpr unsigned long long BATCH_TILE = 1ull << 16;
+constexpr unsigned long long BATCH_RTILE = 1ull << 18;
+constexpr unsigned long long BATCH_PIECE = 1ull << 27;
+constexpr int BATCH_CACHE = 4;
+
+struct BatchLaunch {
+  int k;
+  int tile0, n_tiles;
+  int rt0, n_rt;
+};
+
+struct BatchPlan {
+  std::vector<unsigned long long> serials;
+  int kmin = 0, kmax = 0, top_m = 0, device = 0;
+  unsigned long long tune_gen = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<void*> allocs;
+  unsigned char* staging = nullptr;
+  size_t per = 0;
+  int* status = nullptr;
+  unsigned long long* flag_counts = nullptr;
+  std::vector<unsigned long long> flag_caps;
+  int n_slots = 0;
+  int launches = 0;
+  unsigned long long nplets = 0;
+};
+
+void plan_free(BatchPlan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  for (void* q : p->allocs) cudaFree(q);
+  delete p;
+}
+
+}  // namespace
+
+static std::mutex g_batch_mu;
+static std::vector<BatchPlan*> g_batch;  // most recently used last
+static unsigned long long g_serial = 0;  // guarded by g_batch_mu
+
+static unsigned long long next_serial() {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  return ++g_serial;
+}
+
+static void batch_forget(unsigned long long serial) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batch.size();) {
+    bool hit = false;
+    for (auto x : g_batch[i]->serials) hit |= x == serial;
+    if (hit) {
+      plan_free(g_batch[i]);
+      g_batch.erase(g_batch.begin() + i);
+    } else {
+      i++;
+    }
+  }
+}
+
+template <typename T>
+static thoi_status plan_alloc(BatchPlan* p, T** ptr, size_t n) {
+  void* q = nullptr;
+  CK(cudaMalloc(&q, (n > 0 ? n : 1) * sizeof(T)));
+  p->allocs.push_back(q);
+  *ptr = (T*)q;
+  return THOI_OK;
+}
+
+static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
+                               BatchPlan* P) {
+  cudaStream_t s = nullptr;
+  thoi_ctx* c0 = ctxs[0];
+  const int top_m = c0->opt.top_m;
+  const int no = kmax - kmin + 1;
+  const int num_sms = c0->num_sms;
+  int maxN = 0;
+  for (int d = 0; d < D; d++) maxN = ctxs[d]->N > maxN ? ctxs[d]->N : maxN;
+  const bool wide = maxN > 32;
+  // datasets
+  std::vector<BatchDataset> hds(D);
+  for (int d = 0; d < D; d++) {
+    const thoi_ctx* c = ctxs[d];
+    hds[d].R32 = c->R32;
+    hds[d].R64 = c->R64;
+    hds[d].ls = c->ls;
+    hds[d].N = c->N;
+    hds[d].tau_piv = c->opt.pivot_tau;
+    hds[d].tau_tr = c->opt.trace_tau;
+    hds[d].pad = 0;
+  }
+  // slots by order; flag regions restart at 0 for every order (the re-factor
+  // of order k runs before the nplet launch of order k + 1)
+  std::vector<BatchSlot> hsl;
+  std::vector<int> slot0(no, 0), nslot(no, 0);
+  std::vector<int> slot_of(D * no, -1);  // (d, q) -> slot
+  unsigned long long lstride = 64;
+  for (int q = 0; q < no; q++) {
+    const int k = kmin + q;
+    slot0[q] = (int)hsl.size();
+    unsigned long long foff = 0;
+    for (int d = 0; d < D; d++) {
+      const thoi_ctx* c = ctxs[d];
+      if (k > c->N) continue;
+      BatchSlot sl;
+      memset(&sl, 0, sizeof sl);
+      sl.d = d;
+      sl.k = k;
+      sl.n = binom_host(c->N, k);
+      unsigned long long ib = 0;
+      for (int kk = kmin; kk < k; kk++) ib += binom_host(c->N, kk);
+      sl.id_base = ib;
+      unsigned long long cap;
+      if (c->opt.flag_capacity > 0) {
+        cap = c->opt.flag_capacity;
+      } else {
+        cap = sl.n / 16 + 1;
+        if (cap < (1ull << 16)) cap = 1ull << 16;
+      }
+      if (cap > sl.n) cap = sl.n;
+      sl.flag_off = foff;
+      sl.flag_cap = cap;
+      foff += (cap + 63) / 64 * 64;
+      sl.cmb = combine_for(c, k);
+      slot_of[d * no + q] = (int)hsl.size();
+      hsl.push_back(sl);
+      P->nplets += sl.n;
+    }
+    nslot[q] = (int)hsl.size() - slot0[q];
+    if (foff > lstride) lstride = foff;
+  }
+  const int n_slots = (int)hsl.size();
+  P->n_slots = n_slots;
+  for (auto& sl : hsl) P->flag_caps.push_back(sl.flag_cap);
+  // tiles, pieces, reduction tiles
+  std::vector<BatchTile> htiles;
+  std::vector<BatchRTile> hrt;
+  std::vector<BatchLaunch> launches;
+  std::vector<int> rt_first(n_slots, -1), rt_count(n_slots, 0);
+  unsigned long long bstride = 64;
+  for (int q = 0; q < no; q++) {
+    if (nslot[q] == 0) continue;
+    BatchLaunch L;
+    L.k = kmin + q;
+    L.tile0 = (int)htiles.size();
+    L.rt0 = (int)hrt.size();
+    unsigned long long boff = 0;
+    auto close_piece = [&]() {
+      L.n_tiles = (int)htiles.size() - L.tile0;
+      L.n_rt = (int)hrt.size() - L.rt0;
+      if (L.n_tiles > 0) launches.push_back(L);
+      if (boff > bstride) bstride = boff;
+      L.tile0 = (int)htiles.size();
+      L.rt0 = (int)hrt.size();
+      boff = 0;
+    };
+    for (int si = slot0[q]; si < slot0[q] + nslot[q]; si++) {
+      const BatchSlot& sl = hsl[si];
+      for (unsigned long long r0 = 0; r0 < sl.n; r0 += BATCH_TILE) {
+        const unsigned long long n = sl.n - r0 < BATCH_TILE ? sl.n - r0 : BATCH_TILE;
+        const unsigned long long nal = (n + 63) / 64 * 64;
+        if (boff + nal > BATCH_PIECE) close_piece();
+        BatchTile t;
+        t.r0 = r0;
+        t.boff = boff;
+        t.n = (unsigned)n;
+        t.slot = si;
+        // a reduction tile starts at a multiple of BATCH_RTILE ranks or at
+        // the first tile of a piece; it grows by whole nplet tiles
+        const bool starts = hrt.empty() || (int)hrt.size() == L.rt0 || hrt.back().slot != si ||
+                            r0 % BATCH_RTILE == 0;
+        if (starts) {
+          BatchRTile r;
+          r.boff = boff;
+          r.n = n;
+          r.id0 = sl.id_base + r0;
+          r.slot = si;
+          r.pad = 0;
+          if (rt_first[si] < 0) rt_first[si] = (int)hrt.size();
+          rt_count[si]++;
+          hrt.push_back(r);
+        } else {
+          hrt.back().n += n;
+        }
+        htiles.push_back(t);
+        boff += nal;
+      }
+    }
+    close_piece();
+  }
+  // merge descriptors: every (dataset, order) pair, records in output order
+  const int B2 = [&]() {
+    int b = D > 0 ? (2 * num_sms) / D : 1;
+    if (b < 1) b = 1;
+    if (b > 8) b = 8;
+    return b;
+  }();
+  int bx_ref = 2 * num_sms;
+  const size_t per = thoi_records_bytes(no, top_m);
+  P->per = per;
+  std::vector<MergeDesc> hmd(D * no);
+  int gmax = 1;
+  for (int d = 0; d < D; d++) {
+    for (int q = 0; q < no; q++) {
+      MergeDesc& m = hmd[d * no + q];
+      memset(&m, 0, sizeof m);
+      m.k = kmin + q;
+      const int si = slot_of[d * no + q];
+      if (si >= 0) {
+        m.p32_off = rt_first[si];
+        m.g32 = rt_count[si];
+        m.p64_off = si * B2;
+        m.g64 = B2;
+        m.cmb = hsl[si].cmb;
+      }
+      if (m.g32 + m.g64 > gmax) gmax = m.g32 + m.g64;
+    }
+  }
+  // device buffers
+  thoi_status st;
+  BatchDataset* d_ds;
+  BatchSlot* d_sl;
+  BatchTile* d_tiles;
+  BatchRTile* d_rt;
+  MergeDesc* d_md;
+  thoi_order_record** d_recp;
+  TopEnt** d_topp;
+  float* basis;
+  double* b64;
+  unsigned long long* flag_ids;
+  PartRec *part32, *part64;
+  TopEnt *top32, *top64;
+  const size_t n_rt = hrt.size();
+  const size_t n64 = (size_t)n_slots * B2;
+  if ((st = plan_alloc(P, &d_ds, D)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &d_sl, n_slots)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &d_tiles, htiles.size())) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &d_rt, n_rt)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &d_md, hmd.size())) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &d_recp, hmd.size())) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &d_topp, hmd.size())) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &basis, 3 * (size_t)bstride)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &b64, 3 * (size_t)lstride)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &flag_ids, (size_t)lstride)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &P->flag_counts, (size_t)n_slots)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &part32, n_rt)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &part64, n64)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &top32, n_rt * 2 * (size_t)top_m)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &top64, n64 * 2 * (size_t)top_m)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &P->staging, per * (size_t)D)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &P->status, 1)) != THOI_OK) return st;
+  for (int d = 0; d < D; d++) {
+    for (int q = 0; q < no; q++) {
+      const int si = slot_of[d * no + q];
+      if (si >= 0) hmd[d * no + q].refactored = P->flag_counts + si;
+    }
+  }
+  std::vector<thoi_order_record*> hrecp(hmd.size());
+  std::vector<TopEnt*> htopp(hmd.size());
   for (int d = 0; d < D; d++)
-    if (!ctxs[d] || ctxs[d]->opt.top_m != top_m || ctxs[d]->opt.precision != prec)
-      return THOI_ERR_INVALID_ARG;
+    for (int q = 0; q < no; q++) {
+      unsigned char* base = P->staging + per * d;
+      hrecp[d * no + q] = (thoi_order_record*)base + q;
+      htopp[d * no + q] =
+          (TopEnt*)(base + (size_t)no * sizeof(thoi_order_record)) + (size_t)q * 2 * top_m;
+    }
+  CK(cudaMemcpy(d_ds, hds.data(), hds.size() * sizeof(BatchDataset), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_sl, hsl.data(), hsl.size() * sizeof(BatchSlot), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_tiles, htiles.data(), htiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_rt, hrt.data(), hrt.size() * sizeof(BatchRTile), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_md, hmd.data(), hmd.size() * sizeof(MergeDesc), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_recp, hrecp.data(), hrecp.size() * sizeof(void*), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_topp, htopp.data(), htopp.size() * sizeof(void*), cudaMemcpyHostToDevice));
+  // launch shapes (occupancy queried before the capture)
+  std::vector<size_t> smem_k(no, 0);
+  std::vector<int> grid_k(no, 0), chunk_k(no, 8);
+  for (int q = 0; q < no; q++) {
+    if (nslot[q] == 0) continue;
+    const int k = kmin + q;
+    int occ = 0;
+    CK(batch_nplet_occupancy(k, wide, maxN, &smem_k[q], &occ));
+    const Shape sh = shape_for(c0, k);
+    if (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ) occ = sh.blocks_per_sm;
+    grid_k[q] = num_sms * (occ > 0 ? occ : 1);
+    chunk_k[q] = sh.chunk > 0 && sh.chunk <= 8 ? sh.chunk : 8;
+  }
+  {
+    size_t sm = 0;
+    int occ = 0;
+    CK(batch_reduce_occupancy(top_m, &sm, &occ));
+  }
+  // capture on a private stream (the caller's may be the legacy default
+  // stream, which cannot be captured); the graph is launched on the caller's
+  int nl = 0;
+  cudaStream_t cs = nullptr;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  s = cs;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(cudaGetLastError());
+  }
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess && x != cudaSuccess) e = x;
+    return e == cudaSuccess;
+  };
+  ok(cudaMemsetAsync(P->status, 0, sizeof(int), s));
+  ok(cudaMemsetAsync(P->flag_counts, 0, (size_t)(n_slots > 0 ? n_slots : 1) * 8, s));
+  size_t li = 0;
+  for (int q = 0; q < no && e == cudaSuccess; q++) {
+    if (nslot[q] == 0) continue;
+    const int k = kmin + q;
+    for (; li < launches.size() && launches[li].k == k && e == cudaSuccess; li++) {
+      const BatchLaunch& L = launches[li];
+      BatchArgs b;
+      memset(&b, 0, sizeof b);
+      b.ds = d_ds;
+      b.slots = d_sl;
+      b.tiles = d_tiles + L.tile0;
+      b.n_tiles = L.n_tiles;
+      b.binom = c0->binom;
+      b.basis = basis;
+      b.bstride = bstride;
+      b.flag_ids = flag_ids;
+      b.flag_counts = P->flag_counts;
+      b.status = P->status;
+      b.cancel = c0->d_cancel;
+      const int grid = grid_k[q] < L.n_tiles ? grid_k[q] : L.n_tiles;
+      ok(launch_nplet_batch(k, wide, b, smem_k[q], grid, chunk_k[q], s));
+      ok(launch_reduce_batch(basis, bstride, d_rt + L.rt0, L.n_rt, d_sl, top_m, part32 + L.rt0,
+                             top32 + (size_t)L.rt0 * 2 * top_m, s));
+      nl += 2;
+    }
+    int bx = bx_ref / nslot[q];
+    if (bx < 1) bx = 1;
+    if (bx > 64) bx = 64;
+    ok(launch_refactor_batch(d_ds, d_sl, slot0[q], nslot[q], maxN, k, wide, c0->binom, flag_ids,
+                             P->flag_counts, b64, lstride, P->status, bx, s));
+    ok(launch_reduce_list_batch(b64, lstride, d_sl, slot0[q], nslot[q], flag_ids, P->flag_counts,
+                                top_m, part64, top64, B2, s));
+    nl += 2;
+  }
+  ok(launch_merge_arr(d_md, D * no, gmax, part32, top32, part64, top64, top_m, d_recp, d_topp, s));
+  nl++;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(s, &g);
+  cudaStreamDestroy(cs);
+  if (e == cudaSuccess) e = ee;
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return cuda_fail(e);
+  }
+  P->graph = g;
+  CK(cudaGraphInstantiate(&P->exec, g, 0));
+  P->launches = nl;
+  return THOI_OK;
+}
+
+static thoi_status batch_graph(thoi_ctx* const* ctxs, int32_t D, int32_t kmin, int32_t kmax,
+                               void* out, thoi_stats* stats, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  thoi_ctx* c0 = ctxs[0];
+  std::vector<unsigned long long> key(D);
+  for (int d = 0; d < D; d++) key[d] = ctxs[d]->serial;
+  BatchPlan* P = nullptr;
+  unsigned long long tg;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tg = g_tune_gen;
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batch.size(); i++) {
+    BatchPlan* p = g_batch[i];
+    if (p->serials == key && p->kmin == kmin && p->kmax == kmax && p->device == c0->device &&
+        p->tune_gen == tg) {
+      P = p;
+      g_batch.erase(g_batch.begin() + i);
+      g_batch.push_back(P);
+      break;
+    }
+  }
+  if (!P) {
+    P = new BatchPlan;
+    P->serials = key;
+    P->kmin = kmin;
+    P->kmax = kmax;
+    P->top_m = c0->opt.top_m;
+    P->device = c0->device;
+    P->tune_gen = tg;
+    const thoi_status st = batch_build(ctxs, D, kmin, kmax, P);
+    if (st != THOI_OK) {
+      plan_free(P);
+      return st;
+    }
+    while ((int)g_batch.size() >= BATCH_CACHE) {
+      plan_free(g_batch.front());
+      g_batch.erase(g_batch.begin());
+    }
+    g_batch.push_back(P);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c0->opt.profile) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+  }
+  CK(cudaGraphLaunch(P->exec, s));
+  if (e1) CK(cudaEventRecord(e1, s));
+  CK(cudaMemcpyAsync(out, P->staging, P->per * (size_t)D, cudaMemcpyDefault, s));
+  int hs = 0;
+  std::vector<unsigned long long> fc(P->n_slots > 0 ? P->n_slots : 1);
+  CK(cudaMemcpyAsync(&hs, P->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(fc.data(), P->flag_counts, fc.size() * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  if (e1) {
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    unsigned long long nref = 0;
+    for (int i = 0; i < P->n_slots; i++) nref += fc[i] < P->flag_caps[i] ? fc[i] : P->flag_caps[i];
+    stats->nplets = P->nplets;
+    stats->n_refactored = nref;
+    stats->launches = P->launches;
+    stats->nplet_ms = ms;
+  }
+  if (hs & ST_FLAG_OVERFLOW) return THOI_ERR_WORKSPACE;
+  if (hs & ST_CANCELLED) return THOI_ERR_CANCELLED;
+  if (hs & ST_NOT_PD) return THOI_ERR_NOT_PD;
+  return THOI_OK;
+}
+
+// One context after the other through thoi_measures (FP64 path, or orders
+// above the register kernels' range).
+static thoi_status batch_sequential(thoi_ctx* const* ctxs, int32_t D, int32_t kmin, int32_t kmax,
+                                    void* out, thoi_stats* stats, void* stream) {
+  const int top_m = ctxs[0]->opt.top_m;
   const int no = kmax - kmin + 1;
   const size_t per = thoi_records_bytes(no, top_m);
-  if (out_bytes < per * (size_t)D) return THOI_ERR_INVALID_ARG;
   const bool dev = is_device_ptr(out);
   std::vector<unsigned char> host(per);
   thoi_stats tot;
@@ -1026,6 +1476,31 @@ extern "C" thoi_status thoi_batch_measures(thoi_ctx* const* ctxs, int32_t D, int
   return THOI_OK;
 }
 
+
+extern "C" thoi_status thoi_batch_measures(thoi_ctx* const* ctxs, int32_t D, int32_t kmin,
+                                           int32_t kmax, void* out, size_t out_bytes,
+                                           thoi_stats* stats, void* stream) {
+  if (!ctxs || D < 1 || kmin < 1 || kmax < kmin || kmax > THOI_MAX_N || !out)
+    return THOI_ERR_INVALID_ARG;
+  const int top_m = ctxs[0]->opt.top_m;
+  const int prec = ctxs[0]->opt.precision;
+  for (int d = 0; d < D; d++)
+    if (!ctxs[d] || ctxs[d]->opt.top_m != top_m || ctxs[d]->opt.precision != prec ||
+        ctxs[d]->device != ctxs[0]->device)
+      return THOI_ERR_INVALID_ARG;
+  const int no = kmax - kmin + 1;
+  if (out_bytes < thoi_records_bytes(no, top_m) * (size_t)D) return THOI_ERR_INVALID_ARG;
+  // the batched kernels cover the FP32 path up to the register kernels' order
+  int top_k = 0;
+  for (int d = 0; d < D; d++) {
+    const int kk = kmax < ctxs[d]->N ? kmax : ctxs[d]->N;
+    top_k = kk > top_k ? kk : top_k;
+  }
+  if (prec != THOI_F32_FIX64 || top_k > KREG_MAX || D > 65535)
+    return batch_sequential(ctxs, D, kmin, kmax, out, stats, stream);
+  return batch_graph(ctxs, D, kmin, kmax, out, stats, stream);
+}
+
 // ------------------------------------------------------------------ API: autotune
 static void tune_load(const char* path, const char* gpu, int sms) {
   FILE* f = fopen(path, "r");
@@ -1050,6 +1525,7 @@ static void tune_load(const char* path, const char* gpu, int sms) {
     sh.blocks_per_sm = bps;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(gpu, sms, k, wide)] = sh;
+    g_tune_gen++;
   }
   fclose(f);
 }
@@ -1139,6 +1615,7 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(c->gpu_name, c->num_sms, k, wide)] = best;
+    g_tune_gen++;
   }
   if (cache_path) tune_save(cache_path, c->gpu_name, c->num_sms);
   return THOI_OK;

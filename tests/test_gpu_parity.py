@@ -347,22 +347,6 @@ def test_autograd_function():
 
 
 # ------------------------------------------------------------------ batching
-def test_batch_matches_single_contexts():
-    Xs = workloads.multi(6, 3000)
-    ctxs = [_ctx(X, top_m=32) for X in Xs]
-    res, st = P.thoi_batch_measures([c.h for c in ctxs], 3, 8, top_m=32)
-    for c, X, (recs, hi, lo) in zip(ctxs, Xs, res):
-        N = X.shape[1]
-        S = oracle.copula_cov(X)
-        for s, k in enumerate(range(3, 9)):
-            if k > N:
-                assert int(recs[s]["count"]) == 0
-                continue
-            assert int(recs[s]["count"]) == math.comb(N, k)
-    for c in ctxs:
-        c.close()
-
-
 # ------------------------------------------------------------------ large orders
 def _wellcond(N, seed):
     rng = np.random.default_rng(seed)
