@@ -281,6 +281,34 @@ thoi_status thoi_order_record_noalloc(const double* Sigma, int64_t N, int32_t k,
                                       thoi_order_record* rec_out, thoi_top_entry* top_out,
                                       void* stream);
 
+/* Host-only sharding helpers (no device work, no CUDA calls).  Nplets are
+ * independent (Methods, "Parallel and batched computation of HOI"), so one
+ * request splits into contiguous global-id ranges evaluated by separate
+ * processes, one GPU each, whose per-order records are merged once.
+ *
+ * thoi_partition: bounds[0..R] (caller-owned, R + 1 entries) with bounds[0] = 0,
+ * bounds[R] = thoi_count(N, orders, n_orders), non-decreasing, such that range
+ * r = [bounds[r], bounds[r+1]) holds about 1/R of the work, a nplet of order
+ * k weighing 2/3 k^3 + 2 k^2 (one LDL^T, one unit-lower inverse, the inverse
+ * diagonal).  Exact integer arithmetic: the same bounds on every host.
+ * THOI_ERR_INVALID_ARG for N outside 1..64, an order outside 1..N, R < 1 or a
+ * null pointer. */
+thoi_status thoi_partition(int64_t N, const int32_t* orders, int32_t n_orders, int32_t R,
+                           uint64_t* bounds);
+
+/* thoi_merge_records: merge R per-order record blocks produced for disjoint id
+ * ranges of one request (same orders, same top_m).  in holds the R blocks back
+ * to back, each thoi_records_bytes(n_orders, top_m) bytes in the layout
+ * thoi_measures writes; out (caller-owned, one block) receives: counts summed,
+ * min/max with the smallest id on ties, means weighted by the valid counts
+ * (count - n_not_pd), and each top list re-selected from the union of the
+ * ranks' lists by (value, id) (the union holds the global top-M, because
+ * every global top-M entry is in its own range's top-M).  Host memory only.
+ * THOI_ERR_INVALID_ARG when the blocks disagree on an order or an argument is
+ * out of range. */
+thoi_status thoi_merge_records(const void* in, int32_t R, int32_t n_orders, int32_t top_m,
+                               void* out);
+
 /* Human-readable name of a status. */
 const char* thoi_status_string(thoi_status s);
 

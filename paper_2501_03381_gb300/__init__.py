@@ -107,6 +107,8 @@ def load(build_if_missing: bool = True):
             "thoi_autotune": (ctypes.c_int, [vp, i32, i32, ctypes.c_char_p, vp]),
             "thoi_set_cancel": (ctypes.c_int, [vp, i32]),
             "thoi_order_record_noalloc": (ctypes.c_int, [vp, i64, i32, i32, vp, vp, vp]),
+            "thoi_partition": (ctypes.c_int, [i64, vp, i32, i32, vp]),
+            "thoi_merge_records": (ctypes.c_int, [vp, i32, i32, i32, vp]),
             "thoi_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -187,6 +189,29 @@ def make_options(precision: str | int = "f32_fix64", pivot_tau: float | None = N
 def thoi_count(N: int, orders) -> int:
     o = _orders_arr(orders)
     return int(load().thoi_count(N, _ptr(o), len(o)))
+
+
+def thoi_partition(N: int, orders, R: int) -> np.ndarray:
+    """R + 1 id bounds splitting the request into ranges of equal work."""
+    o = _orders_arr(orders)
+    b = np.zeros(R + 1, dtype=np.uint64)
+    _check(load().thoi_partition(N, _ptr(o), len(o), R, _ptr(b)), "thoi_partition")
+    return b
+
+
+def thoi_merge_records(blocks, n_orders: int, top_m: int) -> np.ndarray:
+    """Merge per-order record blocks of disjoint id ranges (host bytes, one
+    block per range, each thoi_records_bytes(n_orders, top_m) long)."""
+    per = thoi_records_bytes(n_orders, top_m)
+    raw = np.ascontiguousarray(np.concatenate([np.asarray(b).view(np.uint8).ravel()
+                                               for b in blocks]))
+    R = len(blocks)
+    if raw.nbytes != R * per:
+        raise ValueError("record blocks have the wrong size")
+    out = np.zeros(per, dtype=np.uint8)
+    _check(load().thoi_merge_records(_ptr(raw), R, n_orders, top_m, _ptr(out)),
+           "thoi_merge_records")
+    return out
 
 
 def thoi_unrank(N: int, orders, gid: int):

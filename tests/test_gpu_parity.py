@@ -446,3 +446,27 @@ def test_all_lane_shapes_agree(k, tmp_path):
                 out, _ = c.measures(orders, a, b)
                 np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL32)
         _force_shape(c.h, k, 0, 1 if k <= 20 else 2, 8, str(tmp_path / "f.json"))
+
+
+# ------------------------------------------------------------------ id-range sharding
+def test_virtual_ranks_partition_and_merge():
+    # R "ranks" on one GPU: each reduces its id range of the fMRI-shaped
+    # request, the host merge of their records equals the whole-range records
+    from records_pack import assert_same
+    X, orders = workloads.fmri_like()
+    top_m = 64
+    with _ctx(X, top_m=top_m) as c:
+        per = P.thoi_records_bytes(len(orders), top_m)
+        def rec_bytes(a, b):
+            out = np.zeros(per, dtype=np.uint8)
+            P.thoi_measures(c.h, orders, a, b, kind=1, out=out, top_m=top_m)
+            return out
+        total = P.thoi_count(20, orders)
+        whole = rec_bytes(0, total)
+        for R in (2, 5):
+            b = [int(x) for x in P.thoi_partition(20, orders, R)]
+            blocks = [rec_bytes(b[r], b[r + 1]) for r in range(R)]
+            merged = P.thoi_merge_records(blocks, len(orders), top_m)
+            # extremes, ids and top lists are identical; the means differ by
+            # the order of the compensated FP32 block sums only
+            assert_same(merged, whole, len(orders), top_m, mean_atol=1e-7)
