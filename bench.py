@@ -42,6 +42,18 @@ def flops_model(k: int) -> float:
     return 2.0 / 3.0 * k ** 3 + 2.0 * k ** 2
 
 
+# DRAM bytes per nplet of the FP32 nplet kernels, from the ncu capture of the
+# order-16 kernel on this workload (dram__bytes_read.sum + dram__bytes_write.sum
+# = 1.943 GB for 145,422,675 nplets); traffic grows with the nplets written.
+TRAFFIC_BYTES_PER_NPLET = 13.36
+
+
+def grad_flops_model(k: int) -> float:
+    # forward factor and inverse (flops_model) + P = W^T W (k^3/3) +
+    # Q = P diag(1/p) P (k^3) per nplet
+    return flops_model(k) + k ** 3 / 3.0 + k ** 3
+
+
 def total_nplets(N=N_VARS, orders=ORDERS):
     return sum(math.comb(N, k) for k in orders)
 
@@ -59,6 +71,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the adjoint and multi-dataset measurements")
     ap.add_argument("--only-order", type=int, default=0,
                     help="profiling aid: run the per-order reduction of one order a few "
                          "times and exit (for ncu captures of one kernel)")
@@ -324,7 +338,11 @@ def run_ours(args, rank, world, local_rank):
                    "replicas": "one independent dataset per rank",
                    "tuned_shapes_k_lanes_chunk": shapes},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": TRAFFIC_BYTES_PER_NPLET * total_nplets(),
+                     "traffic_basis": "per-step DRAM bytes of the FP32 nplet kernels, scaled by "
+                                      "nplets from the ncu capture of the order-16 kernel "
+                                      "(13.36 B per nplet)",
                      "kernel": "FP32 nplet kernels (k_nplet_reg<k>, k_nplet_gen), CUDA events",
                      "flops_per_step": f_total, "kernel_ms_per_step": kern_s * 1e3,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
@@ -336,6 +354,8 @@ def run_ours(args, rank, world, local_rank):
         "refactor_ms_per_step": sum(ref_ms) / len(ref_ms),
         "fp64_path": fp64,
     }
+    if not args.no_extra:
+        line["other_workloads"] = run_extra(args, dev, stream, flush, peak, rank)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -343,6 +363,106 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.destroy_process_group()
     return 0
+
+# ------------------------------------------------------------------ adjoint and batching
+def run_extra(args, dev, stream, flush, peak, rank):
+    """The adjoint (N=60, T=2000, orders 3..5) and the 64-dataset batch
+    (N ~ U{10..40}, T ~ U{200..2000}, orders 3..min(N,8)), each timed with
+    CUDA events after warm-up, with its FP32 roofline and the oracle beside
+    it (rank 0)."""
+    import numpy as np
+    import torch
+
+    import paper_2501_03381_gb300 as P
+    import workloads
+    out = {}
+    steps = max(3, args.steps)
+
+    def ev_time(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts)
+
+    # adjoint: dL/dSigma of L = sum of O over every nplet of orders 3..5
+    X, orders = workloads.grad60()
+    Nv = X.shape[1]
+    G = torch.empty((Nv, Nv), dtype=torch.float32, device=dev)
+    with P.Context(torch.as_tensor(X, device=dev)) as c:
+        ms = ev_time(lambda: P.thoi_measures_grad(c.h, orders, "O", out=G))
+    n = total_nplets(Nv, orders)
+    fl = sum(math.comb(Nv, k) * grad_flops_model(k) for k in orders)
+    ach = fl / (ms / 1e3) / 1e12
+    entry = {"workload": "N=60, T=2000 random-correlation Gaussian, L = sum of O over orders "
+                         "3..5 (5,983,367 nplets), dL/dSigma (60x60) with the FP64 re-factor",
+             "value": n / (ms / 1e3), "unit": "nplets/s", "ms_per_call": ms,
+             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                          "frac": ach / peak, "flops_per_call": fl,
+                          "flops_model": "2/3k^3+2k^2 forward + 4/3k^3 adjoint per nplet"}}
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        S = oracle.copula_cov(X)
+        t0 = time.perf_counter()
+        oracle.grad(S, orders, "O")
+        dt = time.perf_counter() - t0
+        entry["cpu_baseline"] = {"value": n / dt, "unit": "nplets/s", "cores": os.cpu_count(),
+                                 "kind": "oracle",
+                                 "sample": f"the whole workload ({n:,} nplets), {dt:.2f} s"}
+    out["adjoint_grad60"] = entry
+
+    # 64 datasets through one graph of batched launches
+    Xs, ords = workloads.multi64()
+    ctxs = [P.Context(torch.as_tensor(Xd, device=dev), top_m=TOP_M) for Xd in Xs]
+    prof = P.Context(torch.as_tensor(Xs[0], device=dev), top_m=TOP_M, profile=True)
+    hs = [prof.h] + [c.h for c in ctxs[1:]]
+    try:
+        ms = ev_time(lambda: P.thoi_batch_measures(hs, 3, 8, top_m=TOP_M))
+        _, st = P.thoi_batch_measures(hs, 3, 8, top_m=TOP_M)
+        graph_ms = st.nplet_ms
+        launches = st.launches
+    finally:
+        for c in ctxs + [prof]:
+            c.close()
+    n = sum(math.comb(Xd.shape[1], k) for Xd, o in zip(Xs, ords) for k in o)
+    fl = sum(math.comb(Xd.shape[1], k) * flops_model(k) for Xd, o in zip(Xs, ords) for k in o)
+    ach = fl / (graph_ms / 1e3) / 1e12
+    entry = {"workload": "64 datasets, N ~ U{10..40}, T ~ U{200..2000} (seeds 3000+d), orders "
+                         f"3..min(N,8) ({n:,} nplets), per-order records with top-256 lists, "
+                         "one replayed CUDA graph",
+             "value": n / (ms / 1e3), "unit": "nplets/s", "ms_per_call": ms,
+             "graph_ms": graph_ms, "gpu_launches_per_call": launches,
+             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                          "frac": ach / peak, "flops_per_call": fl,
+                          "kernel": "whole graph (nplet, reduction, re-factor, merge)"}}
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        rng = np.random.default_rng(5)
+        counts = [sum(math.comb(Xd.shape[1], k) for k in o) for Xd, o in zip(Xs, ords)]
+        m = 400000
+        done, dt = 0, 0.0
+        for Xd, o, cnt in zip(Xs, ords, counts):
+            q = max(1, int(round(m * cnt / n)))
+            ids = np.sort(rng.integers(0, cnt, q, dtype=np.uint64))
+            S = oracle.copula_cov(Xd)
+            t0 = time.perf_counter()
+            oracle.measures_ids(S, o, ids)
+            dt += time.perf_counter() - t0
+            done += q
+        entry["cpu_baseline"] = {"value": done / dt, "unit": "nplets/s", "cores": os.cpu_count(),
+                                 "kind": "oracle",
+                                 "sample": f"{done} nplet ids drawn uniformly per dataset "
+                                           f"(seed 5), in proportion to its nplets; {dt:.2f} s"}
+    out["multi_dataset_64"] = entry
+    return out
 
 
 def main():

@@ -1,9 +1,9 @@
 // Multi-dataset batch: dispatch of the batched FP32 nplet kernel by order,
 // and the batched reduction, FP64 re-factor and list-reduction kernels.  The
-// bodies are those of the single-dataset kernels (reduce_core, f64s_body);
-// here a block finds its dataset, order and range from descriptors in device
-// memory instead of from launch arguments, so that one launch covers every
-// dataset of the batch.
+// bodies are those of the single-dataset kernels (reduce_core, f64s_body,
+// f64g_body); here a block finds its dataset, order and range from
+// descriptors in device memory instead of from launch arguments, so that one
+// launch covers every dataset of the batch.
 #include <type_traits>
 
 #include "nplet_f64.cuh"
@@ -85,7 +85,7 @@ cudaError_t launch_reduce_batch(const float* basis, unsigned long long bstride,
 // ------------------------------------------------------------------ FP64 re-factor
 // Block (x, y) re-factors list entries x, x + gridDim.x, ... (times NT) of
 // slot slot0 + y in FP64 and writes their basis triples.
-template <int NT, typename M>
+template <int NT, int G, typename M>
 __global__ void __launch_bounds__(NT) k_refactor_batch(
     const BatchDataset* __restrict__ ds, const BatchSlot* __restrict__ slots, int slot0,
     const unsigned long long* __restrict__ binom, const unsigned long long* flag_ids,
@@ -121,23 +121,25 @@ __global__ void __launch_bounds__(NT) k_refactor_batch(
   a.flag_cap = sl.flag_cap;
   a.status = status;
   a.cancel = nullptr;
-  f64s_body<NT, true, M>(a, b64 + sl.flag_off, lstride, smem);
+  if constexpr (G == 1) f64s_body<NT, true, M>(a, b64 + sl.flag_off, lstride, smem);
+  else f64g_body<NT, G, true, M>(a, b64 + sl.flag_off, lstride, smem);
 }
 
-template <int NT, typename M>
+template <int G, typename M>
 static cudaError_t refactor_batch_t(const BatchDataset* ds, const BatchSlot* slots, int slot0,
                                     int n_slots, const unsigned long long* binom,
                                     const unsigned long long* flag_ids,
                                     unsigned long long* flag_counts, double* b64,
                                     unsigned long long lstride, int* status, int bx, size_t sm,
                                     cudaStream_t s) {
+  constexpr int NT = 128;
   int occ = 0;
-  cudaError_t e = occupancy_cached((const void*)k_refactor_batch<NT, M>, NT, sm, &occ);
+  cudaError_t e = occupancy_cached((const void*)k_refactor_batch<NT, G, M>, NT, sm, &occ);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)bx, (unsigned)n_slots);
-  k_refactor_batch<NT, M><<<grid, NT, sm, s>>>(ds, slots, slot0, binom, flag_ids, flag_counts,
-                                               b64, lstride, status);
+  k_refactor_batch<NT, G, M><<<grid, NT, sm, s>>>(ds, slots, slot0, binom, flag_ids, flag_counts,
+                                                  b64, lstride, status);
   return cudaGetLastError();
 }
 
@@ -150,18 +152,20 @@ cudaError_t launch_refactor_batch(const BatchDataset* ds, const BatchSlot* slots
                                   cudaStream_t s) {
   if (n_slots <= 0) return cudaSuccess;
   if (bx < 1 || n_slots > 65535) return cudaErrorInvalidValue;
-  size_t sm = 0;
-  const int nt = f64s_threads(maxN, k, &sm);
-  if (nt == 0) return cudaErrorInvalidValue;
-#define RB(NTV)                                                                                \
-  (wide ? refactor_batch_t<NTV, unsigned long long>(ds, slots, slot0, n_slots, binom, flag_ids, \
-                                                    flag_counts, b64, lstride, status, bx, sm,   \
-                                                    s)                                           \
-        : refactor_batch_t<NTV, unsigned>(ds, slots, slot0, n_slots, binom, flag_ids,            \
-                                          flag_counts, b64, lstride, status, bx, sm, s))
-  if (nt == 128) return RB(128);
-  if (nt == 64) return RB(64);
-  return RB(32);
+  // shared memory sized for the largest N (the layout grows with N)
+  const F64Cfg c = f64_config(maxN, k);
+#define RB(GG)                                                                                 \
+  case GG:                                                                                     \
+    return wide ? refactor_batch_t<GG, unsigned long long>(ds, slots, slot0, n_slots, binom,   \
+                                                           flag_ids, flag_counts, b64, lstride, \
+                                                           status, bx, c.smem, s)              \
+                : refactor_batch_t<GG, unsigned>(ds, slots, slot0, n_slots, binom, flag_ids,   \
+                                                 flag_counts, b64, lstride, status, bx, c.smem, \
+                                                 s);
+  switch (c.G) {
+    RB(1) RB(2) RB(4) RB(8) RB(16) RB(32)
+    default: return cudaErrorInvalidValue;
+  }
 #undef RB
 }
 

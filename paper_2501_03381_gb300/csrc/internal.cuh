@@ -138,7 +138,14 @@ cudaError_t launch_reduce_list64(const double* basis, unsigned long long stride_
                                  unsigned long long cap, Combine cmb, int top_m, PartRec* part,
                                  TopEnt* part_top, int num_sms, int max_blocks, cudaStream_t s,
                                  int* grid_out);
-// FP64 kernel with shared-memory matrices; threads per block that fit (0: none)
+// FP64 kernels with shared-memory matrices: one thread per nplet (G = 1) or
+// G lanes per nplet, 128 threads per block.
+struct F64Cfg {
+  int G;
+  size_t smem;
+};
+F64Cfg f64_config(int N, int k);
+// Nplets per block of the FP64 shared-memory kernel for (N, k) (never 0).
 int f64s_threads(int N, int k, size_t* smem_out);
 cudaError_t launch_nplet_f64s(const NpletArgs& a, bool list, double* b64,
                               unsigned long long bstride, int num_sms, cudaStream_t s,

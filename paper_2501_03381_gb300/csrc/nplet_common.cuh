@@ -69,6 +69,12 @@ __device__ __forceinline__ void renorm(double& P, int& E, bool& bad) {
   E += ex - 1023;
   P = __longlong_as_double((b & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
 }
+// NaN test in the value's own precision.  (The library isnan may promote a
+// float to double, and a float-to-double conversion runs on the narrow FP64
+// pipe of this GPU: one per element bounded the streaming reduction.)
+template <typename V>
+__device__ __forceinline__ bool is_nan(V x) { return x != x; }
+
 // Reciprocal by the hardware approximation (about 1 ulp), one instruction.
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;

@@ -1,10 +1,11 @@
 // FP64 nplet kernel: the THOI_F64 path and the re-factor of the nplets the
-// FP32 path flagged.  One nplet per thread; each thread's k x k matrix lives
-// in shared memory, interleaved across the block (entry e of thread t at
-// mat[e * NT + t], so a warp's accesses to "its" entry are consecutive).
-// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU, so
-// shared-memory bandwidth is ample; what matters is latency, and shared
-// memory keeps it far below that of per-thread local arrays.
+// FP32 path flagged.  Matrices live in shared memory: for small orders one
+// nplet per thread (each thread's k x k matrix interleaved across the block,
+// entry e of thread t at mat[e * NT + t]); for large orders G lanes share one
+// nplet's matrix (f64g_body), so that a block still holds enough warps to
+// keep the FP64 pipe busy.  FP64 arithmetic runs at a small fraction of the
+// FP32 rate on this GPU, so shared-memory bandwidth is ample; what matters is
+// latency and the number of resident warps.
 //
 // Same quantities as the FP32 kernels: R_S = Lh D Lh^T, log det R_S =
 // sum log D_p, the unit-lower inverse V column by column, and
@@ -14,27 +15,59 @@
 
 namespace thoi {
 
-template <int NT, bool LIST, typename M>
+template <int NT, int G, bool LIST, typename M>
 __global__ void __launch_bounds__(NT) k_nplet_f64s(const NpletArgs a, double* __restrict__ b64,
                                                    unsigned long long bstride) {
   extern __shared__ __align__(16) unsigned char smem[];
-  f64s_body<NT, LIST, M>(a, b64, bstride, smem);
+  if constexpr (G == 1) f64s_body<NT, LIST, M>(a, b64, bstride, smem);
+  else f64g_body<NT, G, LIST, M>(a, b64, bstride, smem);
 }
 
-template <int NT, bool LIST>
+// Lanes per nplet and shared memory for (N, k): one thread per nplet while a
+// block of 128 matrices stays within F64_SMEM_TARGET (three or more blocks,
+// twelve or more warps per SM), else the fewest lanes per nplet that do.
+constexpr size_t F64_SMEM_TARGET = 72 * 1024;
+constexpr int F64_NT = 128;
+
+F64Cfg f64_config(int N, int k) {
+  F64Cfg c;
+  const SmemLayout L = smem_layout(N, k, row_stride(N), sizeof(double), 8, 0);
+  const size_t s1 = L.total + (size_t)(k * (k + 1) / 2) * sizeof(double) * F64_NT;
+  if (s1 <= F64_SMEM_TARGET) {
+    c.G = 1;
+    c.smem = s1;
+    return c;
+  }
+  for (int G = 2; G <= 32; G <<= 1) {
+    const size_t sg = f64g_smem(N, k, F64_NT, G);
+    if (sg <= F64_SMEM_TARGET || G == 32) {
+      c.G = G;
+      c.smem = sg;
+      return c;
+    }
+  }
+  c.G = 32;
+  c.smem = f64g_smem(N, k, F64_NT, 32);
+  return c;
+}
+
+template <int G, bool LIST>
 static cudaError_t launch_f64s_t(const NpletArgs& a, double* b64, unsigned long long bstride,
                                  size_t sm, int num_sms, cudaStream_t s, int* grid_out,
                                  int max_blocks) {
+  constexpr int NT = F64_NT;
   void (*fn)(const NpletArgs, double*, unsigned long long);
-  if (a.N > 32) fn = k_nplet_f64s<NT, LIST, unsigned long long>;
-  else fn = k_nplet_f64s<NT, LIST, unsigned>;
+  if (a.N > 32) fn = k_nplet_f64s<NT, G, LIST, unsigned long long>;
+  else fn = k_nplet_f64s<NT, G, LIST, unsigned>;
   int occ = 0;
   cudaError_t e = occupancy_cached((const void*)fn, NT, sm, &occ);
   if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)num_sms * occ;
   if (!LIST) {
     const unsigned long long n = a.rank_end - a.rank_begin;
-    const long long need = (long long)((n + NT - 1) / NT);
+    const unsigned long long per_block = NT / G;
+    const long long need = (long long)((n + per_block - 1) / per_block);
     if (need < grid) grid = need > 0 ? need : 1;
   }
   if (grid > max_blocks) grid = max_blocks;
@@ -43,20 +76,12 @@ static cudaError_t launch_f64s_t(const NpletArgs& a, double* b64, unsigned long 
   return cudaGetLastError();
 }
 
-// Threads per block so that the block's matrices fit in shared memory; 0 if
-// even 32 matrices do not fit (the caller then uses the generic kernel).
+// Kept for the callers that ask whether the shared-memory FP64 kernels cover
+// (N, k): they always do (up to 32 lanes per nplet).
 int f64s_threads(int N, int k, size_t* smem_out) {
-  const SmemLayout L = smem_layout(N, k, row_stride(N), sizeof(double), 8, 0);
-  const size_t per = (size_t)(k * (k + 1) / 2) * sizeof(double);
-  const size_t budget = 220 * 1024;
-  for (int nt = 128; nt >= 32; nt >>= 1) {
-    const size_t sm = L.total + per * nt;
-    if (sm <= budget) {
-      if (smem_out) *smem_out = sm;
-      return nt;
-    }
-  }
-  return 0;
+  const F64Cfg c = f64_config(N, k);
+  if (smem_out) *smem_out = c.smem;
+  return F64_NT / c.G;
 }
 
 // mode 0: five measures per nplet (SoA, per opt.out_f64); mode 2: basis
@@ -65,17 +90,18 @@ int f64s_threads(int N, int k, size_t* smem_out) {
 cudaError_t launch_nplet_f64s(const NpletArgs& a, bool list, double* b64,
                               unsigned long long bstride, int num_sms, cudaStream_t s,
                               int* grid_out, int max_blocks) {
-  size_t sm = 0;
-  const int nt = f64s_threads(a.N, a.k, &sm);
-  if (nt == 0) return cudaErrorInvalidValue;
-  if (list) {
-    if (nt == 128) return launch_f64s_t<128, true>(a, b64, bstride, sm, num_sms, s, grid_out, max_blocks);
-    if (nt == 64) return launch_f64s_t<64, true>(a, b64, bstride, sm, num_sms, s, grid_out, max_blocks);
-    return launch_f64s_t<32, true>(a, b64, bstride, sm, num_sms, s, grid_out, max_blocks);
+  const F64Cfg c = f64_config(a.N, a.k);
+#define F64_CASE(GG)                                                                          \
+  case GG:                                                                                    \
+    return list ? launch_f64s_t<GG, true>(a, b64, bstride, c.smem, num_sms, s, grid_out,      \
+                                          max_blocks)                                         \
+                : launch_f64s_t<GG, false>(a, b64, bstride, c.smem, num_sms, s, grid_out,     \
+                                           max_blocks);
+  switch (c.G) {
+    F64_CASE(1) F64_CASE(2) F64_CASE(4) F64_CASE(8) F64_CASE(16) F64_CASE(32)
+    default: return cudaErrorInvalidValue;
   }
-  if (nt == 128) return launch_f64s_t<128, false>(a, b64, bstride, sm, num_sms, s, grid_out, max_blocks);
-  if (nt == 64) return launch_f64s_t<64, false>(a, b64, bstride, sm, num_sms, s, grid_out, max_blocks);
-  return launch_f64s_t<32, false>(a, b64, bstride, sm, num_sms, s, grid_out, max_blocks);
+#undef F64_CASE
 }
 
 }  // namespace thoi

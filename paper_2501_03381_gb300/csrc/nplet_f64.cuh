@@ -95,3 +95,156 @@ __device__ void f64s_body(const NpletArgs& a, double* __restrict__ b64, unsigned
 }
 
 }  // namespace thoi
+
+namespace thoi {
+
+// FP64 nplet computation with G lanes per nplet: the group's k x k matrix
+// (lower triangle) and index list live in shared memory, rows are owned
+// cyclically (row i by lane i mod G), and the lanes meet at a warp barrier
+// after every elimination step.  With one nplet per thread a block of
+// large-order matrices fills the shared memory with one or two warps, which
+// leaves schedulers without FP64 work; sharing a matrix among G lanes gives
+// G times as many warps for the same shared memory.
+//
+//   LDL^T, right-looking: step p updates the owned rows i > p with the
+//     unscaled column p, then (after a barrier) scales the owned column
+//     entries to L^_ip and stores 1/D_p on the diagonal.
+//   V = L^-1 (unit lower), right-looking and in place: step m subtracts
+//     L^_im times the finished row m from every owned row i > m; entry
+//     (i, m) becomes -L^_im, and row i is final after step i - 1.
+//   p_j = 1/D_j + sum_{i>j} V_ij^2 / D_i, column j by lane j mod G; the
+//     product of the p_j and the sum of log Sigma_ii are combined across the
+//     group with shuffles.
+template <int NT, int G, bool LIST, typename M>
+__device__ void f64g_body(const NpletArgs& a, double* __restrict__ b64, unsigned long long bstride,
+                          unsigned char* smem) {
+  constexpr int GPB = NT / G;  // nplets per block at a time
+  const int N = a.N, k = a.k, ldr = row_stride(N);
+  const SmemLayout L = smem_layout(N, k, ldr, sizeof(double), 8, 0);
+  load_tables<double>(a, smem, L, a.R64);
+  const unsigned long long* sb = reinterpret_cast<const unsigned long long*>(smem + L.binom);
+  const double* sR = reinterpret_cast<const double*>(smem + L.R);
+  const double* sls = reinterpret_cast<const double*>(smem + L.ls);
+  const int tri = k * (k + 1) / 2;
+  const int lane = threadIdx.x & 31, g = lane % G, grp = threadIdx.x / G;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - g));
+  double* A = reinterpret_cast<double*>(smem + L.total) + (size_t)grp * tri;
+  int* C = reinterpret_cast<int*>(smem + L.total + (size_t)GPB * tri * sizeof(double)) + grp * k;
+#define AG(i, j) A[((((i) * ((i) + 1)) >> 1) + (j))]
+  const CombineV<double> cmbv(a.cmb);
+  unsigned long long n;
+  if (LIST) {
+    const unsigned long long c = *a.flag_count;
+    n = c < a.flag_cap ? c : a.flag_cap;
+  } else {
+    n = a.rank_end - a.rank_begin;
+  }
+  for (unsigned long long e = (unsigned long long)blockIdx.x * GPB + grp; e < n;
+       e += (unsigned long long)gridDim.x * GPB) {
+    unsigned long long r, gid;
+    if (LIST) {
+      gid = a.flag_ids[e];
+      r = gid - a.id_base;
+    } else {
+      r = a.rank_begin + e;
+      gid = a.id_base + r;
+    }
+    // indices (every lane decodes, lane g stores the positions it owns)
+    M m = unrank_s<M>(r, k, N, sb, k + 1);
+    for (int q = 0; q < k; q++) {
+      const int hb = hibit(m);
+      m ^= (M)1 << hb;
+      if (q % G == g) C[q] = N - 1 - hb;
+    }
+    __syncwarp(gmask);
+    double lsum = 0.0;
+    for (int i = g; i < k; i += G) {
+      const int ci = C[i];
+      const double* row = sR + ci * ldr;
+      lsum += sls[ci];
+      for (int j = 0; j <= i; j++) AG(i, j) = row[C[j]];
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) lsum += __shfl_xor_sync(gmask, lsum, o);
+    __syncwarp(gmask);
+    // LDL^T
+    double P1 = 1.0;
+    int E1 = 0;
+    bool bad = false;
+    for (int p = 0; p < k; p++) {
+      const double d = AG(p, p);
+      bad |= !(d > 0.0);
+      P1 *= d;
+      if ((p & 7) == 7 || p == k - 1) renorm(P1, E1, bad);
+      const double rd = 1.0 / d;
+      const int i0 = p + 1 + ((g - (p + 1) % G) + G) % G;  // first owned row > p
+      for (int i = i0; i < k; i += G) {
+        const double u = AG(i, p) * rd;
+        for (int j = p + 1; j <= i; j++) AG(i, j) = fma(-u, AG(j, p), AG(i, j));
+      }
+      __syncwarp(gmask);
+      for (int i = i0; i < k; i += G) AG(i, p) *= rd;
+      if (g == p % G) AG(p, p) = rd;
+      __syncwarp(gmask);
+    }
+    // V = L^-1 in place
+    for (int mm = 0; mm + 1 < k; mm++) {
+      const int i0 = mm + 1 + ((g - (mm + 1) % G) + G) % G;
+      for (int i = i0; i < k; i += G) {
+        const double l = AG(i, mm);
+        for (int c = 0; c < mm; c++) AG(i, c) = fma(-l, AG(mm, c), AG(i, c));
+        AG(i, mm) = -l;
+      }
+      __syncwarp(gmask);
+    }
+    // inverse diagonal, product of the p_j across the group
+    double P2 = 1.0;
+    int E2 = 0;
+    bool bad2 = false;
+    for (int j = g; j < k; j += G) {
+      double pj = AG(j, j);
+      for (int i = j + 1; i < k; i++) {
+        const double v = AG(i, j);
+        pj = fma(v * AG(i, i), v, pj);
+      }
+      P2 *= pj;
+      renorm(P2, E2, bad2);
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      const double q = __shfl_xor_sync(gmask, P2, o);
+      const int eq = __shfl_xor_sync(gmask, E2, o);
+      P2 *= q;
+      E2 += eq;
+      renorm(P2, E2, bad2);
+    }
+    bad |= __any_sync(gmask, bad2);
+    if (g == 0) {
+      const double lr = log_of(P1, E1), sp = log_of(P2, E2);
+      if (bad) atomicOr(a.status, ST_NOT_PD);
+      if (a.mode == 0) {
+        double v[5];
+        combine5<double>(lr, sp, lsum, cmbv, v);
+        if (bad)
+          for (int q = 0; q < 5; q++) v[q] = __longlong_as_double(0x7ff8000000000000ll);
+        store5<double>(a, gid, v);
+      } else {
+        b64[e] = bad ? __longlong_as_double(0x7ff8000000000000ll) : lr;
+        b64[bstride + e] = sp;
+        b64[2 * bstride + e] = lsum;
+      }
+    }
+    __syncwarp(gmask);
+  }
+#undef AG
+}
+
+// Shared memory of the grouped kernel for (N, k) with G lanes per nplet and
+// NT threads per block.
+__host__ __device__ inline size_t f64g_smem(int N, int k, int NT, int G) {
+  const SmemLayout L = smem_layout(N, k, row_stride(N), sizeof(double), 8, 0);
+  const size_t per = (size_t)(k * (k + 1) / 2) * sizeof(double) + (size_t)k * sizeof(int);
+  return L.total + per * (size_t)(NT / G) + 16;
+}
+
+}  // namespace thoi

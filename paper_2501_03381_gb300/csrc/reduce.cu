@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(SEED_NT) k_seed_thresholds(const float* __rest
         e = (unsigned long long)ch * (n - SEED_RUN) / (SEED_CHUNKS - 1) + off;
       }
       const float lr = blr[e];
-      if (!isnan(lr)) {
+      if (!is_nan(lr)) {
         const float sp = bsp[e];
         const float tc = -0.5f * lr + c.tc_c, dtc = 0.5f * (lr + sp) + c.dtc_c;
         o = tc - dtc;

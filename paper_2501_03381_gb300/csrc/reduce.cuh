@@ -89,7 +89,7 @@ __device__ void reduce_core(unsigned long long first, unsigned long long step,
 #pragma unroll
       for (int t = 0; t < RB_PER_THREAD; t++) {
         if (e0 + t >= n) continue;
-        if (isnan(lr[t])) {
+        if (is_nan(lr[t])) {
           notpd += nan_is_notpd ? 1u : 0u;
           continue;
         }
