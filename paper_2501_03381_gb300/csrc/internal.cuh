@@ -9,7 +9,8 @@
 namespace thoi {
 
 constexpr int NB = THOI_MAX_N + 1;  // side of the binomial table C(n, m), n, m <= 64
-constexpr int KREG_MAX = 20;        // largest order with a register-resident FP32 kernel
+constexpr int KREG_MAX = 24;        // largest order with a one-thread register FP32 kernel
+constexpr int KBATCH_MAX = 20;      // largest order of the batched register kernel
 constexpr int RED_NT = 128;         // threads per block of the nplet kernels
 constexpr int TOP_CAP = 2048;       // top-M candidate buffer per side (power of two)
 

@@ -1,6 +1,8 @@
 // Dispatch of the FP32 path by order: one-thread register kernels for
-// k <= 20, lane-group register kernels for 21 <= k <= 32 (2 lanes per nplet
-// up to 24, 4 lanes above), the generic kernel beyond.
+// k <= 24, lane-group register kernels for 13 <= k <= 32 (2 lanes per nplet
+// up to 24, 4 lanes from 21), the generic kernel beyond.  Without a tuned
+// shape, orders up to 20 use one thread per nplet, 21..24 two lanes, 25..32
+// four lanes.
 #include "internal.cuh"
 
 namespace thoi {
@@ -18,7 +20,7 @@ Shape default_shape(int k) {
   Shape s;
   s.blocks_per_sm = 0;
   s.chunk = 8;
-  s.lanes = k <= 20 ? 1 : (k <= 24 ? 2 : (k <= 32 ? 4 : 1));
+  s.lanes = k <= 24 ? 1 : (k <= 32 ? 4 : 1);
   return s;
 }
 
@@ -57,7 +59,7 @@ cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, c
   case KK: return launch_reg_k<KK>(a, sh, num_sms, s, grid_out, max_blocks);
     CASE_K(1) CASE_K(2) CASE_K(3) CASE_K(4) CASE_K(5) CASE_K(6) CASE_K(7) CASE_K(8) CASE_K(9)
     CASE_K(10) CASE_K(11) CASE_K(12) CASE_K(13) CASE_K(14) CASE_K(15) CASE_K(16) CASE_K(17)
-    CASE_K(18) CASE_K(19) CASE_K(20)
+    CASE_K(18) CASE_K(19) CASE_K(20) CASE_K(21) CASE_K(22) CASE_K(23) CASE_K(24)
 #undef CASE_K
     default: return launch_nplet_f32_gen(a, num_sms, s, grid_out, max_blocks);
   }

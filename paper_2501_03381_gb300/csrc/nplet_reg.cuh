@@ -1,5 +1,5 @@
 // Register-resident FP32 nplet kernel (templates), one template instance per order
-// k <= 20: each thread owns one nplet at a time, its k x k correlation
+// k <= 24: each thread owns one nplet at a time, its k x k correlation
 // submatrix lives in registers (packed lower triangle), and the Cholesky
 // factor, the triangular inverse and the leave-one-out diagonal are computed
 // in place with fully unrolled loops (Methods, "Parallel and batched
@@ -96,10 +96,11 @@ __device__ __forceinline__ void nplet_reg_one(M mask, int N, const float* sR, in
 // Minimum resident blocks per SM, picked per order by timing: orders up to
 // 16 are held to three blocks (at most 168 registers a thread), 18..20 to two;
 // order 17 keeps the allocation the compiler picks on its own (three blocks
-// spill there, two are slower than one).
+// spill there, two are slower than one), and so do 21..24, which reach the
+// 255-register limit and spill a little.
 template <int K>
 struct RegBlocks {
-  static constexpr int value = K <= 16 ? 3 : (K == 17 ? 1 : 2);
+  static constexpr int value = K <= 16 ? 3 : ((K == 17 || K > 20) ? 1 : 2);
 };
 
 template <int K, typename M>

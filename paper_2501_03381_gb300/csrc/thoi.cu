@@ -1496,7 +1496,7 @@ extern "C" thoi_status thoi_batch_measures(thoi_ctx* const* ctxs, int32_t D, int
     const int kk = kmax < ctxs[d]->N ? kmax : ctxs[d]->N;
     top_k = kk > top_k ? kk : top_k;
   }
-  if (prec != THOI_F32_FIX64 || top_k > KREG_MAX || D > 65535)
+  if (prec != THOI_F32_FIX64 || top_k > KBATCH_MAX || D > 65535)
     return batch_sequential(ctxs, D, kmin, kmax, out, stats, stream);
   return batch_graph(ctxs, D, kmin, kmax, out, stats, stream);
 }
@@ -1599,8 +1599,9 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
     double best_ms = -1.0;
     for (int lanes = 1; lanes <= 4; lanes <<= 1) {
       if (!shape_available(k, lanes)) continue;
-      if (lanes == 1 && k > 20 && shape_available(k, 2)) continue;  // generic kernel: never faster
-      if (lanes == 1 && k > 20 && shape_available(k, 4)) continue;
+      // above the one-thread register kernels, lanes = 1 is the generic
+      // kernel: never faster than a lane group
+      if (lanes == 1 && k > KREG_MAX && (shape_available(k, 2) || shape_available(k, 4))) continue;
       for (int chunk = 4; chunk <= 8; chunk <<= 1) {
         Shape sh;
         sh.lanes = lanes;
