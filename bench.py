@@ -42,16 +42,38 @@ def flops_model(k: int) -> float:
     return 2.0 / 3.0 * k ** 3 + 2.0 * k ** 2
 
 
-# DRAM bytes per nplet of the FP32 nplet kernels, from the ncu capture of the
-# order-16 kernel on this workload (dram__bytes_read.sum + dram__bytes_write.sum
-# = 1.943 GB for 145,422,675 nplets); traffic grows with the nplets written.
-TRAFFIC_BYTES_PER_NPLET = 13.36
+# DRAM bytes per nplet of the FP32 nplet kernels, from ncu captures of the
+# order-16 kernels on this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch / 145,422,675 nplets); traffic grows with
+# the nplets written.  None: not captured for the current kernel.
+TRAFFIC_BYTES_PER_NPLET = {"dense": 13.36, "prefix": 69.6}
 
 
 def grad_flops_model(k: int) -> float:
     # forward factor and inverse (flops_model) + P = W^T W (k^3/3) +
     # Q = P diag(1/p) P (k^3) per nplet
     return flops_model(k) + k ** 3 / 3.0 + k ** 3
+
+
+def prefix_level_flops(i: int) -> float:
+    # one bordered step onto i factored variables: forward and backward
+    # unit-triangular solves (i(i-1)/2 FMAs each), the new row and pivot
+    # (i FMUL + i FMA) and the inverse-diagonal update (i FMUL + i FMA)
+    return 2.0 * i * (i - 1) + 6.0 * i
+
+
+def prefix_order_flops(N: int, k: int) -> float:
+    # prefix-shared kernel: every (k-1)-prefix is built once (levels
+    # 0..k-2), every nplet is one final bordered step plus the product of its
+    # k inverse-diagonal entries
+    P = k - 1
+    per_prefix = sum(prefix_level_flops(i) for i in range(P))
+    per_nplet = prefix_level_flops(P) + 2.0 * P
+    return math.comb(N - 1, P) * per_prefix + math.comb(N, k) * per_nplet
+
+
+def order_flops(N: int, k: int, prefix: bool) -> float:
+    return prefix_order_flops(N, k) if prefix else math.comb(N, k) * flops_model(k)
 
 
 def total_nplets(N=N_VARS, orders=ORDERS):
@@ -78,6 +100,8 @@ def parse():
                          "times and exit (for ncu captures of one kernel)")
     ap.add_argument("--precision", default="f32_fix64", choices=["f32_fix64", "f64"],
                     help="precision of the --only-order runs")
+    ap.add_argument("--shape", default="",
+                    help="--only-order runs: launch shape 'lanes,chunk,prefix' (else built-in)")
     return ap.parse_args()
 
 
@@ -91,6 +115,17 @@ def run_only_order(args, local_rank):
     X, _ = workloads.planted30()
     with P.Context(torch.as_tensor(X, device="cuda"), precision=args.precision, top_m=TOP_M,
                    profile=True) as c:
+        if args.shape:
+            # load one launch shape for this order through the autotuner's cache file
+            lanes, chunk, prefix = (int(v) for v in args.shape.split(","))
+            props = torch.cuda.get_device_properties(local_rank)
+            ent = {"gpu": props.name, "sms": props.multi_processor_count, "k": args.only_order,
+                   "wide": 0, "lanes": lanes, "chunk": chunk, "blocks_per_sm": 0,
+                   "prefix": prefix}
+            path = os.path.join(tempfile.gettempdir(), f"thoi_shape_{os.getpid()}.json")
+            with open(path, "w") as fh:
+                fh.write("[\n" + json.dumps(ent) + "\n]\n")
+            P.thoi_autotune(c.h, args.only_order, args.only_order, path)
         for _ in range(max(1, args.steps)):
             (recs, _, _), st = c.measures([args.only_order], reduction="per_order")
     torch.cuda.synchronize()
@@ -273,7 +308,8 @@ def run_ours(args, rank, world, local_rank):
     finally:
         P.thoi_destroy(h)
     try:
-        shapes = {e["k"]: [e["lanes"], e["chunk"]] for e in json.load(open(tune_path))}
+        shapes = {e["k"]: [e["lanes"], e["chunk"], e.get("prefix", 0)]
+                  for e in json.load(open(tune_path))}
     except Exception:
         shapes = {}
     sampler = ClockSampler(local_rank)
@@ -321,8 +357,14 @@ def run_ours(args, rank, world, local_rank):
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_t) / len(e2e_t)
 
-    # roofline of the dominant kernels (the FP32 nplet kernels of all orders)
-    f_total = total_flops()
+    # roofline of the dominant kernels (the FP32 nplet kernels of all orders),
+    # each order counted with the work of the kernel the autotuner chose
+    f_total = sum(order_flops(N_VARS, k, bool(shapes.get(k, [1, 8, 0])[2])) for k in ORDERS)
+    f_dense = total_flops()
+    traffic = 0.0
+    for k in ORDERS:
+        b = TRAFFIC_BYTES_PER_NPLET["prefix" if shapes.get(k, [1, 8, 0])[2] else "dense"]
+        traffic = None if (traffic is None or b is None) else traffic + b * math.comb(N_VARS, k)
     kern_s = sum(nplet_ms) / len(nplet_ms) / 1e3
     achieved = f_total / kern_s / 1e12
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
@@ -339,12 +381,16 @@ def run_ours(args, rank, world, local_rank):
                    "tuned_shapes_k_lanes_chunk": shapes},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": TRAFFIC_BYTES_PER_NPLET * total_nplets(),
+                     "traffic": traffic,
                      "traffic_basis": "per-step DRAM bytes of the FP32 nplet kernels, scaled by "
-                                      "nplets from the ncu capture of the order-16 kernel "
-                                      "(13.36 B per nplet)",
-                     "kernel": "FP32 nplet kernels (k_nplet_reg<k>, k_nplet_gen), CUDA events",
+                                      "nplets from ncu captures of the order-16 kernels "
+                                      f"(B per nplet: {TRAFFIC_BYTES_PER_NPLET})",
+                     "kernel": "FP32 nplet kernels (k_nplet_reg, k_nplet_pfx, k_nplet_grp), CUDA events",
                      "flops_per_step": f_total, "kernel_ms_per_step": kern_s * 1e3,
+                     "flops_model": "dense orders 2/3k^3+2k^2 per nplet; prefix-shared orders "
+                                    "(tuned_shapes third entry 1) one bordered build per "
+                                    "(k-1)-prefix plus one bordered step per nplet",
+                     "dense_equivalent_tflops": f_dense / kern_s / 1e12,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
         "e2e": {"value": n_total / e2e_s, "unit": "nplets/s",
                 "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(nb)},

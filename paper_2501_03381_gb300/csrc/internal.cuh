@@ -88,9 +88,12 @@ struct NpletArgs {
 cudaError_t occupancy_cached(const void* fn, int block, size_t smem, int* occ);
 struct Shape {
   int blocks_per_sm;  // 0 = occupancy maximum
-  int chunk;          // nplets per thread (or lane group) per round, 1..8
+  int chunk;          // nplets (prefixes for the prefix-shared kernel) per thread per round, 1..8
   int lanes;          // lanes per nplet: 1 (one-thread kernel), 2 or 4 (lane-group kernel)
+  int prefix;         // 1: prefix-shared kernel (whole orders, KPFX_MIN <= k <= KPFX_MAX)
 };
+constexpr int KPFX_MIN = 3;   // orders with a prefix-shared kernel
+constexpr int KPFX_MAX = 20;
 // Built-in launch shape of the FP32 kernel for order k (used when no tuned
 // shape is cached).
 Shape default_shape(int k);

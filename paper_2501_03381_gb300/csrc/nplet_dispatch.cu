@@ -10,6 +10,9 @@ namespace thoi {
 template <int K>
 cudaError_t launch_reg_k(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                          int* grid_out, int max_blocks);
+template <int K>
+cudaError_t launch_pfx_k(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
+                         int* grid_out, int max_blocks);
 template <int K, int G>
 cudaError_t launch_grp_k(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                          int* grid_out, int max_blocks);
@@ -21,6 +24,7 @@ Shape default_shape(int k) {
   s.blocks_per_sm = 0;
   s.chunk = 8;
   s.lanes = k <= 24 ? 1 : (k <= 32 ? 4 : 1);
+  s.prefix = 0;
   return s;
 }
 
@@ -31,8 +35,28 @@ bool shape_available(int k, int lanes) {
   return false;
 }
 
+static unsigned long long binom_u(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  unsigned __int128 r = 1;
+  for (int i = 1; i <= k; i++) r = r * (unsigned)(n - k + i) / (unsigned)i;
+  return (unsigned long long)r;
+}
+
 cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                              int* grid_out, int max_blocks) {
+  // the prefix-shared kernel covers whole orders only
+  if (sh.prefix && a.k >= KPFX_MIN && a.k <= KPFX_MAX && a.rank_begin == 0 &&
+      a.rank_end == binom_u(a.N, a.k)) {
+    switch (a.k) {
+#define CASE_P(KK) \
+  case KK: return launch_pfx_k<KK>(a, sh, num_sms, s, grid_out, max_blocks);
+      CASE_P(3) CASE_P(4) CASE_P(5) CASE_P(6) CASE_P(7) CASE_P(8) CASE_P(9) CASE_P(10)
+      CASE_P(11) CASE_P(12) CASE_P(13) CASE_P(14) CASE_P(15) CASE_P(16) CASE_P(17) CASE_P(18)
+      CASE_P(19) CASE_P(20)
+#undef CASE_P
+      default: break;
+    }
+  }
   const int lanes = shape_available(a.k, sh.lanes) ? sh.lanes : default_shape(a.k).lanes;
   if (lanes == 2) {
     switch (a.k) {

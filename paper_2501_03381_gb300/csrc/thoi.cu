@@ -1519,10 +1519,14 @@ static void tune_load(const char* path, const char* gpu, int sms) {
                &sm, &k, &wide, &lanes, &chunk, &bps) != 6)
       continue;
     if (strcmp(g, gpu) != 0 || sm != sms || !shape_available(k, lanes)) continue;
+    int prefix = 0;
+    const char* pq = strstr(line, "\"prefix\"");
+    if (pq && sscanf(pq, "\"prefix\": %d", &prefix) != 1) prefix = 0;
     Shape sh;
     sh.lanes = lanes;
     sh.chunk = chunk;
     sh.blocks_per_sm = bps;
+    sh.prefix = prefix ? 1 : 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(gpu, sms, k, wide)] = sh;
     g_tune_gen++;
@@ -1542,9 +1546,9 @@ static void tune_save(const char* path, const char* gpu, int sms) {
     if (sscanf(kv.first.c_str(), "%255[^|]|%d|%d|%d", g, &sm, &k, &wide) != 4) continue;
     if (strcmp(g, gpu) != 0 || sm != sms) continue;
     fprintf(f, "%s{\"gpu\": \"%s\", \"sms\": %d, \"k\": %d, \"wide\": %d, \"lanes\": %d, "
-               "\"chunk\": %d, \"blocks_per_sm\": %d}",
+               "\"chunk\": %d, \"blocks_per_sm\": %d, \"prefix\": %d}",
             first ? "" : ",\n", g, sm, k, wide, kv.second.lanes, kv.second.chunk,
-            kv.second.blocks_per_sm);
+            kv.second.blocks_per_sm, kv.second.prefix);
     first = false;
   }
   fprintf(f, "\n]\n");
@@ -1607,7 +1611,24 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
         sh.lanes = lanes;
         sh.chunk = chunk;
         sh.blocks_per_sm = 0;
-        const double ms = time_shape(c, k, n, sh, s);
+        sh.prefix = 0;
+        const double ms = time_shape(c, k, n, sh, s) * (double)total / (double)n;
+        if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
+          best_ms = ms;
+          best = sh;
+        }
+      }
+    }
+    // the prefix-shared kernel covers whole orders: timed on the whole order
+    // when that is affordable (up to 2^28 nplets)
+    if (k >= KPFX_MIN && k <= KPFX_MAX && total <= (1ull << 28)) {
+      for (int chunk = 1; chunk <= 4; chunk <<= 1) {
+        Shape sh;
+        sh.lanes = 1;
+        sh.chunk = chunk;
+        sh.blocks_per_sm = 0;
+        sh.prefix = 1;
+        const double ms = time_shape(c, k, total, sh, s);
         if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
           best_ms = ms;
           best = sh;

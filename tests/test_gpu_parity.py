@@ -222,7 +222,7 @@ def test_not_positive_definite():
 
 
 # ------------------------------------------------------------------ reductions
-def _check_records(recs, hi, lo, ref_recs, tol, S, orders, top_m):
+def _check_records(recs, hi, lo, ref_recs, tol, S, orders, top_m, o_ref=None):
     """Per-order records against the oracle's reduction.  Values within tol;
     the reported ids must carry the reported extreme values (near-ties may
     pick a different but equally valid id)."""
@@ -247,8 +247,9 @@ def _check_records(recs, hi, lo, ref_recs, tol, S, orders, top_m):
         tv, _ = oracle.measures_ids(S, orders, np.concatenate([h["id"], l_["id"]]))
         np.testing.assert_allclose(tv[3], np.concatenate([h["value"], l_["value"]]), atol=tol)
         assert len(set(h["id"].tolist())) == n and len(set(l_["id"].tolist())) == n
-        # O < 0 count: exact up to nplets within tol of zero
-        near0 = 0
+        # O < 0 count: exact up to the nplets whose reference O lies within
+        # tol of zero (o_ref: the reference O values of this order, if given)
+        near0 = int((np.abs(o_ref[s_]) <= tol).sum()) if o_ref is not None else 0
         assert abs(int(r["count_neg_O"]) - e["neg_O"]) <= max(near0, e["count"] // 10 ** 5)
 
 
@@ -406,7 +407,10 @@ def test_autotune_cache_and_parity(tmp_path):
         ks = sorted(e["k"] for e in ents)
         assert ks == [12, 13, 14]
         for e in ents:
-            assert e["lanes"] in (1, 2) and e["chunk"] in (4, 8)
+            if e.get("prefix", 0):
+                assert e["lanes"] == 1 and e["chunk"] in (1, 2, 4)
+            else:
+                assert e["lanes"] in (1, 2) and e["chunk"] in (4, 8)
         # the tuned shapes compute the same measures
         total = oracle.count(30, orders)
         off = sum(math.comb(30, k) for k in range(3, 13))
@@ -419,13 +423,13 @@ def test_autotune_cache_and_parity(tmp_path):
         assert json.load(open(path)) == ents
 
 
-def _force_shape(h, k, wide, lanes, chunk, path):
+def _force_shape(h, k, wide, lanes, chunk, path, prefix=0):
     """Make the library use one launch shape for order k by loading it
     through the autotuner's cache file."""
     import json
     props = torch.cuda.get_device_properties(0)
     ent = {"gpu": props.name, "sms": props.multi_processor_count, "k": k, "wide": wide,
-           "lanes": lanes, "chunk": chunk, "blocks_per_sm": 0}
+           "lanes": lanes, "chunk": chunk, "blocks_per_sm": 0, "prefix": prefix}
     with open(path, "w") as fh:
         fh.write("[\n" + json.dumps(ent) + "\n]\n")
     P.thoi_autotune(h, k, k, path)
@@ -456,6 +460,12 @@ def test_virtual_ranks_partition_and_merge():
     X, orders = workloads.fmri_like()
     top_m = 64
     with _ctx(X, top_m=top_m) as c:
+        # one kernel for every range (the prefix-shared kernel covers whole
+        # orders only), so that the extremes compare bit for bit
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            for k in orders:
+                _force_shape(c.h, k, 0, 1, 8, f"{td}/d{k}.json", prefix=0)
         per = P.thoi_records_bytes(len(orders), top_m)
         def rec_bytes(a, b):
             out = np.zeros(per, dtype=np.uint8)
@@ -470,3 +480,39 @@ def test_virtual_ranks_partition_and_merge():
             # extremes, ids and top lists are identical; the means differ by
             # the order of the compensated FP32 block sums only
             assert_same(merged, whole, len(orders), top_m, mean_atol=1e-7)
+
+
+# ------------------------------------------------------------------ prefix-shared kernel
+@pytest.mark.parametrize("chunk", [1, 3])
+def test_prefix_kernel_every_order_matches_oracle(chunk, tmp_path):
+    # the prefix-shared kernel (bordered steps over a shared (k-1)-prefix) on
+    # every order of the fMRI-shaped workload, every nplet against the oracle
+    X, orders = workloads.fmri_like()
+    S = oracle.copula_cov(X)
+    with _ctx(X, out_f64=True) as c:
+        for k in orders:
+            _force_shape(c.h, k, 0, 1, chunk, str(tmp_path / f"p{k}.json"), prefix=1)
+            ref, _ = _refs(S, [k])
+            got, _ = c.measures([k])
+            np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=TOL32)
+
+
+def test_prefix_kernel_wide_masks_and_records(tmp_path):
+    # 64-bit masks (N = 40) and the records path, on a random correlation
+    # matrix whose O values are not crowded around zero
+    S = workloads.random_corr(np.random.default_rng(12), 40)
+    orders = [3, 4]
+    with _ctx(Sigma=S, out_f64=True, top_m=16) as c:
+        for k in orders:
+            _force_shape(c.h, k, 1, 1, 2, str(tmp_path / f"w{k}.json"), prefix=1)
+        for k in orders:
+            ref, _ = _refs(S, [k])
+            got, _ = c.measures([k])
+            np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=TOL32)
+        vals, fl = _refs(S, orders)
+        ids = np.arange(vals.shape[1], dtype=np.uint64)
+        ref_recs = oracle.reduce_per_order(40, orders, vals, ids, fl, top_m=16)
+        (recs, hi, lo), _ = c.measures(orders, reduction="per_order")
+        n3 = math.comb(40, 3)
+        _check_records(recs, hi, lo, ref_recs, TOL32, S, orders, 16,
+                       o_ref=[vals[3, :n3], vals[3, n3:]])
