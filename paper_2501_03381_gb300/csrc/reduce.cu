@@ -14,70 +14,152 @@
 
 namespace thoi {
 
-// Starting thresholds of the top-M buffers: the M-th largest and M-th
-// smallest O among a sample of the elements (SEED_CHUNKS runs of SEED_RUN
-// consecutive elements spread over the range).  The M-th best of any subset
-// is no better than the M-th best of the whole set, so every element of the
-// true top-M still passes; with the thresholds starting near their final
-// values, the blocks see few candidates and rarely compact.
+// Starting thresholds of the top-M buffers: the M-th largest and the M-th
+// smallest O of a sample of the range (SEED_RUNS runs of SEED_RUN
+// consecutive elements, evenly spaced).  The M-th best of any subset is no
+// better than the M-th best of the whole set, so every element of the true
+// top M still passes; started near their final values, the reduction blocks
+// see few candidates and sort little.  The M-th best is found by a radix
+// select on order-preserving integer keys: a histogram of the top 11 bits
+// picks the bin holding it, a histogram of the next 11 bits inside that bin
+// narrows it, and the lower edge of that 22-bit bin (at least M samples at
+// or above it) is the bound.
 constexpr int SEED_NT = 1024;
-constexpr int SEED_CHUNKS = 64;
 constexpr int SEED_RUN = 256;
-constexpr int SEED_S = SEED_CHUNKS * SEED_RUN;  // 16384 sampled elements
+constexpr int SEED_RUNS = 512;
+constexpr int SEED_S = SEED_RUN * SEED_RUNS;  // 131072 sampled elements
+constexpr int SEED_BINS = 2048;
+
+__device__ __forceinline__ unsigned fkey(float v) {
+  unsigned u = __float_as_uint(v);
+  if ((u << 1) == 0) u = 0;
+  return (u >> 31) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_value(unsigned k) {
+  return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Bin (counting from the top) in which the running count of a descending
+// scan of hist[SEED_BINS] reaches target; *above = count of the bins above
+// it.  Run by warp 0.
+__device__ void seed_find_bin(const unsigned* hist, unsigned target, int* bin, unsigned* above) {
+  const int lane = threadIdx.x & 31;
+  constexpr int PER = SEED_BINS / 32;
+  // lane l owns bins [SEED_BINS - (l+1) PER, SEED_BINS - l PER), top first
+  const int hi = SEED_BINS - lane * PER;
+  unsigned mine = 0;
+  for (int b = hi - 1; b >= hi - PER; b--) mine += hist[b];
+  unsigned incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const unsigned excl = incl - mine;
+  const bool here = excl < target && incl >= target;
+  const unsigned who = __ballot_sync(0xffffffffu, here);
+  if (who == 0) {
+    if (lane == 0) {
+      *bin = -1;
+      *above = 0;
+    }
+    return;
+  }
+  if (lane == __ffs(who) - 1) {
+    unsigned run = excl;
+    for (int b = hi - 1; b >= hi - PER; b--) {
+      if (run + hist[b] >= target) {
+        *bin = b;
+        *above = run;
+        break;
+      }
+      run += hist[b];
+    }
+  }
+}
 
 __global__ void __launch_bounds__(SEED_NT) k_seed_thresholds(const float* __restrict__ blr,
                                                              const float* __restrict__ bsp,
                                                              unsigned long long n, Combine cmb,
                                                              int top_m, float* __restrict__ thr) {
-  extern __shared__ __align__(16) float sv[];  // SEED_S values
-  __shared__ int s_valid;
+  __shared__ unsigned h[2][SEED_BINS];
+  __shared__ int s_bin[2];
+  __shared__ unsigned s_above[2];
+  __shared__ unsigned s_valid;
   const CombineV<float> c(cmb);
+  const unsigned long long S = n < (unsigned long long)SEED_S ? n : (unsigned long long)SEED_S;
+  auto sample_key = [&](int q, unsigned& kh, unsigned& kl) -> bool {
+    unsigned long long e;
+    if (n <= (unsigned long long)SEED_S) {
+      e = q;
+    } else {
+      const int run = q / SEED_RUN, off = q % SEED_RUN;
+      e = (unsigned long long)run * (n - SEED_RUN) / (SEED_RUNS - 1) + off;
+    }
+    const float lr = blr[e];
+    if (is_nan(lr)) return false;
+    const float sp = bsp[e];
+    const float tc = -0.5f * lr + c.tc_c, dtc = 0.5f * (lr + sp) + c.dtc_c;
+    kh = fkey(tc - dtc);  // largest O = largest key
+    kl = ~kh;             // smallest O = largest inverted key
+    return true;
+  };
+  for (int q = threadIdx.x; q < 2 * SEED_BINS; q += SEED_NT) (&h[0][0])[q] = 0;
   if (threadIdx.x == 0) s_valid = 0;
   __syncthreads();
-  const unsigned long long S = n < (unsigned long long)SEED_S ? n : (unsigned long long)SEED_S;
-  int valid = 0;
-  for (int q = threadIdx.x; q < SEED_S; q += SEED_NT) {
-    float o = pinf<float>();
-    if ((unsigned long long)q < S) {
-      unsigned long long e;
-      if (n <= (unsigned long long)SEED_S) {
-        e = q;
-      } else {
-        const int ch = q / SEED_RUN, off = q % SEED_RUN;
-        e = (unsigned long long)ch * (n - SEED_RUN) / (SEED_CHUNKS - 1) + off;
-      }
-      const float lr = blr[e];
-      if (!is_nan(lr)) {
-        const float sp = bsp[e];
-        const float tc = -0.5f * lr + c.tc_c, dtc = 0.5f * (lr + sp) + c.dtc_c;
-        o = tc - dtc;
-        valid++;
-      }
-    }
-    sv[q] = o;  // invalid -> +inf, sorted to the end
+  unsigned valid = 0;
+  for (int q = threadIdx.x; q < (int)S; q += SEED_NT) {
+    unsigned kh, kl;
+    if (!sample_key(q, kh, kl)) continue;
+    valid++;
+    atomicAdd(&h[0][kh >> 21], 1u);
+    atomicAdd(&h[1][kl >> 21], 1u);
   }
   atomicAdd(&s_valid, valid);
   __syncthreads();
-  for (int kk = 2; kk <= SEED_S; kk <<= 1) {
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < SEED_S; i += SEED_NT) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const bool up = (i & kk) == 0;
-          const float x = sv[i], y = sv[ixj];
-          if (up ? (y < x) : (x < y)) { sv[i] = y; sv[ixj] = x; }
-        }
-      }
-      __syncthreads();
+  const unsigned M = (unsigned)top_m;
+  if (threadIdx.x < 32) {
+    seed_find_bin(h[0], M, &s_bin[0], &s_above[0]);
+    seed_find_bin(h[1], M, &s_bin[1], &s_above[1]);
+  }
+  __syncthreads();
+  const int b0 = s_bin[0], b1 = s_bin[1];
+  const unsigned a0 = s_above[0], a1 = s_above[1];
+  __syncthreads();
+  for (int q = threadIdx.x; q < 2 * SEED_BINS; q += SEED_NT) (&h[0][0])[q] = 0;
+  __syncthreads();
+  if (s_valid >= M && b0 >= 0 && b1 >= 0) {
+    for (int q = threadIdx.x; q < (int)S; q += SEED_NT) {
+      unsigned kh, kl;
+      if (!sample_key(q, kh, kl)) continue;
+      if ((int)(kh >> 21) == b0) atomicAdd(&h[0][(kh >> 10) & (SEED_BINS - 1)], 1u);
+      if ((int)(kl >> 21) == b1) atomicAdd(&h[1][(kl >> 10) & (SEED_BINS - 1)], 1u);
     }
   }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    if (s_valid >= M && b0 >= 0 && b1 >= 0) {
+      seed_find_bin(h[0], M - a0, &s_bin[0], &s_above[0]);
+      seed_find_bin(h[1], M - a1, &s_bin[1], &s_above[1]);
+    } else if (threadIdx.x == 0) {
+      s_bin[0] = s_bin[1] = -1;
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    // widened by a relative 1e-6 so that a rounding difference between this
-    // kernel's O and the reduction's O can never reject a top-M element
-    const int V = s_valid;
-    const float hi = sv[V >= top_m ? V - top_m : 0], lo = sv[top_m - 1 < SEED_S ? top_m - 1 : 0];
-    thr[0] = V >= top_m ? hi - 1e-6f * fabsf(hi) - 1e-30f : -pinf<float>();  // M-th largest
-    thr[1] = V >= top_m ? lo + 1e-6f * fabsf(lo) + 1e-30f : pinf<float>();   // M-th smallest
+    // lower edges of the 22-bit bins (at least M samples at or above each),
+    // widened by a relative 1e-6 so that a rounding difference between two
+    // evaluations of O can never reject a top-M element
+    if (s_bin[0] >= 0 && s_bin[1] >= 0) {
+      const unsigned kh = ((unsigned)b0 << 21) | ((unsigned)s_bin[0] << 10);
+      const unsigned kl = ((unsigned)b1 << 21) | ((unsigned)s_bin[1] << 10);
+      const float hi = fkey_value(kh), lo = fkey_value(~kl);
+      thr[0] = hi - 1e-6f * fabsf(hi) - 1e-30f;  // M-th largest (bound)
+      thr[1] = lo + 1e-6f * fabsf(lo) + 1e-30f;  // M-th smallest (bound)
+    } else {
+      thr[0] = -pinf<float>();
+      thr[1] = pinf<float>();
+    }
   }
 }
 
@@ -133,12 +215,8 @@ cudaError_t launch_reduce_basis(const float* basis, unsigned long long stride_el
                                 int top_m, float* seed_thr, PartRec* part, TopEnt* part_top,
                                 int num_sms, int max_blocks, cudaStream_t s, int* grid_out) {
   const float* thr = nullptr;
-  if (top_m > 0 && seed_thr && n > (8ull << 20)) {
-    const size_t sm = (size_t)SEED_S * sizeof(float);
-    int occ = 0;
-    cudaError_t e = occupancy_cached((const void*)k_seed_thresholds, SEED_NT, sm, &occ);
-    if (e != cudaSuccess) return e;
-    k_seed_thresholds<<<1, SEED_NT, sm, s>>>(basis, basis + stride_elems, n, cmb, top_m, seed_thr);
+  if (top_m > 0 && seed_thr && n > (1ull << 20)) {
+    k_seed_thresholds<<<1, SEED_NT, 0, s>>>(basis, basis + stride_elems, n, cmb, top_m, seed_thr);
     thr = seed_thr;
   }
   return launch_reduce_t<float, false>(basis, stride_elems, n, nullptr, nullptr, 0, id0, cmb, top_m,

@@ -1598,7 +1598,11 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
     }
     const uint64_t total = binom_host(c->N, k);
     if (total < (1ull << 17)) continue;  // too small to matter: built-in shape
-    const uint64_t n = total < (1ull << 22) ? total : (1ull << 22);
+    // where the prefix-shared kernel competes, every candidate is timed on
+    // the whole order (that kernel covers whole orders only); elsewhere on the
+    // first 2^22 nplets, scaled to the order
+    const bool pfx_candidate = k >= KPFX_MIN && k <= KPFX_MAX && total <= (1ull << 28);
+    const uint64_t n = pfx_candidate ? total : (total < (1ull << 22) ? total : (1ull << 22));
     Shape best = default_shape(k);
     double best_ms = -1.0;
     for (int lanes = 1; lanes <= 4; lanes <<= 1) {
@@ -1621,7 +1625,7 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
     }
     // the prefix-shared kernel covers whole orders: timed on the whole order
     // when that is affordable (up to 2^28 nplets)
-    if (k >= KPFX_MIN && k <= KPFX_MAX && total <= (1ull << 28)) {
+    if (pfx_candidate) {
       for (int chunk = 1; chunk <= 4; chunk <<= 1) {
         Shape sh;
         sh.lanes = 1;

@@ -483,15 +483,15 @@ def test_virtual_ranks_partition_and_merge():
 
 
 # ------------------------------------------------------------------ prefix-shared kernel
-@pytest.mark.parametrize("chunk", [1, 3])
-def test_prefix_kernel_every_order_matches_oracle(chunk, tmp_path):
+@pytest.mark.parametrize("variant,chunk", [(1, 1), (1, 3)])
+def test_prefix_kernel_every_order_matches_oracle(variant, chunk, tmp_path):
     # the prefix-shared kernel (bordered steps over a shared (k-1)-prefix) on
     # every order of the fMRI-shaped workload, every nplet against the oracle
     X, orders = workloads.fmri_like()
     S = oracle.copula_cov(X)
     with _ctx(X, out_f64=True) as c:
         for k in orders:
-            _force_shape(c.h, k, 0, 1, chunk, str(tmp_path / f"p{k}.json"), prefix=1)
+            _force_shape(c.h, k, 0, 1, chunk, str(tmp_path / f"p{k}.json"), prefix=variant)
             ref, _ = _refs(S, [k])
             got, _ = c.measures([k])
             np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=TOL32)
