@@ -42,11 +42,12 @@ def flops_model(k: int) -> float:
     return 2.0 / 3.0 * k ** 3 + 2.0 * k ** 2
 
 
-# DRAM bytes per nplet of the FP32 nplet kernels, from ncu captures of the
-# order-16 kernels on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum per launch / 145,422,675 nplets); traffic grows with
-# the nplets written.  None: not captured for the current kernel.
-TRAFFIC_BYTES_PER_NPLET = {"dense": 13.36, "prefix": 69.6}
+# DRAM bytes per nplet of the FP32 nplet kernels, from ncu captures on this
+# workload (dram__bytes_read.sum + dram__bytes_write.sum per launch / nplets):
+# dense and one-level prefix kernels at order 16 (145,422,675 nplets), the
+# two-level prefix kernel at order 15 (155,117,520); traffic grows with the
+# nplets written.  None: not captured for the current kernel.
+TRAFFIC_BYTES_PER_NPLET = {"dense": 13.36, "prefix": 69.6, "prefix2": 51.5}
 
 
 def grad_flops_model(k: int) -> float:
@@ -72,7 +73,20 @@ def prefix_order_flops(N: int, k: int) -> float:
     return math.comb(N - 1, P) * per_prefix + math.comb(N, k) * per_nplet
 
 
-def order_flops(N: int, k: int, prefix: bool) -> float:
+def prefix2_order_flops(N: int, k: int) -> float:
+    # two-level prefix-shared kernel: every (k-2)-prefix built once, one
+    # stored bordered step per (k-1)-prefix, one final step per nplet
+    GP = k - 2
+    per_grand = sum(prefix_level_flops(i) for i in range(GP))
+    per_middle = prefix_level_flops(GP)
+    per_nplet = prefix_level_flops(k - 1) + 2.0 * (k - 1)
+    return (math.comb(N - 2, GP) * per_grand + math.comb(N - 1, k - 1) * per_middle +
+            math.comb(N, k) * per_nplet)
+
+
+def order_flops(N: int, k: int, prefix: int) -> float:
+    if prefix == 2:
+        return prefix2_order_flops(N, k)
     return prefix_order_flops(N, k) if prefix else math.comb(N, k) * flops_model(k)
 
 
@@ -359,11 +373,11 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernels (the FP32 nplet kernels of all orders),
     # each order counted with the work of the kernel the autotuner chose
-    f_total = sum(order_flops(N_VARS, k, bool(shapes.get(k, [1, 8, 0])[2])) for k in ORDERS)
+    f_total = sum(order_flops(N_VARS, k, int(shapes.get(k, [1, 8, 0])[2])) for k in ORDERS)
     f_dense = total_flops()
     traffic = 0.0
     for k in ORDERS:
-        b = TRAFFIC_BYTES_PER_NPLET["prefix" if shapes.get(k, [1, 8, 0])[2] else "dense"]
+        b = TRAFFIC_BYTES_PER_NPLET[("dense", "prefix", "prefix2")[int(shapes.get(k, [1, 8, 0])[2])]]
         traffic = None if (traffic is None or b is None) else traffic + b * math.comb(N_VARS, k)
     kern_s = sum(nplet_ms) / len(nplet_ms) / 1e3
     achieved = f_total / kern_s / 1e12
@@ -389,7 +403,9 @@ def run_ours(args, rank, world, local_rank):
                      "flops_per_step": f_total, "kernel_ms_per_step": kern_s * 1e3,
                      "flops_model": "dense orders 2/3k^3+2k^2 per nplet; prefix-shared orders "
                                     "(tuned_shapes third entry 1) one bordered build per "
-                                    "(k-1)-prefix plus one bordered step per nplet",
+                                    "(k-1)-prefix plus one bordered step per nplet; entry 2: "
+                                    "one build per (k-2)-prefix, one stored step per "
+                                    "(k-1)-prefix, one final step per nplet",
                      "dense_equivalent_tflops": f_dense / kern_s / 1e12,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
         "e2e": {"value": n_total / e2e_s, "unit": "nplets/s",

@@ -90,7 +90,8 @@ struct Shape {
   int blocks_per_sm;  // 0 = occupancy maximum
   int chunk;          // nplets (prefixes for the prefix-shared kernel) per thread per round, 1..8
   int lanes;          // lanes per nplet: 1 (one-thread kernel), 2 or 4 (lane-group kernel)
-  int prefix;         // 1: prefix-shared kernel (whole orders, KPFX_MIN <= k <= KPFX_MAX)
+  int prefix;         // prefix-shared kernels (whole orders, KPFX_MIN <= k <= KPFX_MAX):
+                      // 1 shares a (k-1)-prefix, 2 a (k-2)-prefix; 0 dense
 };
 constexpr int KPFX_MIN = 3;   // orders with a prefix-shared kernel
 constexpr int KPFX_MAX = 20;

@@ -1,0 +1,239 @@
+// Two-level prefix-shared FP32 nplet kernel for whole orders.  It extends
+// the one-level kernel (nplet_pfx.cuh; the same bordered LDL^T steps) one
+// level down: a thread factors a (k-2)-prefix G once, then for every middle
+// index a > max(G) adds a as one stored bordered step, and for every last
+// index b > a adds b as a final bordered step.  The nplets (G, a, b) of one
+// (G, a) have consecutive ranks.
+//
+// Thread order: the (k-2)-prefixes are grouped by their largest index g;
+// every prefix of a group runs the same nested loops (a over g+1 .. N-2, b
+// over a+1 .. N-1), so the lanes of a warp stay together.
+#pragma once
+#include "nplet_common.cuh"
+
+namespace thoi {
+
+template <int K, typename M>
+__global__ void __launch_bounds__(RED_NT) k_nplet_pfx2(const NpletArgs a, const int chunk) {
+  constexpr int P = K - 1;   // variables before the last one
+  constexpr int GP = K - 2;  // grand-prefix size
+  constexpr int GQ = K - 3;  // grand-prefix indices below its largest index g
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = a.N, ldr = row_stride(N);
+  const SmemLayout L = smem_layout(N, K, ldr, sizeof(float), sizeof(unsigned), 0);
+  load_tables<float>(a, smem, L, a.R32);
+  const unsigned long long* sb = reinterpret_cast<const unsigned long long*>(smem + L.binom);
+  const float* sR = reinterpret_cast<const float*>(smem + L.R);
+  const float* sls = reinterpret_cast<const float*>(smem + L.ls);
+  constexpr int bs = K + 1;
+  const bool basis = a.mode == 2;
+  const unsigned long long T = binom_s(sb, bs, N - 2, GP);  // grand prefixes (largest <= N-3)
+  const unsigned long long NK = binom_s(sb, bs, N, K);
+  const unsigned long long nch = (T + chunk - 1) / chunk;
+  const unsigned long long stride = (unsigned long long)gridDim.x * RED_NT;
+  const float tau_piv = a.tau_piv, tau_tr = a.tau_tr;
+  const CombineV<float> cmbv(a.cmb);
+  constexpr int MB = 8 * sizeof(M);
+
+  float Lh[P][P];
+  float dd[P], qd[P], qb[GP];
+  int c[P];
+  float P1 = 1.f, pmin = pinf<float>(), lsp = 0.f;
+  int E1 = 0;
+  bool badp = false;
+
+  // Stored bordered step: variable ci joins the factored variables c[0..i-1]
+  // as row i (Lh row i, dd[i], the inverse diagonal qd[0..i]).
+  auto level = [&](const int i, const int ci) {
+    const float* rowc = sR + ci * ldr;
+    lsp += sls[ci];
+    float x[P];
+#pragma unroll
+    for (int r = 0; r < i; r++) x[r] = rowc[c[r]];
+#pragma unroll
+    for (int r = 1; r < i; r++)
+#pragma unroll
+      for (int s = 0; s < r; s++) x[r] = fmaf(-Lh[r][s], x[s], x[r]);
+    float Dn = rowc[ci];
+#pragma unroll
+    for (int r = 0; r < i; r++) {
+      const float l = x[r] * dd[r];
+      Dn = fmaf(-x[r], l, Dn);
+      x[r] = l;
+      Lh[i][r] = l;
+    }
+    pmin = fminf(pmin, Dn);
+    P1 *= Dn;
+    renorm(P1, E1, badp);
+    const float dn = rcp_approx(Dn);
+    dd[i] = dn;
+#pragma unroll
+    for (int r = i - 1; r >= 0; r--) {
+      float s = -x[r];
+#pragma unroll
+      for (int t = r + 1; t < i; t++) s = fmaf(-Lh[t][r], x[t], s);
+      x[r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < i; r++) qd[r] = fmaf(x[r] * dn, x[r], qd[r]);
+    qd[i] = dn;
+  };
+
+  for (unsigned long long ch = (unsigned long long)blockIdx.x * RED_NT + threadIdx.x; ch < nch;
+       ch += stride) {
+    if (((ch / stride) & 63) == 0 && a.cancel && *(volatile const int*)a.cancel) {
+      atomicOr(a.status, ST_CANCELLED);
+      break;
+    }
+    const unsigned long long g0 = ch * chunk;
+    const int cnt = T - g0 < (unsigned long long)chunk ? (int)(T - g0) : chunk;
+    int g = GQ;
+    unsigned long long off = 0, gsz = binom_s(sb, bs, g, GQ);
+    while (g0 >= off + gsz) {
+      off += gsz;
+      g++;
+      gsz = binom_s(sb, bs, g, GQ);
+    }
+    unsigned long long j = g0 - off;
+    M pm = unrank_s<M>(j, GQ, g, sb, bs);
+    for (int jn = 0; jn < cnt; jn++) {
+      {
+        M t = pm;
+#pragma unroll
+        for (int q = 0; q < GQ; q++) {
+          const int hb = hibit(t);
+          t ^= (M)1 << hb;
+          c[q] = g - 1 - hb;
+        }
+        c[GQ] = g;
+      }
+      // ---- grand prefix
+      P1 = 1.f;
+      E1 = 0;
+      pmin = pinf<float>();
+      lsp = 0.f;
+      badp = false;
+#pragma unroll
+      for (int i = 0; i < GP; i++) level(i, c[i]);
+#pragma unroll
+      for (int r = 0; r < GP; r++) qb[r] = qd[r];
+      const float P1g = P1, pming = pmin, lspg = lsp;
+      const int E1g = E1;
+      const bool badg = badp;
+      unsigned long long rbase = NK - 1ull;
+#pragma unroll
+      for (int i = 0; i < GP; i++) rbase -= binom_s(sb, bs, N - 1 - c[i], K - i);
+      // ---- middle variables
+      for (int am = g + 1; am < N - 1; am++) {
+#pragma unroll
+        for (int r = 0; r < GP; r++) qd[r] = qb[r];
+        P1 = P1g;
+        E1 = E1g;
+        pmin = pming;
+        lsp = lspg;
+        badp = badg;
+        c[GP] = am;
+        level(GP, am);
+        const unsigned long long r0 =
+            rbase - binom_s(sb, bs, N - 1 - am, 2) - (unsigned long long)(N - 2 - am);
+        // ---- last variables: one final bordered step each
+        for (int cl = am + 1; cl < N; cl++) {
+          const float* rowc = sR + cl * ldr;
+          float x[P];
+#pragma unroll
+          for (int r = 0; r < P; r++) x[r] = rowc[c[r]];
+#pragma unroll
+          for (int r = 1; r < P; r++)
+#pragma unroll
+            for (int s = 0; s < r; s++) x[r] = fmaf(-Lh[r][s], x[s], x[r]);
+          float Dn = rowc[cl];
+#pragma unroll
+          for (int r = 0; r < P; r++) {
+            const float l = x[r] * dd[r];
+            Dn = fmaf(-x[r], l, Dn);
+            x[r] = l;
+          }
+          const float dn = rcp_approx(Dn);
+#pragma unroll
+          for (int r = P - 1; r >= 0; r--) {
+            float s = -x[r];
+#pragma unroll
+            for (int t = r + 1; t < P; t++) s = fmaf(-Lh[t][r], x[t], s);
+            x[r] = s;
+          }
+          bool bad = badp;
+          float Pl = P1 * Dn;
+          int El = E1;
+          renorm(Pl, El, bad);
+          float P2 = dn, trace = dn;
+          int E2 = 0;
+#pragma unroll
+          for (int r = 0; r < P; r++) {
+            const float pr = fmaf(x[r] * dn, x[r], qd[r]);
+            trace += pr;
+            P2 *= pr;
+            if ((r & 3) == 3 || r == P - 1) renorm(P2, E2, bad);
+          }
+          const float lr = log_of(Pl, El), sp = log_of(P2, E2);
+          const float lsum = lsp + sls[cl];
+          bad |= !(fminf(pmin, Dn) >= tau_piv) | !(trace <= tau_tr);
+          const unsigned long long gid = a.id_base + r0 + (unsigned long long)(cl - am - 1);
+          if (basis) {
+            store_basis(a, gid, lr, sp, lsum, bad);
+          } else {
+            float v[5];
+            combine5<float>(lr, sp, lsum, cmbv, v);
+            store5<float>(a, gid, v);
+          }
+          flag_append(a, bad, gid);
+        }
+      }
+      if (jn + 1 < cnt) {
+        if (j + 1 < gsz) {
+          const M fullg = (g >= MB) ? ~(M)0 : (((M)1 << g) - 1);
+          pm = lex_succ(pm, fullg);
+          j++;
+        } else {
+          g++;
+          gsz = binom_s(sb, bs, g, GQ);
+          j = 0;
+          pm = unrank_s<M>(0, GQ, g, sb, bs);
+        }
+      }
+    }
+  }
+}
+
+template <int K, typename M>
+static cudaError_t launch_pfx2_t(const NpletArgs& a, const Shape& sh, int num_sms,
+                                 cudaStream_t s, int* grid_out, int max_blocks) {
+  const SmemLayout L = smem_layout(a.N, K, row_stride(a.N), sizeof(float), sizeof(unsigned), 0);
+  void (*fn)(const NpletArgs, const int) = k_nplet_pfx2<K, M>;
+  int occ = 0;
+  cudaError_t e = occupancy_cached((const void*)fn, RED_NT, L.total, &occ);
+  if (e != cudaSuccess) return e;
+  if (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ) occ = sh.blocks_per_sm;
+  int chunk = sh.chunk > 0 ? sh.chunk : 1;
+  if (chunk > 8) chunk = 8;
+  // grand prefixes of the order: C(N-2, K-2)
+  unsigned __int128 t = 1;
+  for (int i = 1; i <= K - 2; i++) t = t * (unsigned)(a.N - K + i) / (unsigned)i;
+  const unsigned long long T = (unsigned long long)t;
+  long long grid = (long long)num_sms * occ;
+  const long long need =
+      (long long)((T + (unsigned long long)RED_NT * chunk - 1) / ((unsigned long long)RED_NT * chunk));
+  if (need < grid) grid = need > 0 ? need : 1;
+  if (grid > max_blocks) grid = max_blocks;
+  fn<<<(unsigned)grid, RED_NT, L.total, s>>>(a, chunk);
+  if (grid_out) *grid_out = (int)grid;
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_pfx2_k(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
+                          int* grid_out, int max_blocks) {
+  if (a.N <= 32) return launch_pfx2_t<K, unsigned>(a, sh, num_sms, s, grid_out, max_blocks);
+  return launch_pfx2_t<K, unsigned long long>(a, sh, num_sms, s, grid_out, max_blocks);
+}
+
+}  // namespace thoi

@@ -1526,7 +1526,7 @@ static void tune_load(const char* path, const char* gpu, int sms) {
     sh.lanes = lanes;
     sh.chunk = chunk;
     sh.blocks_per_sm = bps;
-    sh.prefix = prefix ? 1 : 0;
+    sh.prefix = (prefix >= 0 && prefix <= 2) ? prefix : 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(gpu, sms, k, wide)] = sh;
     g_tune_gen++;
@@ -1626,12 +1626,14 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
     // the prefix-shared kernel covers whole orders: timed on the whole order
     // when that is affordable (up to 2^28 nplets)
     if (pfx_candidate) {
-      for (int chunk = 1; chunk <= 4; chunk <<= 1) {
+      // (k-1)-prefix kernel with 1, 2, 4 prefixes per thread per round, then
+      // the (k-2)-prefix kernel with 1, 2
+      for (int v = 0; v < 5; v++) {
         Shape sh;
         sh.lanes = 1;
-        sh.chunk = chunk;
+        sh.chunk = v < 3 ? 1 << v : 1 << (v - 3);
         sh.blocks_per_sm = 0;
-        sh.prefix = 1;
+        sh.prefix = v < 3 ? 1 : 2;
         const double ms = time_shape(c, k, total, sh, s);
         if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
           best_ms = ms;
