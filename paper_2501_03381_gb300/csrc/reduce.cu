@@ -78,6 +78,16 @@ __device__ void seed_find_bin(const unsigned* hist, unsigned target, int* bin, u
   }
 }
 
+// Histogram increment aggregated over the lanes of a warp that hit the same
+// bin (neighbouring samples usually share their high key bits, so one atomic
+// per distinct bin replaces up to 32 on one address).
+__device__ __forceinline__ void hist_add(unsigned* hist, unsigned bin, bool on) {
+  const unsigned act = __ballot_sync(0xffffffffu, on);
+  if (!on) return;
+  const unsigned peers = __match_any_sync(act, bin);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
+}
+
 __global__ void __launch_bounds__(SEED_NT) k_seed_thresholds(const float* __restrict__ blr,
                                                              const float* __restrict__ bsp,
                                                              unsigned long long n, Combine cmb,
@@ -88,32 +98,55 @@ __global__ void __launch_bounds__(SEED_NT) k_seed_thresholds(const float* __rest
   __shared__ unsigned s_valid;
   const CombineV<float> c(cmb);
   const unsigned long long S = n < (unsigned long long)SEED_S ? n : (unsigned long long)SEED_S;
-  auto sample_key = [&](int q, unsigned& kh, unsigned& kl) -> bool {
-    unsigned long long e;
-    if (n <= (unsigned long long)SEED_S) {
-      e = q;
-    } else {
-      const int run = q / SEED_RUN, off = q % SEED_RUN;
-      e = (unsigned long long)run * (n - SEED_RUN) / (SEED_RUNS - 1) + off;
+  // Samples are read SEED_ILP at a time, all loads issued before any is used:
+  // one block walks the whole sample, so the loop is bound by memory latency
+  // unless many loads are in flight per thread.  Every lane of a warp runs the
+  // same iterations (absent samples take part with on = false), as hist_add
+  // needs.
+  constexpr int SEED_ILP = 8;
+  __shared__ unsigned long long s_run[SEED_RUNS];  // first element of each sampled run
+  for (int r = threadIdx.x; r < SEED_RUNS; r += SEED_NT)
+    s_run[r] = n > (unsigned long long)SEED_S
+                   ? (unsigned long long)r * (n - SEED_RUN) / (SEED_RUNS - 1) : 0ull;
+  __syncthreads();
+  const int iters = ((int)S + SEED_NT * SEED_ILP - 1) / (SEED_NT * SEED_ILP);
+  auto load_group = [&](int i0, float (&lr)[SEED_ILP], float (&sp)[SEED_ILP]) {
+#pragma unroll
+    for (int j = 0; j < SEED_ILP; j++) {
+      const int q = threadIdx.x + (i0 * SEED_ILP + j) * SEED_NT;
+      lr[j] = pinf<float>() - pinf<float>();
+      sp[j] = 0.f;
+      if (q < (int)S) {
+        const unsigned long long e =
+            n <= (unsigned long long)SEED_S ? (unsigned long long)q : s_run[q / SEED_RUN] + q % SEED_RUN;
+        lr[j] = blr[e];
+        sp[j] = bsp[e];
+      }
     }
-    const float lr = blr[e];
+  };
+  // order-preserving keys: largest O = largest kh; smallest O = largest kl
+  auto keys_of = [&](float lr, float sp, unsigned& kh, unsigned& kl) -> bool {
     if (is_nan(lr)) return false;
-    const float sp = bsp[e];
     const float tc = -0.5f * lr + c.tc_c, dtc = 0.5f * (lr + sp) + c.dtc_c;
-    kh = fkey(tc - dtc);  // largest O = largest key
-    kl = ~kh;             // smallest O = largest inverted key
+    kh = fkey(tc - dtc);
+    kl = ~kh;
     return true;
   };
   for (int q = threadIdx.x; q < 2 * SEED_BINS; q += SEED_NT) (&h[0][0])[q] = 0;
   if (threadIdx.x == 0) s_valid = 0;
   __syncthreads();
   unsigned valid = 0;
-  for (int q = threadIdx.x; q < (int)S; q += SEED_NT) {
-    unsigned kh, kl;
-    if (!sample_key(q, kh, kl)) continue;
-    valid++;
-    atomicAdd(&h[0][kh >> 21], 1u);
-    atomicAdd(&h[1][kl >> 21], 1u);
+  for (int i0 = 0; i0 < iters; i0++) {
+    float lr[SEED_ILP], sp[SEED_ILP];
+    load_group(i0, lr, sp);
+#pragma unroll
+    for (int j = 0; j < SEED_ILP; j++) {
+      unsigned kh = 0, kl = 0;
+      const bool on = keys_of(lr[j], sp[j], kh, kl);
+      valid += on ? 1u : 0u;
+      hist_add(h[0], kh >> 21, on);
+      hist_add(h[1], kl >> 21, on);
+    }
   }
   atomicAdd(&s_valid, valid);
   __syncthreads();
@@ -129,11 +162,16 @@ __global__ void __launch_bounds__(SEED_NT) k_seed_thresholds(const float* __rest
   for (int q = threadIdx.x; q < 2 * SEED_BINS; q += SEED_NT) (&h[0][0])[q] = 0;
   __syncthreads();
   if (s_valid >= M && b0 >= 0 && b1 >= 0) {
-    for (int q = threadIdx.x; q < (int)S; q += SEED_NT) {
-      unsigned kh, kl;
-      if (!sample_key(q, kh, kl)) continue;
-      if ((int)(kh >> 21) == b0) atomicAdd(&h[0][(kh >> 10) & (SEED_BINS - 1)], 1u);
-      if ((int)(kl >> 21) == b1) atomicAdd(&h[1][(kl >> 10) & (SEED_BINS - 1)], 1u);
+    for (int i0 = 0; i0 < iters; i0++) {
+      float lr[SEED_ILP], sp[SEED_ILP];
+      load_group(i0, lr, sp);
+#pragma unroll
+      for (int j = 0; j < SEED_ILP; j++) {
+        unsigned kh = 0, kl = 0;
+        const bool on = keys_of(lr[j], sp[j], kh, kl);
+        hist_add(h[0], (kh >> 10) & (SEED_BINS - 1), on && (int)(kh >> 21) == b0);
+        hist_add(h[1], (kl >> 10) & (SEED_BINS - 1), on && (int)(kl >> 21) == b1);
+      }
     }
   }
   __syncthreads();
