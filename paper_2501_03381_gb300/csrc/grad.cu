@@ -123,13 +123,10 @@ __global__ void __launch_bounds__(RED_NT) k_grad(const NpletArgs a, const int me
         for (int x = 0; x < k; x++)
           for (int y = 0; y <= x; y++) {
             const V g = grad_entry<V>(measure, x, y, P, Q, k);
-            if (FP32_PATH) {
-              atomicAdd(&Gs[c[x] * N + c[y]], (float)g);
-              if (x != y) atomicAdd(&Gs[c[y] * N + c[x]], (float)g);
-            } else {
-              atomicAdd(&Gb[c[x] * N + c[y]], (double)g);
-              if (x != y) atomicAdd(&Gb[c[y] * N + c[x]], (double)g);
-            }
+            // lower triangle only (c ascending, so c[x] >= c[y]); the
+            // finishing kernel mirrors it
+            if (FP32_PATH) atomicAdd(&Gs[c[x] * N + c[y]], (float)g);
+            else atomicAdd(&Gb[c[x] * N + c[y]], (double)g);
           }
       }
     }
@@ -151,15 +148,184 @@ __global__ void __launch_bounds__(RED_NT) k_grad(const NpletArgs a, const int me
   }
 }
 
-// Sum the per-block partials in block order and scale to Sigma coordinates.
+// Sum the per-block partials (lower triangle) in block order, mirror, and
+// scale to Sigma coordinates.
 __global__ void k_grad_finish(const double* __restrict__ Gpart, int nblk, const double* __restrict__ sig64,
                               int N, float* __restrict__ out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N * N) return;
   const int x = idx / N, y = idx % N;
+  const int lo = (x > y ? x : y) * N + (x > y ? y : x);
   double s = 0;
-  for (int b = 0; b < nblk; b++) s += Gpart[(size_t)b * N * N + idx];
+  for (int b = 0; b < nblk; b++) s += Gpart[(size_t)b * N * N + lo];
   out[idx] = (float)(s / sqrt(sig64[x * N + x] * sig64[y * N + y]));
+}
+
+// Register-resident FP32 pass for small orders (compile-time K): the k x k
+// correlation submatrix, its factor, P = R_S^-1 and Q = P diag(1/p) P live in
+// registers; consecutive ranks per thread (one unrank, then the lexicographic
+// successor).  Contributions go to the lower triangle of the block's shared
+// FP32 accumulator, flushed into the FP64 per-block partial every round of
+// GRAD_CHUNK nplets per thread.
+constexpr int GRAD_CHUNK = 8;
+
+template <int K>
+__device__ __forceinline__ float grad_entry_reg(int measure, bool diag, float pab, float qab) {
+  const float id = diag ? 1.f : 0.f;
+  switch (measure) {
+    case THOI_H: return 0.5f * pab;
+    case THOI_TC: return 0.5f * (id - pab);
+    case THOI_DTC: return 0.5f * (pab - qab);
+    case THOI_O: return 0.5f * (id - 2.f * pab + qab);
+    default: return 0.5f * (id - qab);
+  }
+}
+
+template <int K, typename M>
+__global__ void __launch_bounds__(RED_NT) k_grad_reg(const NpletArgs a, const int measure,
+                                                     double* __restrict__ Gpart) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_stop;
+  const int N = a.N, ldr = row_stride(N);
+  const SmemLayout L = smem_layout(N, K, ldr, sizeof(float), sizeof(unsigned), 0);
+  float* Gs = reinterpret_cast<float*>(smem + L.total);
+  if (threadIdx.x == 0) s_stop = 0;
+  for (int q = threadIdx.x; q < N * N; q += RED_NT) Gs[q] = 0.f;
+  load_tables<float>(a, smem, L, a.R32);
+  const unsigned long long* sb = reinterpret_cast<const unsigned long long*>(smem + L.binom);
+  const float* sR = reinterpret_cast<const float*>(smem + L.R);
+  double* Gb = Gpart + (size_t)blockIdx.x * N * N;
+  const M full = (N >= (int)(8 * sizeof(M))) ? ~(M)0 : (((M)1 << N) - 1);
+  const unsigned long long n = a.rank_end - a.rank_begin;
+  const unsigned long long nch = (n + GRAD_CHUNK - 1) / GRAD_CHUNK;
+  const unsigned long long stride = (unsigned long long)gridDim.x * RED_NT;
+  const unsigned long long rounds = (nch + stride - 1) / stride;
+  const float tau_piv = a.tau_piv, tau_tr = a.tau_tr;
+  for (unsigned long long rd = 0; rd < rounds; rd++) {
+    const unsigned long long ch = rd * stride + (unsigned long long)blockIdx.x * RED_NT + threadIdx.x;
+    if (ch < nch) {
+      const unsigned long long r0 = a.rank_begin + ch * GRAD_CHUNK;
+      const unsigned long long left = a.rank_end - r0;
+      const int cnt = left < (unsigned long long)GRAD_CHUNK ? (int)left : GRAD_CHUNK;
+      M mask = unrank_s<M>(r0, K, N, sb, K + 1);
+      for (int jn = 0; jn < cnt; jn++) {
+        int c[K];
+        {
+          M m = mask;
+#pragma unroll
+          for (int i = 0; i < K; i++) {
+            const int hb = hibit(m);
+            m ^= (M)1 << hb;
+            c[i] = N - 1 - hb;
+          }
+        }
+        // Cholesky R_S = L L^T in place (1/L_pp on the diagonal)
+        float A[K][K];
+#pragma unroll
+        for (int i = 0; i < K; i++) {
+          const float* row = sR + c[i] * ldr;
+#pragma unroll
+          for (int j = 0; j <= i; j++) A[i][j] = row[c[j]];
+        }
+        float pmin = pinf<float>();
+        bool bad = false;
+#pragma unroll
+        for (int p = 0; p < K; p++) {
+          const float d = A[p][p];
+          pmin = fminf(pmin, d);
+          bad |= !(d > 0.f);
+          const float inv = rsqrtf(d);
+          A[p][p] = inv;
+#pragma unroll
+          for (int i = p + 1; i < K; i++) A[i][p] *= inv;
+#pragma unroll
+          for (int i = p + 1; i < K; i++)
+#pragma unroll
+            for (int j = p + 1; j <= i; j++) A[i][j] = fmaf(-A[i][p], A[j][p], A[i][j]);
+        }
+        // W = L^-1 in place (lower)
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+          const float wjj = A[j][j];
+#pragma unroll
+          for (int i = j + 1; i < K; i++) {
+            float s2 = A[i][j] * wjj;
+#pragma unroll
+            for (int q = j + 1; q < i; q++) s2 = fmaf(A[i][q], A[q][j], s2);
+            A[i][j] = -A[i][i] * s2;
+          }
+        }
+        // P = W^T W (lower half, x >= y), p = diag(P)
+        float Pm[K][K];
+        float trace = 0.f;
+#pragma unroll
+        for (int x = 0; x < K; x++)
+#pragma unroll
+          for (int y = 0; y <= x; y++) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int i = x; i < K; i++) s2 = fmaf(A[i][x], A[i][y], s2);
+            Pm[x][y] = s2;
+            if (x == y) trace += s2;
+          }
+        bad |= !(pmin >= tau_piv) | !(trace <= tau_tr);
+        const unsigned long long gid = a.id_base + r0 + jn;
+        flag_append(a, bad, gid);
+        if (!bad) {
+          float dinv[K];
+#pragma unroll
+          for (int j = 0; j < K; j++) dinv[j] = 1.f / Pm[j][j];
+#pragma unroll
+          for (int x = 0; x < K; x++)
+#pragma unroll
+            for (int y = 0; y <= x; y++) {
+              float qxy = 0.f;
+              if (measure == THOI_DTC || measure == THOI_O || measure == THOI_S) {
+#pragma unroll
+                for (int j = 0; j < K; j++) {
+                  const float pxj = j <= x ? Pm[x][j] : Pm[j][x];
+                  const float pjy = j <= y ? Pm[y][j] : Pm[j][y];
+                  qxy = fmaf(pxj * dinv[j], pjy, qxy);
+                }
+              }
+              atomicAdd(&Gs[c[x] * N + c[y]], grad_entry_reg<K>(measure, x == y, Pm[x][y], qxy));
+            }
+        }
+        if (jn + 1 < cnt) mask = lex_succ(mask, full);
+      }
+    }
+    if (threadIdx.x == 0 && a.cancel && *(volatile const int*)a.cancel) s_stop = 1;
+    __syncthreads();
+    for (int q = threadIdx.x; q < N * N; q += RED_NT) {
+      Gb[q] += (double)Gs[q];
+      Gs[q] = 0.f;
+    }
+    __syncthreads();
+    if (s_stop) {
+      if (threadIdx.x == 0) atomicOr(a.status, ST_CANCELLED);
+      break;
+    }
+  }
+}
+
+template <int K, typename M>
+static cudaError_t launch_grad_reg_t(const NpletArgs& a, double* Gpart, int grid, int measure,
+                                     cudaStream_t s) {
+  const SmemLayout L = smem_layout(a.N, K, row_stride(a.N), sizeof(float), sizeof(unsigned), 0);
+  const size_t sm = L.total + (size_t)a.N * a.N * sizeof(float);
+  void (*fn)(const NpletArgs, const int, double*) = k_grad_reg<K, M>;
+  int occ = 0;
+  cudaError_t e = occupancy_cached((const void*)fn, RED_NT, sm, &occ);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, RED_NT, sm, s>>>(a, measure, Gpart);
+  return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t launch_grad_reg_k(const NpletArgs& a, double* Gpart, int grid, int measure,
+                                     cudaStream_t s) {
+  if (a.N > 32) return launch_grad_reg_t<K, unsigned long long>(a, Gpart, grid, measure, s);
+  return launch_grad_reg_t<K, unsigned>(a, Gpart, grid, measure, s);
 }
 
 template <typename V, int KMAX, bool LIST>
@@ -179,6 +345,19 @@ static cudaError_t launch_grad_t(const NpletArgs& a, double* Gpart, int grid, in
 // grid: number of blocks (<= the Gpart regions allocated).
 cudaError_t launch_grad_pass(const NpletArgs& a, double* Gpart, int grid, int measure, bool list,
                              cudaStream_t s) {
+  if (!list) {
+    switch (a.k) {
+      case 1: return launch_grad_reg_k<1>(a, Gpart, grid, measure, s);
+      case 2: return launch_grad_reg_k<2>(a, Gpart, grid, measure, s);
+      case 3: return launch_grad_reg_k<3>(a, Gpart, grid, measure, s);
+      case 4: return launch_grad_reg_k<4>(a, Gpart, grid, measure, s);
+      case 5: return launch_grad_reg_k<5>(a, Gpart, grid, measure, s);
+      case 6: return launch_grad_reg_k<6>(a, Gpart, grid, measure, s);
+      case 7: return launch_grad_reg_k<7>(a, Gpart, grid, measure, s);
+      case 8: return launch_grad_reg_k<8>(a, Gpart, grid, measure, s);
+      default: break;
+    }
+  }
   const int kb = a.k <= 8 ? 8 : (a.k <= 16 ? 16 : 32);
   if (list) {
     if (kb == 8) return launch_grad_t<double, 8, true>(a, Gpart, grid, measure, s);
