@@ -281,6 +281,23 @@ thoi_status thoi_order_record_noalloc(const double* Sigma, int64_t N, int32_t k,
                                       thoi_order_record* rec_out, thoi_top_entry* top_out,
                                       void* stream);
 
+/* Greedy search (Methods, "Heuristics", "Greedy Algorithm").  Start from the
+ * kappa best nplets of order k0 (an exhaustive pass over all C(N, k0)); then,
+ * for each order k = k0+1 .. k1, grow every selected set by each variable it
+ * lacks, evaluate the distinct candidates and keep the kappa best.  "Best" is
+ * the largest (maximize != 0) or smallest value of `measure` (thoi_measure);
+ * ties go to the smaller lexicographic rank.  All evaluations run in the FP64
+ * path on the device, whatever the context's precision; candidates that are
+ * not positive definite are left out.
+ *  sets_out   : host uint64_t[(k1-k0+1) * kappa]; row k-k0 holds the selected
+ *               sets of order k, best first, as bit masks (bit i = variable i)
+ *  values_out : host double[(k1-k0+1) * kappa], the measure of each set
+ * Unused slots (fewer than kappa candidates) hold mask 0 and NaN.
+ * 1 <= k0 <= k1 <= N, 1 <= kappa <= THOI_MAX_TOP_M.  Synchronises `stream`. */
+thoi_status thoi_greedy(thoi_ctx* ctx, int32_t k0, int32_t k1, int32_t kappa, int32_t measure,
+                        int32_t maximize, uint64_t* sets_out, double* values_out,
+                        thoi_stats* stats, void* stream);
+
 /* Host-only sharding helpers (no device work, no CUDA calls).  Nplets are
  * independent (Methods, "Parallel and batched computation of HOI"), so one
  * request splits into contiguous global-id ranges evaluated by separate

@@ -19,6 +19,7 @@ Paper passages followed (arXiv 2501.03381):
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -285,3 +286,46 @@ def reduce_per_order(N: int, orders, vals: np.ndarray, ids: np.ndarray, notpd: n
         rec["top_lo_val"], rec["top_lo_id"] = o[lo].copy(), i[lo].copy()
         recs.append(rec)
     return recs
+
+
+def subset_rank(N: int, members) -> int:
+    """Lexicographic rank of a sorted k-subset among all k-subsets of N
+    (Supp. eq. comb; rank = C(N,k) - 1 - sum_i C(N-1-c_i, k-i))."""
+    k = len(members)
+    return math.comb(N, k) - 1 - sum(math.comb(N - 1 - c, k - i) for i, c in enumerate(members))
+
+
+def greedy(Sigma: np.ndarray, k0: int, k1: int, kappa: int, measure: str = "O",
+           maximize: bool = True):
+    """Greedy search (Methods, "Heuristics", "Greedy Algorithm"), literally:
+    the kappa best nplets of order k0 from an exhaustive evaluation, then for
+    each next order every selected set grows by each variable it lacks, the
+    distinct candidates are evaluated, and the kappa best are kept.  Best =
+    largest (or smallest) value of the measure; ties by smaller lexicographic
+    rank; nplets that are not positive definite are left out.  Returns one
+    (members list, values array) pair per order k0..k1."""
+    S = np.ascontiguousarray(Sigma, dtype=np.float64)
+    N = S.shape[0]
+    m = MEASURES.index(measure)
+
+    def pick(ids, vals, notpd, k):
+        keep = notpd == 0
+        ids, vals = ids[keep], vals[keep]
+        key = -vals if maximize else vals
+        order = np.lexsort((ids, key))[:kappa]
+        sets = [tuple(int(x) for x in row) for row in unrank_ids(N, [k], ids[order])]
+        return sets, vals[order]
+
+    out = []
+    vals, notpd = measures(S, [k0])
+    sets, best = pick(np.arange(vals.shape[1], dtype=np.uint64), vals[m], notpd, k0)
+    out.append((sets, best))
+    for k in range(k0 + 1, k1 + 1):
+        cand = sorted({tuple(sorted(s + (v,))) for s in sets for v in range(N) if v not in s})
+        if not cand:
+            break
+        ids = np.array([subset_rank(N, c) for c in cand], dtype=np.uint64)
+        vals, notpd = measures_ids(S, [k], ids)
+        sets, best = pick(ids, vals[m], notpd, k)
+        out.append((sets, best))
+    return out

@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True):
             "thoi_set_cancel": (ctypes.c_int, [vp, i32]),
             "thoi_order_record_noalloc": (ctypes.c_int, [vp, i64, i32, i32, vp, vp, vp]),
             "thoi_partition": (ctypes.c_int, [i64, vp, i32, i32, vp]),
+            "thoi_greedy": (ctypes.c_int, [vp, i32, i32, i32, i32, i32, vp, vp,
+                                           ctypes.POINTER(thoi_stats), vp]),
             "thoi_merge_records": (ctypes.c_int, [vp, i32, i32, i32, vp]),
             "thoi_destroy": (None, [vp]),
         }
@@ -376,6 +378,21 @@ def thoi_batch_measures(handles, kmin: int, kmax: int, top_m: int = 256, out=Non
     return res, st
 
 
+def thoi_greedy(h, k0: int, k1: int, kappa: int, measure: str = "O", maximize: bool = True,
+                stream=None):
+    """Greedy search from the exhaustive top-kappa of order k0 up to order k1.
+    Returns (masks uint64[k1-k0+1, kappa], values float64[k1-k0+1, kappa],
+    stats); row k-k0 holds the selected sets of order k, best first."""
+    L = k1 - k0 + 1
+    masks = np.zeros((L, kappa), dtype=np.uint64)
+    values = np.zeros((L, kappa), dtype=np.float64)
+    st = thoi_stats()
+    _check(load().thoi_greedy(h, k0, k1, kappa, MEASURES.index(measure), int(bool(maximize)),
+                              _ptr(masks), _ptr(values), ctypes.byref(st), _stream_ptr(stream)),
+           "thoi_greedy")
+    return masks, values, st
+
+
 def thoi_autotune(h, kmin: int, kmax: int, cache_path: str | None = None, stream=None):
     _check(load().thoi_autotune(h, kmin, kmax, cache_path.encode() if cache_path else None,
                                 _stream_ptr(stream)), "thoi_autotune")
@@ -454,6 +471,10 @@ class Context:
                              out_f64=bool(self.opt.out_f64) if self.opt.out_f64 >= 0
                              else self.opt.precision == THOI_F64,
                              top_m=self.opt.top_m, stream=stream)
+
+    def greedy(self, k0, k1, kappa, measure="O", maximize=True, stream=None):
+        masks, values, _ = thoi_greedy(self.h, k0, k1, kappa, measure, maximize, stream)
+        return masks, values
 
     def grad(self, orders, measure="O", out=None, stream=None):
         return thoi_measures_grad(self.h, orders, measure, out, stream)

@@ -50,6 +50,8 @@ static_assert(sizeof(TopEnt) == sizeof(thoi_top_entry), "layout");
 // The constants carry 1/2 k log(2 pi e) and the optional bias terms.
 struct Combine {
   double h_c, tc_c, dtc_c;
+  int top;  // measure the top-M lists rank (thoi_measure; O for the records API)
+  int pad;
 };
 
 // Everything a nplet kernel needs for one order.

@@ -129,6 +129,8 @@ extern "C" thoi_status thoi_order_record_noalloc(const double* Sigma, int64_t N,
   a.cmb.h_c = 0.5 * k * 2.8378770664093454835606594728112;
   a.cmb.tc_c = 0.0;
   a.cmb.dtc_c = 0.0;
+  a.cmb.top = THOI_O;
+  a.cmb.pad = 0;
   a.mode = 1;
   a.part = part;
   a.part_top = top;

@@ -107,6 +107,17 @@ struct CombineV {
       : h_c((V)c.h_c), tc_c((V)c.tc_c), dtc_c((V)c.dtc_c) {}
 };
 
+// One of the five combined values by runtime index (selects, no local memory).
+template <typename V>
+__device__ __forceinline__ V pick5(const V (&v)[5], int m) {
+  V r = v[3];
+  r = m == 0 ? v[0] : r;
+  r = m == 1 ? v[1] : r;
+  r = m == 2 ? v[2] : r;
+  r = m == 4 ? v[4] : r;
+  return r;
+}
+
 template <typename V>
 __device__ __forceinline__ void combine5(V lr, V sp, V lsum, const CombineV<V>& c, V (&v)[5]) {
   const V tc = (V)(-0.5) * lr + c.tc_c;

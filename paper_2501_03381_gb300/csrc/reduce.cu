@@ -127,8 +127,9 @@ __global__ void __launch_bounds__(SEED_NT) k_seed_thresholds(const float* __rest
   // order-preserving keys: largest O = largest kh; smallest O = largest kl
   auto keys_of = [&](float lr, float sp, unsigned& kh, unsigned& kl) -> bool {
     if (is_nan(lr)) return false;
-    const float tc = -0.5f * lr + c.tc_c, dtc = 0.5f * (lr + sp) + c.dtc_c;
-    kh = fkey(tc - dtc);
+    float v[5];
+    combine5<float>(lr, sp, 0.f, c, v);  // the ranked measure (H would need the log-variances)
+    kh = fkey(pick5(v, cmb.top));
     kl = ~kh;
     return true;
   };
@@ -253,7 +254,8 @@ cudaError_t launch_reduce_basis(const float* basis, unsigned long long stride_el
                                 int top_m, float* seed_thr, PartRec* part, TopEnt* part_top,
                                 int num_sms, int max_blocks, cudaStream_t s, int* grid_out) {
   const float* thr = nullptr;
-  if (top_m > 0 && seed_thr && n > (1ull << 20)) {
+  // the seed samples do not read the log-variances, so H-ranked lists start unseeded
+  if (top_m > 0 && seed_thr && n > (1ull << 20) && cmb.top != THOI_H) {
     k_seed_thresholds<<<1, SEED_NT, 0, s>>>(basis, basis + stride_elems, n, cmb, top_m, seed_thr);
     thr = seed_thr;
   }

@@ -98,11 +98,11 @@ __device__ void reduce_core(unsigned long long first, unsigned long long step,
         if (LIST) {
           const I id = (I)ids[e0 + t];
           tr.add(v, id, lr[t], sp[t], ls[t]);
-          if (with_top) top_offer(tb, v[3], id, thr_hi, thr_lo);
+          if (with_top) top_offer(tb, pick5(v, cmb.top), id, thr_hi, thr_lo);
         } else {
           const I loc = (I)(e0 + t);
           tr.add_mono(v, loc, lr[t], sp[t], ls[t]);
-          if (with_top) top_offer(tb, v[3], loc, thr_hi, thr_lo);
+          if (with_top) top_offer(tb, pick5(v, cmb.top), loc, thr_hi, thr_lo);
         }
         if ((t & 3) == 3) tr.flush();
       }

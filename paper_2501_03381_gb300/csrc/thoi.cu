@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -83,6 +84,7 @@ struct thoi_ctx {
   int force_shape_valid = 0;
   Shape force_shape;
   unsigned long long serial = 0;  // unique per context (keys the batch graph cache)
+  int top_meas = THOI_O;          // measure ranked by the top-M lists
 };
 
 // ------------------------------------------------------------------ occupancy cache
@@ -225,6 +227,8 @@ static Combine combine_for(const thoi_ctx* c, int k) {
   cb.h_c = 0.5 * k * LOG2PIE;
   cb.tc_c = 0.0;
   cb.dtc_c = 0.0;
+  cb.top = c->top_meas;
+  cb.pad = 0;
   if (c->opt.bias_correct && c->T_bias > k + 1) {
     const double ek = eta_host(k, c->T_bias), e1 = eta_host(1, c->T_bias),
                  ekm = eta_host(k - 1, c->T_bias);
@@ -1499,6 +1503,182 @@ extern "C" thoi_status thoi_batch_measures(thoi_ctx* const* ctxs, int32_t D, int
   if (prec != THOI_F32_FIX64 || top_k > KBATCH_MAX || D > 65535)
     return batch_sequential(ctxs, D, kmin, kmax, out, stats, stream);
   return batch_graph(ctxs, D, kmin, kmax, out, stats, stream);
+}
+
+// ------------------------------------------------------------------ API: greedy search
+// Greedy search (Methods, "Heuristics", "Greedy Algorithm"): the kappa best
+// nplets of order k0 by an exhaustive pass, then order by order every
+// selected set grows by each variable it lacks, the distinct candidates are
+// evaluated, and the kappa best become the next selection.  Evaluation in the
+// FP64 path on the device (shared-memory FP64 kernels), selection on the
+// device by the per-block top lists and their merge, ranked by one measure;
+// ties go to the smallest lexicographic rank.  The host only forms and
+// de-duplicates the candidate sets (at most kappa * N per order).
+static uint64_t set_rank(int N, const int* idx, int k) {
+  uint64_t rp = 0;
+  for (int i = 0; i < k; i++) rp += binom_host(N - 1 - idx[i], k - i);
+  return binom_host(N, k) - 1 - rp;
+}
+
+static uint64_t rank_to_mask(int N, int k, uint64_t rank) {
+  int32_t idx[THOI_MAX_N];
+  int32_t kk = 0;
+  const int32_t ord = k;
+  if (thoi_unrank(N, &ord, 1, rank, idx, &kk) != THOI_OK) return 0;
+  uint64_t m = 0;
+  for (int i = 0; i < kk; i++) m |= 1ull << idx[i];
+  return m;
+}
+
+extern "C" thoi_status thoi_greedy(thoi_ctx* c, int32_t k0, int32_t k1, int32_t kappa,
+                                   int32_t measure, int32_t maximize, uint64_t* sets_out,
+                                   double* values_out, thoi_stats* stats, void* stream) {
+  if (!c || !sets_out || !values_out || k0 < 1 || k1 < k0 || k1 > c->N || kappa < 1 ||
+      kappa > THOI_MAX_TOP_M || measure < THOI_H || measure > THOI_S)
+    return THOI_ERR_INVALID_ARG;
+  const int N = c->N;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int side = maximize ? 0 : 1;
+  const int levels = k1 - k0 + 1;
+  for (size_t q = 0; q < (size_t)levels * kappa; q++) {
+    sets_out[q] = 0;
+    values_out[q] = NAN;
+  }
+  // run the FP64 path with the requested top lists; restored on every exit
+  struct Saved {
+    thoi_ctx* c;
+    thoi_options opt;
+    int top_meas;
+    ~Saved() {
+      c->opt = opt;
+      c->top_meas = top_meas;
+    }
+  } saved{c, c->opt, c->top_meas};
+  c->opt.precision = THOI_F64;
+  c->opt.top_m = kappa;
+  c->opt.profile = 0;
+  c->top_meas = measure;
+  const size_t rec_bytes = thoi_records_bytes(1, kappa);
+  std::vector<unsigned char> host(rec_bytes);
+  thoi_status st = grow(&c->rec_buf, &c->rec_cap, rec_bytes);
+  if (st != THOI_OK) return st;
+  thoi_order_record* recs = (thoi_order_record*)c->rec_buf;
+  TopEnt* tops = (TopEnt*)(c->rec_buf + sizeof(thoi_order_record));
+  std::vector<uint64_t> parents;
+  uint64_t evaluated = 0;
+  int launches = 0;
+  auto take = [&](int level, int k) -> thoi_status {
+    CK(cudaMemcpyAsync(host.data(), c->rec_buf, rec_bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const thoi_order_record* R = (const thoi_order_record*)host.data();
+    const thoi_top_entry* T =
+        (const thoi_top_entry*)(host.data() + sizeof(thoi_order_record)) + (size_t)side * kappa;
+    const int n = R->top_count < kappa ? R->top_count : kappa;
+    parents.clear();
+    for (int i = 0; i < n; i++) {
+      const uint64_t m = rank_to_mask(N, k, T[i].id);
+      sets_out[(size_t)level * kappa + i] = m;
+      values_out[(size_t)level * kappa + i] = T[i].value;
+      parents.push_back(m);
+    }
+    return THOI_OK;
+  };
+  // order k0: exhaustive
+  {
+    const int32_t ord = k0;
+    int nl = 0;
+    st = enqueue_measures(c, &ord, 1, 0, binom_host(N, k0), THOI_RED_PER_ORDER, nullptr, recs,
+                          tops, s, &nl);
+    if (st != THOI_OK) return st;
+    launches += nl;
+    evaluated += binom_host(N, k0);
+    st = take(0, k0);
+    if (st != THOI_OK) return st;
+  }
+  // orders k0+1 .. k1: expansion of the selection
+  const int ref_cap = c->num_sms * REFACTOR_BLOCKS_PER_SM;
+  PartRec* part = nullptr;
+  TopEnt* ptop = nullptr;
+  unsigned long long* d_ids = nullptr;
+  unsigned long long* d_cnt = nullptr;
+  double* b64 = nullptr;
+  struct Bufs {
+    void* p[5];
+    ~Bufs() {
+      for (void* q : p) if (q) cudaFree(q);
+    }
+  } bufs{{nullptr, nullptr, nullptr, nullptr, nullptr}};
+  const size_t cap = (size_t)kappa * N;
+  const size_t lstride = (cap + 63) / 64 * 64;
+  CK(cudaMalloc(&part, ref_cap * sizeof(PartRec)));
+  bufs.p[0] = part;
+  CK(cudaMalloc(&ptop, (size_t)ref_cap * 2 * kappa * sizeof(TopEnt)));
+  bufs.p[1] = ptop;
+  CK(cudaMalloc(&d_ids, cap * sizeof(unsigned long long)));
+  bufs.p[2] = d_ids;
+  CK(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
+  bufs.p[3] = d_cnt;
+  CK(cudaMalloc(&b64, 3 * lstride * sizeof(double)));
+  bufs.p[4] = b64;
+  std::vector<uint64_t> cand;
+  std::vector<unsigned long long> ids;
+  for (int k = k0 + 1; k <= k1; k++) {
+    cand.clear();
+    for (uint64_t p : parents)
+      for (int v = 0; v < N; v++)
+        if (!(p >> v & 1ull)) cand.push_back(p | 1ull << v);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    if (cand.empty()) break;
+    ids.resize(cand.size());
+    for (size_t i = 0; i < cand.size(); i++) {
+      int idx[THOI_MAX_N];
+      int q = 0;
+      for (int v = 0; v < N; v++)
+        if (cand[i] >> v & 1ull) idx[q++] = v;
+      ids[i] = set_rank(N, idx, k);
+    }
+    const unsigned long long n = ids.size();
+    CK(cudaMemcpyAsync(d_ids, ids.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_cnt, &n, sizeof(n), cudaMemcpyHostToDevice, s));
+    SlotRange r;
+    r.k = k;
+    r.off = 0;
+    r.r0 = 0;
+    r.r1 = binom_host(N, k);
+    NpletArgs a = base_args(c, r);
+    a.mode = 2;
+    a.flag_ids = d_ids;
+    a.flag_count = d_cnt;
+    a.flag_cap = n;
+    a.cancel = c->d_cancel;
+    int grid = 0;
+    CK(launch_nplet_f64s(a, true, b64, lstride, c->num_sms, s, &grid,
+                         c->num_sms * MAX_BLOCKS_PER_SM_OUT));
+    CK(launch_reduce_list64(b64, lstride, d_ids, d_cnt, n, a.cmb, kappa, part, ptop, c->num_sms,
+                            ref_cap, s, &grid));
+    MergeDescs D;
+    memset(&D, 0, sizeof D);
+    D.d[0].p32_off = 0;
+    D.d[0].g32 = grid;
+    D.d[0].k = k;
+    D.d[0].cmb = a.cmb;
+    CK(launch_merge(D, 1, part, ptop, part, ptop, kappa, recs, tops, s));
+    launches += 3;
+    evaluated += n;
+    st = take(k - k0, k);
+    if (st != THOI_OK) return st;
+  }
+  int hs = 0;
+  CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->nplets = evaluated;
+    stats->launches = launches;
+  }
+  if (hs & ST_CANCELLED) return THOI_ERR_CANCELLED;
+  return THOI_OK;  // candidates that are not positive definite are left out, not fatal
 }
 
 // ------------------------------------------------------------------ API: autotune

@@ -13,6 +13,7 @@ import pytest
 import scipy.special
 
 import oracle
+import workloads
 
 LOG2PIE_HALF = 1.4189385332046727  # entropy of N(0,1), the 1.4189 of the padding section
 
@@ -456,3 +457,45 @@ def test_planted_signs():
             prev = ci
         out, _ = oracle.measures_ids(S, [k], [rk])
         assert np.sign(out[3, 0]) == sign
+
+
+# ------------------------------------------------------------------ greedy search (Methods, "Greedy Algorithm")
+def test_subset_rank_inverts_enumeration():
+    for N in (1, 5, 9):
+        for k in range(1, N + 1):
+            subs = oracle.enumerate_subsets(N, [k])
+            got = [oracle.subset_rank(N, [int(x) for x in row]) for row in subs]
+            assert got == list(range(len(subs)))
+
+
+@pytest.mark.parametrize("measure,maximize", [("O", True), ("O", False), ("S", True), ("TC", False)])
+def test_greedy_covering_kappa_equals_exhaustive(measure, maximize):
+    # with kappa at least the number of subsets of every order, the selection
+    # holds every set, so each order's result is the exhaustive top list
+    rng = np.random.default_rng(31)
+    S = workloads.random_corr(rng, 8)
+    m = oracle.MEASURES.index(measure)
+    res = oracle.greedy(S, 2, 7, 70, measure, maximize)
+    for (sets, vals), k in zip(res, range(2, 8)):
+        v, _ = oracle.measures(S, [k])
+        ids = np.arange(v.shape[1], dtype=np.uint64)
+        key = -v[m] if maximize else v[m]
+        order = np.lexsort((ids, key))
+        ref = [tuple(int(x) for x in r) for r in oracle.unrank_ids(8, [k], ids[order])]
+        assert sets == ref
+        np.testing.assert_array_equal(vals, v[m][order])
+
+
+def test_greedy_selection_properties():
+    rng = np.random.default_rng(32)
+    S = workloads.random_corr(rng, 12)
+    res = oracle.greedy(S, 3, 8, 10, "O", False)
+    prev = None
+    for (sets, vals), k in zip(res, range(3, 9)):
+        assert all(len(s) == k for s in sets)
+        assert len(set(sets)) == len(sets) == 10
+        assert np.all(np.diff(vals) >= 0)  # best (smallest) first
+        if prev is not None:
+            # every selected set grew from a set selected one order below
+            assert all(any(set(p) < set(s) for p in prev) for s in sets)
+        prev = sets
