@@ -1655,8 +1655,11 @@ extern "C" thoi_status thoi_greedy(thoi_ctx* c, int32_t k0, int32_t k1, int32_t 
     int grid = 0;
     CK(launch_nplet_f64s(a, true, b64, lstride, c->num_sms, s, &grid,
                          c->num_sms * MAX_BLOCKS_PER_SM_OUT));
+    // few candidates per order: a few blocks, so that the merge folds few lists
+    int red_blocks = (int)(n / 4096) + 1;
+    if (red_blocks > ref_cap) red_blocks = ref_cap;
     CK(launch_reduce_list64(b64, lstride, d_ids, d_cnt, n, a.cmb, kappa, part, ptop, c->num_sms,
-                            ref_cap, s, &grid));
+                            red_blocks, s, &grid));
     MergeDescs D;
     memset(&D, 0, sizeof D);
     D.d[0].p32_off = 0;
