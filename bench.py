@@ -566,6 +566,42 @@ def run_extra(args, dev, stream, flush, peak, rank):
                                  "sample": f"the whole search, {dt:.2f} s",
                                  "same_selection": bool(same)}
     out["greedy_grad60"] = entry
+
+    # simulated annealing (Methods, "Simulated Annealing Algorithm"): N=60,
+    # 16384 chains of 2000 steps over orders 3..20, maximising O, FP64 energies
+    klo, khi, chains, iters, T0, alpha = 3, 20, 16384, 2000, 0.2, 0.998
+    with P.Context(torch.as_tensor(X, device=dev)) as c:
+        ms = ev_time(lambda: P.thoi_anneal(c.h, klo, khi, chains, iters, T0, alpha, "O", True, 1))
+        fm, fv, bm, bv, st = P.thoi_anneal(c.h, klo, khi, chains, iters, T0, alpha, "O", True, 1)
+    n_eval = int(st.nplets)
+    sizes = [bin(int(m)).count("1") for m in fm]
+    kbar = sum(sizes) / len(sizes)
+    fl = n_eval * flops_model(kbar)
+    ach = fl / (ms / 1e3) / 1e12
+    entry = {"workload": f"N=60, T=2000 random-correlation Gaussian; {chains} annealing chains x "
+                         f"{iters} steps over orders {klo}..{khi}, maximising O "
+                         f"({n_eval:,} FP64 energies)",
+             "value": n_eval / (ms / 1e3), "unit": "nplets/s", "ms_per_call": ms,
+             "best_O": float(max(bv)), "accepted": int(st.n_refactored),
+             "roofline": {"bound": "fp64", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",
+                          "frac": ach / 1.25,
+                          "peak_basis": "nominal GB300 FP64 (1.25 TFLOP/s)",
+                          "flops_model": f"2/3k^3+2k^2 per energy at the mean final order "
+                                         f"{kbar:.1f}"}}
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        S = oracle.copula_cov(X)
+        n_ref = 4
+        t0 = time.perf_counter()
+        ref = oracle.anneal(S, klo, khi, n_ref, iters, T0, alpha, "O", True, 1)
+        dt = time.perf_counter() - t0
+        same = [tuple(i for i in range(64) if int(m) >> i & 1) for m in bm[:n_ref]] == ref[2]
+        entry["cpu_baseline"] = {"value": n_ref * (iters + 1) / dt, "unit": "nplets/s",
+                                 "cores": 1, "kind": "oracle",
+                                 "sample": f"the first {n_ref} chains ({n_ref * (iters + 1)} "
+                                           f"energies), {dt:.2f} s, one thread",
+                                 "same_best_sets": bool(same)}
+    out["anneal_grad60"] = entry
     return out
 
 

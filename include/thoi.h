@@ -298,6 +298,32 @@ thoi_status thoi_greedy(thoi_ctx* ctx, int32_t k0, int32_t k1, int32_t kappa, in
                         int32_t maximize, uint64_t* sets_out, double* values_out,
                         thoi_stats* stats, void* stream);
 
+/* Simulated annealing (Methods, "Heuristics", "Simulated Annealing
+ * Algorithm").  n_chains independent chains, each a set of k_lo..k_hi
+ * variables (k_hi <= 32), run `iters` steps on the device:
+ *  - start: a random set (size uniform in k_lo..k_hi, members by a partial
+ *    Fisher-Yates shuffle);
+ *  - move: within one order (k_lo == k_hi) swap a member for a non-member;
+ *    across orders add or remove a random variable while the size stays in
+ *    range, else swap;
+ *  - energy E = the measure (maximize != 0) or its negative, in FP64; sets
+ *    that are not positive definite are rejected;
+ *  - acceptance: always if E rises, else with probability exp(dE / Temp)
+ *    (the usual Metropolis rule; the paper's printed exp(-dE / Temp) would
+ *    accept every worse move);
+ *  - cooling: Temp = T0 * alpha^step.
+ * Random numbers: draw (chain, step, slot) is the
+ * ((chain * (iters+1) + step) * 64 + slot)-th output of SplitMix64 seeded with
+ * `seed` (integers in [0, n): (z * n) >> 64; uniforms: (z >> 11) * 2^-53), so a
+ * run is reproducible and checkable draw for draw.
+ * Outputs (host, n_chains each): the final and the best set of every chain as
+ * bit masks and their measure values.  stats->nplets = energies evaluated,
+ * stats->n_refactored = accepted moves.  Synchronises `stream`. */
+thoi_status thoi_anneal(thoi_ctx* ctx, int32_t k_lo, int32_t k_hi, int32_t n_chains, int32_t iters,
+                        double T0, double alpha, int32_t measure, int32_t maximize, uint64_t seed,
+                        uint64_t* final_masks, double* final_values, uint64_t* best_masks,
+                        double* best_values, thoi_stats* stats, void* stream);
+
 /* Host-only sharding helpers (no device work, no CUDA calls).  Nplets are
  * independent (Methods, "Parallel and batched computation of HOI"), so one
  * request splits into contiguous global-id ranges evaluated by separate

@@ -329,3 +329,88 @@ def greedy(Sigma: np.ndarray, k0: int, k1: int, kappa: int, measure: str = "O",
         sets, best = pick(ids, vals[m], notpd, k)
         out.append((sets, best))
     return out
+
+
+# ------------------------------------------------------------------ simulated annealing
+M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, c: int) -> int:
+    """Output c (0-based) of the SplitMix64 generator seeded with `seed`:
+    the finaliser of seed + (c + 1) * 0x9E3779B97F4A7C15 (mod 2^64)."""
+    z = (seed + (c + 1) * 0x9E3779B97F4A7C15) & M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def anneal(Sigma: np.ndarray, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float,
+           alpha: float, measure: str = "O", maximize: bool = True, seed: int = 0):
+    """Simulated annealing (Methods, "Heuristics", "Simulated Annealing
+    Algorithm"), chain by chain, with the moves, draws and acceptance rule
+    stated for thoi_anneal: draw (chain, step, slot) is SplitMix64 output
+    ((chain * (iters+1) + step) * 64 + slot); integers (z * n) >> 64; uniforms
+    (z >> 11) * 2^-53; accept when the energy rises, else with probability
+    exp(dE / Temp).  Returns (final sets, final values, best sets, best
+    values) with sets as sorted tuples."""
+    S = np.ascontiguousarray(Sigma, dtype=np.float64)
+    N = S.shape[0]
+    m = MEASURES.index(measure)
+    sgn = 1.0 if maximize else -1.0
+
+    def value(members):
+        k = len(members)
+        vals, notpd = measures_ids(S, [k], np.array([subset_rank(N, members)], dtype=np.uint64))
+        return float("nan") if notpd[0] else float(vals[m, 0])
+
+    out = ([], [], [], [])
+    for ch in range(n_chains):
+        base = ch * (iters + 1)
+
+        def draw(step, slot):
+            return splitmix64(seed, (base + step) * 64 + slot)
+
+        size = k_lo + ((draw(0, 0) * (k_hi - k_lo + 1)) >> 64)
+        perm = list(range(N))
+        for j in range(size):
+            r = j + ((draw(0, 1 + j) * (N - j)) >> 64)
+            perm[j], perm[r] = perm[r], perm[j]
+        cur = tuple(sorted(perm[:size]))
+        E = sgn * value(cur)
+        best, bestE = cur, E
+        T = T0
+        for it in range(1, iters + 1):
+            members = list(cur)
+            size = len(members)
+            prop = cur
+            swap = k_lo == k_hi
+            if not swap:
+                v = (draw(it, 0) * N) >> 64
+                if v not in cur and size < k_hi:
+                    prop = tuple(sorted(members + [v]))
+                elif v in cur and size > k_lo:
+                    prop = tuple(x for x in members if x != v)
+                else:
+                    swap = True
+            if swap and size < N:
+                v = members[(draw(it, 1) * size) >> 64]
+                outside = [x for x in range(N) if x not in cur]
+                w = outside[(draw(it, 2) * (N - size)) >> 64]
+                prop = tuple(sorted([x for x in members if x != v] + [w]))
+            En = sgn * value(prop)
+            if En == En:
+                dE = En - E
+                ok = dE > 0.0
+                if not ok:
+                    p = 1.0 if dE == 0.0 else math.exp(dE / T)
+                    ok = (draw(it, 3) >> 11) * 2.0 ** -53 < p
+                if ok:
+                    cur, E = prop, En
+                    if E > bestE:
+                        best, bestE = cur, E
+            T *= alpha
+        out[0].append(cur)
+        out[1].append(sgn * E)
+        out[2].append(best)
+        out[3].append(sgn * bestE)
+    return out

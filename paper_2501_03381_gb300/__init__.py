@@ -111,6 +111,9 @@ def load(build_if_missing: bool = True):
             "thoi_greedy": (ctypes.c_int, [vp, i32, i32, i32, i32, i32, vp, vp,
                                            ctypes.POINTER(thoi_stats), vp]),
             "thoi_merge_records": (ctypes.c_int, [vp, i32, i32, i32, vp]),
+            "thoi_anneal": (ctypes.c_int, [vp, i32, i32, i32, i32, ctypes.c_double,
+                                           ctypes.c_double, i32, i32, u64, vp, vp, vp, vp,
+                                           ctypes.POINTER(thoi_stats), vp]),
             "thoi_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -393,6 +396,22 @@ def thoi_greedy(h, k0: int, k1: int, kappa: int, measure: str = "O", maximize: b
     return masks, values, st
 
 
+def thoi_anneal(h, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float, alpha: float,
+                measure: str = "O", maximize: bool = True, seed: int = 0, stream=None):
+    """Simulated annealing chains on the device.  Returns (final_masks,
+    final_values, best_masks, best_values, stats), n_chains entries each."""
+    fm = np.zeros(n_chains, dtype=np.uint64)
+    fv = np.zeros(n_chains, dtype=np.float64)
+    bm = np.zeros(n_chains, dtype=np.uint64)
+    bv = np.zeros(n_chains, dtype=np.float64)
+    st = thoi_stats()
+    _check(load().thoi_anneal(h, k_lo, k_hi, n_chains, iters, T0, alpha, MEASURES.index(measure),
+                              int(bool(maximize)), seed & ((1 << 64) - 1), _ptr(fm), _ptr(fv),
+                              _ptr(bm), _ptr(bv), ctypes.byref(st), _stream_ptr(stream)),
+           "thoi_anneal")
+    return fm, fv, bm, bv, st
+
+
 def thoi_autotune(h, kmin: int, kmax: int, cache_path: str | None = None, stream=None):
     _check(load().thoi_autotune(h, kmin, kmax, cache_path.encode() if cache_path else None,
                                 _stream_ptr(stream)), "thoi_autotune")
@@ -471,6 +490,12 @@ class Context:
                              out_f64=bool(self.opt.out_f64) if self.opt.out_f64 >= 0
                              else self.opt.precision == THOI_F64,
                              top_m=self.opt.top_m, stream=stream)
+
+    def anneal(self, k_lo, k_hi, n_chains, iters, T0, alpha, measure="O", maximize=True, seed=0,
+               stream=None):
+        fm, fv, bm, bv, _ = thoi_anneal(self.h, k_lo, k_hi, n_chains, iters, T0, alpha, measure,
+                                        maximize, seed, stream)
+        return fm, fv, bm, bv
 
     def greedy(self, k0, k1, kappa, measure="O", maximize=True, stream=None):
         masks, values, _ = thoi_greedy(self.h, k0, k1, kappa, measure, maximize, stream)

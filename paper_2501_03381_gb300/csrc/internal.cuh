@@ -192,6 +192,15 @@ cudaError_t launch_grad_pass(const NpletArgs& a, double* Gpart, int grid, int me
 cudaError_t launch_grad_finish(const double* Gpart, int nblk, const double* sig64, int N, float* out,
                                cudaStream_t s);
 
+// Simulated annealing: n_chains independent chains, one thread each (see
+// anneal.cu); cmb_tab[k] = combine constants of order k (k <= k_hi <= 32).
+cudaError_t launch_anneal(const double* R64, const double* ls, int N, int klo, int khi,
+                          const Combine* cmb_tab, int n_chains, int iters, double T0, double alpha,
+                          int measure, int maximize, unsigned long long seed,
+                          unsigned long long* final_mask, double* final_val,
+                          unsigned long long* best_mask, double* best_val,
+                          unsigned long long* accepted, cudaStream_t s);
+
 // ------------------------------------------------------------------ multi-dataset batch
 // Many datasets of uneven (N, T) in one graph: per order k one persistent
 // nplet launch walks a list of tiles (dataset, rank range) of every dataset,

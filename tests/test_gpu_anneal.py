@@ -1,0 +1,48 @@
+"""Simulated annealing chains on the device against the oracle's chains,
+draw for draw (same counter-based generator, same moves, FP64 energies)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+import paper_2501_03381_gb300 as P  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _sets(masks):
+    return [tuple(i for i in range(64) if int(m) >> i & 1) for m in masks]
+
+
+@pytest.mark.parametrize("klo,khi,measure,maximize", [(3, 10, "O", True), (3, 10, "O", False),
+                                                      (6, 6, "S", True), (4, 9, "TC", False)])
+def test_anneal_matches_oracle(klo, khi, measure, maximize):
+    S = workloads.random_corr(np.random.default_rng(61), 14)
+    chains, iters, T0, alpha, seed = 24, 80, 0.3, 0.96, 12345
+    ref = oracle.anneal(S, klo, khi, chains, iters, T0, alpha, measure, maximize, seed)
+    with P.Context(Sigma=S) as c:
+        fm, fv, bm, bv = c.anneal(klo, khi, chains, iters, T0, alpha, measure, maximize, seed)
+    assert _sets(fm) == ref[0]
+    assert _sets(bm) == ref[2]
+    np.testing.assert_allclose(fv, ref[1], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(bv, ref[3], rtol=0, atol=1e-10)
+
+
+def test_anneal_wide_masks():
+    S = workloads.random_corr(np.random.default_rng(62), 40)
+    ref = oracle.anneal(S, 3, 12, 8, 40, 0.5, 0.9, "O", True, 77)
+    with P.Context(Sigma=S) as c:
+        fm, fv, bm, bv = c.anneal(3, 12, 8, 40, 0.5, 0.9, "O", True, 77)
+    assert _sets(fm) == ref[0] and _sets(bm) == ref[2]
+    np.testing.assert_allclose(bv, ref[3], rtol=0, atol=1e-10)
+
+
+def test_anneal_arguments():
+    S = workloads.random_corr(np.random.default_rng(63), 8)
+    with P.Context(Sigma=S) as c:
+        for bad in [(3, 9, 4, 10, 1.0, 0.9), (5, 4, 4, 10, 1.0, 0.9), (3, 5, 0, 10, 1.0, 0.9),
+                    (3, 5, 4, 10, 0.0, 0.9)]:
+            with pytest.raises(P.ThoiError):
+                c.anneal(*bad)

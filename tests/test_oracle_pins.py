@@ -499,3 +499,32 @@ def test_greedy_selection_properties():
             # every selected set grew from a set selected one order below
             assert all(any(set(p) < set(s) for p in prev) for s in sets)
         prev = sets
+
+
+# ------------------------------------------------------------------ simulated annealing (Methods, "Simulated Annealing Algorithm")
+def test_splitmix64_published_outputs():
+    # the first outputs of SplitMix64 seeded with 0, as published with the generator
+    assert [oracle.splitmix64(0, i) for i in range(3)] == [
+        0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_anneal_zero_temperature_only_climbs():
+    # with a vanishing temperature a worse move is never taken, so the final
+    # set of every chain is its best one
+    S = workloads.random_corr(np.random.default_rng(51), 12)
+    fin, fval, best, bval = oracle.anneal(S, 3, 8, 6, 40, 1e-300, 0.9, "O", True, seed=3)
+    assert fin == best
+    np.testing.assert_array_equal(fval, bval)
+
+
+def test_anneal_start_and_ranges():
+    S = workloads.random_corr(np.random.default_rng(52), 10)
+    fin, fval, best, bval = oracle.anneal(S, 4, 7, 20, 0, 1.0, 0.9, "S", False, seed=9)
+    assert fin == best
+    for s in fin:
+        assert 4 <= len(s) <= 7 and len(set(s)) == len(s) and all(0 <= x < 10 for x in s)
+    fin, _, best, bval = oracle.anneal(S, 5, 5, 10, 50, 0.3, 0.95, "O", False, seed=1)
+    assert all(len(s) == 5 for s in fin + best)
+    # minimising: the best value is no worse than the final one
+    assert all(b <= f + 1e-15 for b, f in zip(bval, oracle.anneal(S, 5, 5, 10, 50, 0.3, 0.95, "O",
+                                                                   False, seed=1)[1]))
