@@ -568,8 +568,8 @@ def run_extra(args, dev, stream, flush, peak, rank):
     out["greedy_grad60"] = entry
 
     # simulated annealing (Methods, "Simulated Annealing Algorithm"): N=60,
-    # 16384 chains of 2000 steps over orders 3..20, maximising O, FP64 energies
-    klo, khi, chains, iters, T0, alpha = 3, 20, 16384, 2000, 0.2, 0.998
+    # 4096 chains of 1000 steps over orders 3..20, maximising O, FP64 energies
+    klo, khi, chains, iters, T0, alpha = 3, 20, 4096, 1000, 0.2, 0.996
     with P.Context(torch.as_tensor(X, device=dev)) as c:
         ms = ev_time(lambda: P.thoi_anneal(c.h, klo, khi, chains, iters, T0, alpha, "O", True, 1))
         fm, fv, bm, bv, st = P.thoi_anneal(c.h, klo, khi, chains, iters, T0, alpha, "O", True, 1)
