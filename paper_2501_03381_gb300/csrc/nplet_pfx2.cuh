@@ -13,8 +13,17 @@
 
 namespace thoi {
 
+// Minimum resident blocks per SM: three (168 registers) up to order 14,
+// measured 2-10% faster there despite a few spilled registers at 13 and 14;
+// above, the compiler's own allocation (up to 255 registers, two blocks).
+template <int K>
+struct Pfx2Blocks {
+  static constexpr int value = K <= 14 ? 3 : 1;
+};
+
 template <int K, typename M>
-__global__ void __launch_bounds__(RED_NT) k_nplet_pfx2(const NpletArgs a, const int chunk) {
+__global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(const NpletArgs a,
+                                                                            const int chunk) {
   constexpr int P = K - 1;   // variables before the last one
   constexpr int GP = K - 2;  // grand-prefix size
   constexpr int GQ = K - 3;  // grand-prefix indices below its largest index g
