@@ -1,0 +1,78 @@
+"""Parity at the bench's full size and launch configuration: the N = 30
+exhaustive workload (1,073,741,358 nplets of orders 3..30), per-order records
+with top-256 O lists, launch shapes from the autotuner (dense, one-level and
+two-level prefix-shared kernels).  The oracle cannot evaluate every nplet, so
+the records are checked through what it can compute one by one (every
+reported extreme and top-list entry at its id) and against the GPU FP64
+path's records of the same workload."""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+import paper_2501_03381_gb300 as P  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-4
+TOL64 = 1e-10
+TOP_M = 256
+
+
+def test_planted30_records_full_size():
+    X, orders = workloads.planted30()
+    S = oracle.copula_cov(X)
+    Xd = torch.as_tensor(X, device="cuda")
+    with P.Context(Xd, top_m=TOP_M) as c32, P.Context(Xd, top_m=TOP_M, precision="f64") as c64:
+        path = os.path.join(tempfile.mkdtemp(), "tune.json")
+        P.thoi_autotune(c32.h, 3, 30, path)
+        (r32, hi32, lo32), st32 = c32.measures(orders, reduction="per_order")
+        (r64, hi64, lo64), _ = c64.measures(orders, reduction="per_order")
+    assert st32.nplets == sum(math.comb(30, k) for k in orders)
+    ids_all, vals_all = [], []
+    for q, k in enumerate(orders):
+        a, b = r32[q], r64[q]
+        assert int(a["k"]) == int(b["k"]) == k
+        assert int(a["count"]) == int(b["count"]) == math.comb(30, k)
+        assert int(a["n_not_pd"]) == int(b["n_not_pd"]) == 0
+        # FP32 path with the FP64 re-factor against the FP64 path
+        np.testing.assert_allclose(a["min"], b["min"], rtol=0, atol=TOL32)
+        np.testing.assert_allclose(a["max"], b["max"], rtol=0, atol=TOL32)
+        np.testing.assert_allclose(a["mean"], b["mean"], rtol=0, atol=TOL32)
+        n = int(a["top_count"])
+        assert n == int(b["top_count"]) == min(TOP_M, math.comb(30, k))
+        np.testing.assert_allclose(hi32[q]["value"][:n], hi64[q]["value"][:n], rtol=0, atol=TOL32)
+        np.testing.assert_allclose(lo32[q]["value"][:n], lo64[q]["value"][:n], rtol=0, atol=TOL32)
+        # top lists sorted, distinct ids
+        assert np.all(np.diff(hi32[q]["value"][:n]) <= 0) and np.all(np.diff(lo32[q]["value"][:n]) >= 0)
+        assert len(set(hi32[q]["id"][:n].tolist())) == n and len(set(lo32[q]["id"][:n].tolist())) == n
+        # ids to check against the oracle one by one
+        ids_all += [a["argmin"], a["argmax"], b["argmin"], b["argmax"],
+                    hi32[q]["id"][:n], lo32[q]["id"][:n], hi64[q]["id"][:n], lo64[q]["id"][:n]]
+        vals_all += [a["min"], a["max"], b["min"], b["max"],
+                     hi32[q]["value"][:n], lo32[q]["value"][:n], hi64[q]["value"][:n],
+                     lo64[q]["value"][:n]]
+    # every reported id carries its reported value (the five measures for the
+    # extremes, O for the top lists)
+    ids = np.concatenate([np.asarray(x, dtype=np.uint64) for x in ids_all])
+    ref, fl = oracle.measures_ids(S, orders, ids)
+    assert not fl.any()
+    pos = 0
+    for q in range(len(orders)):
+        n = int(r32[q]["top_count"])
+        for part, tol in ((0, TOL32), (1, TOL32), (2, TOL64), (3, TOL64)):
+            v = vals_all[8 * q + part]
+            got = ref[np.arange(5), pos + np.arange(5)]
+            np.testing.assert_allclose(got, v, rtol=0, atol=tol)
+            pos += 5
+        for part, tol in ((4, TOL32), (5, TOL32), (6, TOL64), (7, TOL64)):
+            v = vals_all[8 * q + part]
+            np.testing.assert_allclose(ref[3, pos:pos + n], v, rtol=0, atol=tol)
+            pos += n
+    assert pos == len(ids)
