@@ -172,11 +172,17 @@ __device__ void f64g_body(const NpletArgs& a, double* __restrict__ b64, unsigned
     int E1 = 0;
     bool bad = false;
     for (int p = 0; p < k; p++) {
-      const double d = AG(p, p);
-      bad |= !(d > 0.0);
-      P1 *= d;
-      if ((p & 7) == 7 || p == k - 1) renorm(P1, E1, bad);
-      const double rd = 1.0 / d;
+      // the owner of row p divides once and publishes 1/D_p on the diagonal
+      // (an FP64 division is a long sequence on the narrow FP64 pipe); lane
+      // 0 keeps the product of the 1/D_p, so log det R_S = -log(product)
+      if (g == p % G) AG(p, p) = 1.0 / AG(p, p);
+      __syncwarp(gmask);
+      const double rd = AG(p, p);
+      if (g == 0) {
+        bad |= !(rd > 0.0) | !(rd < pinf<double>());  // D_p <= 0, zero, or not finite
+        P1 *= rd;
+        if ((p & 7) == 7 || p == k - 1) renorm(P1, E1, bad);
+      }
       const int i0 = p + 1 + ((g - (p + 1) % G) + G) % G;  // first owned row > p
       for (int i = i0; i < k; i += G) {
         const double u = AG(i, p) * rd;
@@ -184,7 +190,6 @@ __device__ void f64g_body(const NpletArgs& a, double* __restrict__ b64, unsigned
       }
       __syncwarp(gmask);
       for (int i = i0; i < k; i += G) AG(i, p) *= rd;
-      if (g == p % G) AG(p, p) = rd;
       __syncwarp(gmask);
     }
     // V = L^-1 in place
@@ -220,7 +225,7 @@ __device__ void f64g_body(const NpletArgs& a, double* __restrict__ b64, unsigned
     }
     bad |= __any_sync(gmask, bad2);
     if (g == 0) {
-      const double lr = log_of(P1, E1), sp = log_of(P2, E2);
+      const double lr = -log_of(P1, E1), sp = log_of(P2, E2);
       if (bad) atomicOr(a.status, ST_NOT_PD);
       if (a.mode == 0) {
         double v[5];
