@@ -15,6 +15,14 @@ Paper passages followed (arXiv 2501.03381):
   * batch-level reduction -- Fig. 1A caption (per-batch custom function,
                              e.g. the minimum O), read as the fixed set
                              min/max/mean/count/count(O<0)/top-M per order.
+  * greedy search         -- Methods, "Heuristics", "Greedy Algorithm"
+  * simulated annealing   -- Methods, "Heuristics", "Simulated Annealing
+                             Algorithm"
+  * group objectives      -- Results, "Leveraging Gaussian entropy
+                             estimators with batch processing" (average O
+                             across datasets); Methods, "Heuristics" (the
+                             searches take several datasets) and "fMRI
+                             analysis" (paired Cohen's d between conditions)
 """
 from __future__ import annotations
 
@@ -295,18 +303,19 @@ def subset_rank(N: int, members) -> int:
     return math.comb(N, k) - 1 - sum(math.comb(N - 1 - c, k - i) for i, c in enumerate(members))
 
 
-def greedy(Sigma: np.ndarray, k0: int, k1: int, kappa: int, measure: str = "O",
-           maximize: bool = True):
+def greedy(Sigma, k0: int, k1: int, kappa: int, measure: str = "O",
+           maximize: bool = True, objective: str | None = None):
     """Greedy search (Methods, "Heuristics", "Greedy Algorithm"), literally:
     the kappa best nplets of order k0 from an exhaustive evaluation, then for
     each next order every selected set grows by each variable it lacks, the
     distinct candidates are evaluated, and the kappa best are kept.  Best =
     largest (or smallest) value of the measure; ties by smaller lexicographic
-    rank; nplets that are not positive definite are left out.  Returns one
-    (members list, values array) pair per order k0..k1."""
-    S = np.ascontiguousarray(Sigma, dtype=np.float64)
-    N = S.shape[0]
-    m = MEASURES.index(measure)
+    rank; nplets that are not positive definite are left out.  With a list of
+    covariances and a group objective ("mean" or "cohen_d"), the value is that
+    objective over the datasets (Methods, "Heuristics": the searches accept
+    several datasets).  Returns one (members list, values array) pair per
+    order k0..k1."""
+    by_range, by_ids, N = _evaluator(Sigma, measure, objective)
 
     def pick(ids, vals, notpd, k):
         keep = notpd == 0
@@ -317,16 +326,16 @@ def greedy(Sigma: np.ndarray, k0: int, k1: int, kappa: int, measure: str = "O",
         return sets, vals[order]
 
     out = []
-    vals, notpd = measures(S, [k0])
-    sets, best = pick(np.arange(vals.shape[1], dtype=np.uint64), vals[m], notpd, k0)
+    vals, notpd = by_range(k0)
+    sets, best = pick(np.arange(len(vals), dtype=np.uint64), vals, notpd, k0)
     out.append((sets, best))
     for k in range(k0 + 1, k1 + 1):
         cand = sorted({tuple(sorted(s + (v,))) for s in sets for v in range(N) if v not in s})
         if not cand:
             break
         ids = np.array([subset_rank(N, c) for c in cand], dtype=np.uint64)
-        vals, notpd = measures_ids(S, [k], ids)
-        sets, best = pick(ids, vals[m], notpd, k)
+        vals, notpd = by_ids(k, ids)
+        sets, best = pick(ids, vals, notpd, k)
         out.append((sets, best))
     return out
 
@@ -344,24 +353,24 @@ def splitmix64(seed: int, c: int) -> int:
     return z ^ (z >> 31)
 
 
-def anneal(Sigma: np.ndarray, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float,
-           alpha: float, measure: str = "O", maximize: bool = True, seed: int = 0):
+def anneal(Sigma, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float,
+           alpha: float, measure: str = "O", maximize: bool = True, seed: int = 0,
+           objective: str | None = None):
     """Simulated annealing (Methods, "Heuristics", "Simulated Annealing
     Algorithm"), chain by chain, with the moves, draws and acceptance rule
     stated for thoi_anneal: draw (chain, step, slot) is SplitMix64 output
     ((chain * (iters+1) + step) * 64 + slot); integers (z * n) >> 64; uniforms
     (z >> 11) * 2^-53; accept when the energy rises, else with probability
-    exp(dE / Temp).  Returns (final sets, final values, best sets, best
-    values) with sets as sorted tuples."""
-    S = np.ascontiguousarray(Sigma, dtype=np.float64)
-    N = S.shape[0]
-    m = MEASURES.index(measure)
+    exp(dE / Temp).  With a list of covariances and a group objective the
+    energy is that objective over the datasets.  Returns (final sets, final
+    values, best sets, best values) with sets as sorted tuples."""
+    _, by_ids, N = _evaluator(Sigma, measure, objective)
     sgn = 1.0 if maximize else -1.0
 
     def value(members):
         k = len(members)
-        vals, notpd = measures_ids(S, [k], np.array([subset_rank(N, members)], dtype=np.uint64))
-        return float("nan") if notpd[0] else float(vals[m, 0])
+        vals, notpd = by_ids(k, np.array([subset_rank(N, members)], dtype=np.uint64))
+        return float("nan") if notpd[0] else float(vals[0])
 
     out = ([], [], [], [])
     for ch in range(n_chains):
@@ -414,3 +423,86 @@ def anneal(Sigma: np.ndarray, k_lo: int, k_hi: int, n_chains: int, iters: int, T
         out[2].append(best)
         out[3].append(sgn * bestE)
     return out
+
+
+# ------------------------------------------------------------------ group objectives
+GROUP_OBJECTIVES = ("mean", "cohen_d")
+
+
+def group_objective(V: np.ndarray, notpd: np.ndarray, objective: str):
+    """Group objective of one measure over D datasets, per nplet.  V and notpd
+    are D x n (values and not-PD flags of each dataset).  Results,
+    "Leveraging Gaussian entropy estimators with batch processing": the nplet
+    with the smallest average O across datasets; Methods, "fMRI analysis":
+    nplets that maximise or minimise the paired Cohen's d between two
+    conditions.
+      mean    : (1/D) sum_d V[d]
+      cohen_d : D = 2P (P >= 2); dataset i (condition A) is paired with dataset
+                P + i (condition B); delta_i = V[i] - V[P + i];
+                g = mean(delta) / sd(delta), sd with the P - 1 denominator
+                (Cohen's d of paired samples)
+    Returns (g, bad): an nplet is excluded (bad = 1, g = NaN) when it is not
+    positive definite in some dataset, or, for cohen_d, when sd(delta) = 0."""
+    V = np.asarray(V, dtype=np.float64)
+    bad = np.asarray(notpd).astype(bool).any(axis=0)
+    if objective == "mean":
+        g = V.mean(axis=0)
+    elif objective == "cohen_d":
+        D = V.shape[0]
+        if D % 2 or D < 4:
+            raise ValueError("cohen_d needs D = 2P datasets with P >= 2")
+        P = D // 2
+        delta = V[:P] - V[P:]
+        sd = delta.std(axis=0, ddof=1)
+        bad = bad | ~(sd > 0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g = delta.mean(axis=0) / sd
+    else:
+        raise ValueError(f"unknown group objective {objective!r}")
+    return np.where(bad, np.nan, g), bad.astype(np.uint8)
+
+
+def _t_biases(T_bias, D: int):
+    return list(T_bias) if isinstance(T_bias, (list, tuple)) else [T_bias] * D
+
+
+def group_measures(Sigmas, orders, measure: str, objective: str, id_begin: int = 0,
+                   id_end: int | None = None, T_bias=0, nthreads: int = 0):
+    """Per-nplet group objective over the datasets' covariances (all N x N)."""
+    m = MEASURES.index(measure)
+    tb = _t_biases(T_bias, len(Sigmas))
+    res = [measures(S, orders, id_begin, id_end, tb[d], nthreads) for d, S in enumerate(Sigmas)]
+    return group_objective(np.stack([r[0][m] for r in res]), np.stack([r[1] for r in res]),
+                           objective)
+
+
+def group_measures_ids(Sigmas, orders, measure: str, objective: str, ids, T_bias=0,
+                       nthreads: int = 0):
+    """Group objective of the listed global ids."""
+    m = MEASURES.index(measure)
+    tb = _t_biases(T_bias, len(Sigmas))
+    res = [measures_ids(S, orders, ids, tb[d], nthreads) for d, S in enumerate(Sigmas)]
+    return group_objective(np.stack([r[0][m] for r in res]), np.stack([r[1] for r in res]),
+                           objective)
+
+
+def _evaluator(Sigma, measure: str, objective: str | None):
+    """(values of every nplet of order k, values of listed ids of order k, N)
+    for one covariance and a measure, or a list of covariances and a group
+    objective."""
+    if objective is None:
+        S = np.ascontiguousarray(Sigma, dtype=np.float64)
+        m = MEASURES.index(measure)
+
+        def by_range(k):
+            v, f = measures(S, [k])
+            return v[m], f
+
+        def by_ids(k, ids):
+            v, f = measures_ids(S, [k], ids)
+            return v[m], f
+
+        return by_range, by_ids, S.shape[0]
+    Ss = [np.ascontiguousarray(S, dtype=np.float64) for S in Sigma]
+    return (lambda k: group_measures(Ss, [k], measure, objective),
+            lambda k, ids: group_measures_ids(Ss, [k], measure, objective, ids), Ss[0].shape[0])

@@ -528,3 +528,125 @@ def test_anneal_start_and_ranges():
     # minimising: the best value is no worse than the final one
     assert all(b <= f + 1e-15 for b, f in zip(bval, oracle.anneal(S, 5, 5, 10, 50, 0.3, 0.95, "O",
                                                                    False, seed=1)[1]))
+
+
+# ------------------------------------------------------------------ group objectives (Results,
+# "Leveraging Gaussian entropy estimators with batch processing"; Methods, "fMRI analysis")
+def _equicorr(N, rho):
+    return np.full((N, N), rho) + (1 - rho) * np.eye(N)
+
+
+def test_group_mean_equicorrelated_closed_form():
+    # the mean TC over datasets of equicorrelated systems, against the closed
+    # form TC = -1/2 log det of each, averaged by hand
+    rhos = [0.1, 0.35, -0.05, 0.6, 0.8]
+    N = 7
+    Ss = [_equicorr(N, r) for r in rhos]
+    for k in range(2, N + 1):
+        g, bad = oracle.group_measures(Ss, [k], "TC", "mean")
+        assert not bad.any()
+        ref = sum(-0.5 * _equicorr_logdet(k, r) for r in rhos) / len(rhos)
+        np.testing.assert_allclose(g, ref, rtol=0, atol=1e-13)
+
+
+def test_group_mean_of_copies_is_the_measure():
+    rng = np.random.default_rng(61)
+    S = workloads.random_corr(rng, 9)
+    v, _ = oracle.measures(S, [3, 4, 5])
+    g, bad = oracle.group_measures([S] * 5, [3, 4, 5], "O", "mean")
+    assert not bad.any()
+    np.testing.assert_allclose(g, v[3], rtol=1e-14, atol=1e-15)
+
+
+def test_group_cohen_d_matches_paired_t_statistic():
+    # the paired Cohen's d is the paired t statistic over sqrt(P); the t
+    # statistic comes from scipy's paired t test
+    stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(62)
+    P, N = 6, 8
+    Ss = [workloads.random_corr(rng, N) for _ in range(2 * P)]
+    for meas in ("O", "S", "TC"):
+        g, bad = oracle.group_measures(Ss, [3, 5], meas, "cohen_d")
+        assert not bad.any()
+        m = oracle.MEASURES.index(meas)
+        V = np.stack([oracle.measures(S, [3, 5])[0][m] for S in Ss])
+        t = stats.ttest_rel(V[:P], V[P:], axis=0).statistic
+        np.testing.assert_allclose(g, t / math.sqrt(P), rtol=1e-12, atol=1e-13)
+
+
+def test_group_cohen_d_equicorrelated_closed_form():
+    # condition A and B are equicorrelated with subject-specific rho: each
+    # difference of TC is a closed form; d from Python's statistics module
+    import statistics
+    ra = [0.2, 0.3, 0.25, 0.5]
+    rb = [0.1, 0.22, 0.2, 0.3]
+    N, k = 6, 4
+    Ss = [_equicorr(N, r) for r in ra + rb]
+    g, _ = oracle.group_measures(Ss, [k], "TC", "cohen_d")
+    dl = [0.5 * (_equicorr_logdet(k, b) - _equicorr_logdet(k, a)) for a, b in zip(ra, rb)]
+    ref = statistics.mean(dl) / statistics.stdev(dl)
+    np.testing.assert_allclose(g, ref, rtol=1e-12)
+
+
+def test_group_cohen_d_invariants():
+    rng = np.random.default_rng(63)
+    P, N = 5, 8
+    A = [workloads.random_corr(rng, N) for _ in range(P)]
+    B = [workloads.random_corr(rng, N) for _ in range(P)]
+    g, _ = oracle.group_measures(A + B, [3, 4], "O", "cohen_d")
+    # swapping the conditions flips the sign
+    g2, _ = oracle.group_measures(B + A, [3, 4], "O", "cohen_d")
+    np.testing.assert_allclose(g2, -g, rtol=1e-13, atol=1e-14)
+    # permuting the subjects (jointly in both conditions) changes nothing
+    perm = [3, 0, 4, 1, 2]
+    g3, _ = oracle.group_measures([A[i] for i in perm] + [B[i] for i in perm], [3, 4], "O",
+                                  "cohen_d")
+    np.testing.assert_allclose(g3, g, rtol=1e-12, atol=1e-13)
+    # breaking the pairing (condition B rotated) changes the value
+    g4, _ = oracle.group_measures(A + B[1:] + B[:1], [3, 4], "O", "cohen_d")
+    assert np.max(np.abs(g4 - g)) > 1e-3
+
+
+def test_group_degenerate_and_not_pd_excluded():
+    rng = np.random.default_rng(64)
+    A = [workloads.random_corr(rng, 6) for _ in range(3)]
+    # identical conditions: every difference is 0, sd = 0 -> excluded
+    g, bad = oracle.group_measures(A + A, [3], "O", "cohen_d")
+    assert bad.all() and np.isnan(g).all()
+    # a rank-deficient dataset: nplets holding both copies of a variable are
+    # not positive definite there, and so excluded from the group
+    S = A[0].copy()
+    S[5, :] = S[4, :]
+    S[:, 5] = S[:, 4]
+    g, bad = oracle.group_measures([A[1], S, A[2]], [3], "O", "mean")
+    sets = oracle.enumerate_subsets(6, [3])
+    both = np.array([4 in r and 5 in r for r in sets])
+    np.testing.assert_array_equal(bad.astype(bool), both)
+    assert np.isnan(g[both]).all() and np.isfinite(g[~both]).all()
+    with pytest.raises(ValueError):
+        oracle.group_objective(np.zeros((3, 2)), np.zeros((3, 2)), "cohen_d")
+
+
+def test_group_greedy_covering_kappa_equals_exhaustive():
+    rng = np.random.default_rng(65)
+    Ss = [workloads.random_corr(rng, 7) for _ in range(6)]
+    for obj in ("mean", "cohen_d"):
+        res = oracle.greedy(Ss, 2, 6, 40, "O", False, objective=obj)
+        for (sets, vals), k in zip(res, range(2, 7)):
+            g, bad = oracle.group_measures(Ss, [k], "O", obj)
+            ids = np.arange(len(g), dtype=np.uint64)[bad == 0]
+            order = np.lexsort((ids, g[bad == 0]))
+            ref = [tuple(int(x) for x in r) for r in oracle.unrank_ids(7, [k], ids[order])]
+            assert sets == ref
+            np.testing.assert_array_equal(vals, g[bad == 0][order])
+
+
+def test_group_anneal_of_copies_matches_single():
+    # the mean over copies of one dataset takes the same path, draw for draw,
+    # as the single-dataset search
+    S = workloads.random_corr(np.random.default_rng(66), 10)
+    one = oracle.anneal(S, 3, 6, 4, 30, 0.05, 0.95, "O", True, seed=5)
+    grp = oracle.anneal([S, S, S], 3, 6, 4, 30, 0.05, 0.95, "O", True, seed=5, objective="mean")
+    assert one[0] == grp[0] and one[2] == grp[2]
+    np.testing.assert_allclose(grp[1], one[1], rtol=1e-14)
+    np.testing.assert_allclose(grp[3], one[3], rtol=1e-14)

@@ -24,12 +24,23 @@ Workload recipes (all draws from numpy.random.Generator(PCG64(seed))):
   T ~ U{200..2000} first, then X as in ``plain``.  Stands in for the paper's
   collection of 920 heterogeneous datasets (not available here).
 * ``plain`` with N=60, T=2000, seed 4: the differentiation workload.
+* ``paired``: P subjects x 2 conditions (datasets 0..P-1 condition A,
+  P..2P-1 condition B; subject p in both).  Subject p draws (seed 5000+p) a
+  random correlation R_p; the network matrix B has 11 blocks of 5 variables
+  (1 on the diagonal, 0.6 inside a block, 0 elsewhere); condition c mixes
+  Sigma_pc = (1 - w_c) R_p + w_c B with w_A = 0.5, w_B = 0.3 (weaker
+  within-network coupling in B).  X is N AR(1) series (phi = 0.7, as in
+  ``ar1``) mixed by chol(Sigma_pc), condition A drawn before B.  Stands in
+  for the anesthesia study (16 subjects, awake and deep, 55 regions in 11
+  networks of 5); the recordings are not available and their length is not
+  stated, T = 300 is assumed.
 """
 from __future__ import annotations
 
 import numpy as np
 
-SEEDS = {"small": 0, "ar1": 1, "planted": 2, "multi_base": 3000, "grad": 4}
+SEEDS = {"small": 0, "ar1": 1, "planted": 2, "multi_base": 3000, "grad": 4,
+         "paired_base": 5000}
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -94,6 +105,35 @@ def multi(D: int = 64, base_seed: int = 3000):
     return out
 
 
+def _ar1_mix(rng: np.random.Generator, S: np.ndarray, T: int, phi: float) -> np.ndarray:
+    N = S.shape[0]
+    L = np.linalg.cholesky(S)
+    e = np.empty((T, N))
+    e[0] = rng.standard_normal(N)
+    s = np.sqrt(1.0 - phi * phi)
+    xi = rng.standard_normal((T - 1, N))
+    for t in range(1, T):
+        e[t] = phi * e[t - 1] + s * xi[t - 1]
+    return np.ascontiguousarray(e @ L.T)
+
+
+def paired(P: int = 16, N: int = 55, T: int = 300, base_seed: int = 5000,
+           block: int = 5, w=(0.5, 0.3), phi: float = 0.7):
+    """2P datasets: subjects 0..P-1 in condition A, then the same subjects in
+    condition B (dataset p pairs with dataset P + p)."""
+    B = np.zeros((N, N))
+    for b0 in range(0, N, block):
+        B[b0:b0 + block, b0:b0 + block] = 0.6
+    np.fill_diagonal(B, 1.0)
+    A_sets, B_sets = [], []
+    for p in range(P):
+        rng = _rng(base_seed + p)
+        R = random_corr(rng, N)
+        A_sets.append(_ar1_mix(rng, (1 - w[0]) * R + w[0] * B, T, phi))
+        B_sets.append(_ar1_mix(rng, (1 - w[1]) * R + w[1] * B, T, phi))
+    return A_sets + B_sets
+
+
 # Named workloads: (X, orders).  Orders are inclusive ranges of subset sizes.
 def small():
     return plain(10, 500, SEEDS["small"]), list(range(3, 11))
@@ -114,3 +154,8 @@ def grad60():
 def multi64():
     Xs = multi(64, SEEDS["multi_base"])
     return Xs, [list(range(3, min(X.shape[1], 8) + 1)) for X in Xs]
+
+
+def paired55():
+    """16 subjects x 2 conditions, N = 55, orders 3..6 (exhaustive)."""
+    return paired(16, 55, 300, SEEDS["paired_base"]), [3, 4, 5, 6]
