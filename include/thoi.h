@@ -41,6 +41,7 @@ extern "C" {
 
 #define THOI_MAX_N 64      /* largest number of variables */
 #define THOI_MAX_TOP_M 1024 /* largest top-M list per order and side */
+#define THOI_MAX_GROUP 1024 /* largest number of datasets in a group objective */
 
 typedef struct thoi_ctx thoi_ctx;
 
@@ -71,6 +72,12 @@ typedef enum {
 typedef enum { THOI_DTYPE_F32 = 0, THOI_DTYPE_F64 = 1 } thoi_dtype;
 
 typedef enum { THOI_H = 0, THOI_TC = 1, THOI_DTC = 2, THOI_O = 3, THOI_S = 4 } thoi_measure;
+
+/* Group objectives over D datasets (see thoi_group_measures). */
+typedef enum {
+  THOI_GROUP_MEAN = 0,    /* mean of the measure over the datasets */
+  THOI_GROUP_COHEN_D = 1  /* paired Cohen's d between two conditions */
+} thoi_group_objective;
 
 typedef enum {
   THOI_SIGMA32_TENSORCORE = 0, /* split-BF16 tensor-core GEMM, FP32 accumulation */
@@ -323,6 +330,67 @@ thoi_status thoi_anneal(thoi_ctx* ctx, int32_t k_lo, int32_t k_hi, int32_t n_cha
                         double T0, double alpha, int32_t measure, int32_t maximize, uint64_t seed,
                         uint64_t* final_masks, double* final_values, uint64_t* best_masks,
                         double* best_values, thoi_stats* stats, void* stream);
+
+/* Group objective of one measure over D datasets, for every nplet (Results,
+ * "Leveraging Gaussian entropy estimators with batch processing": the nplet
+ * with the smallest average O across datasets; Methods, "fMRI analysis": the
+ * paired Cohen's d between two conditions).  With v_d the measure of the
+ * nplet in dataset d:
+ *   THOI_GROUP_MEAN    : g = (1/D) sum_d v_d
+ *   THOI_GROUP_COHEN_D : D = 2P, P >= 2; dataset i (condition A) is paired with
+ *                        dataset P + i (condition B); delta_i = v_i - v_{P+i};
+ *                        g = mean(delta) / sd(delta), sd with the P - 1
+ *                        denominator
+ * A nplet that is not positive definite in some dataset, or whose differences
+ * all coincide (sd = 0), has no value: NaN per nplet, and in the records it is
+ * left out and counted in n_not_pd.
+ *  ctxs    : D contexts (1 <= D <= THOI_MAX_GROUP, 4 <= D even for Cohen's d)
+ *            with the same N; a context may appear more than once.  Each
+ *            dataset is evaluated by its own path (precision, thresholds,
+ *            bias correction of its context); ctxs[0] holds the workspace
+ *            and gives top_m.
+ *  orders, id_begin, id_end : as in thoi_measures
+ *  measure : thoi_measure the objective is taken of
+ *  kind    : THOI_RED_NONE -- `out` is a device double[n], g of every nplet in
+ *            [id_begin, id_end) in id order (out_bytes >= 8 n);
+ *            THOI_RED_PER_ORDER -- `out` (host or device) receives the records
+ *            in thoi_measures' layout, thoi_records_bytes(n_orders, top_m)
+ *            bytes; every measure slot of a record carries g's minimum,
+ *            maximum, mean and their ids, count_neg_O counts g < 0, the top
+ *            lists rank g, and n_refactored sums the datasets' re-factors.
+ * Device memory: ctxs[0] keeps a D x P_g matrix of FP64 values (at most
+ * 16 GiB and a quarter of the free memory, P_g >= 65536), plus one FP64 basis
+ * piece of P_g nplets; orders larger than P_g run in pieces.  stats: nplets =
+ * evaluations (D per nplet), n_refactored summed over the datasets.
+ * Statuses as in thoi_measures (THOI_ERR_NOT_PD when some nplet failed in
+ * some dataset).  Synchronises `stream`. */
+thoi_status thoi_group_measures(thoi_ctx* const* ctxs, int32_t D, const int32_t* orders,
+                                int32_t n_orders, uint64_t id_begin, uint64_t id_end,
+                                int32_t measure, int32_t objective, int32_t kind, void* out,
+                                size_t out_bytes, thoi_stats* stats, void* stream);
+
+/* Greedy search on a group objective (Methods, "Heuristics": the searches
+ * take several datasets; Methods, "fMRI analysis": nplets that maximise or
+ * minimise the paired Cohen's d).  As thoi_greedy, with "best" the largest
+ * (maximize != 0) or smallest group objective g of `measure` over the D
+ * contexts (thoi_group_measures); every evaluation in FP64.  Nplets without a
+ * value are left out.  Same outputs and limits as thoi_greedy. */
+thoi_status thoi_group_greedy(thoi_ctx* const* ctxs, int32_t D, int32_t k0, int32_t k1,
+                              int32_t kappa, int32_t measure, int32_t objective,
+                              int32_t maximize, uint64_t* sets_out, double* values_out,
+                              thoi_stats* stats, void* stream);
+
+/* Simulated annealing on a group objective: thoi_anneal with the energy
+ * the group objective g (thoi_group_measures) of `measure` over the D
+ * contexts, each set evaluated in FP64 in every dataset; sets without a
+ * value are rejected.  Same draws, moves, outputs and limits as
+ * thoi_anneal. */
+thoi_status thoi_group_anneal(thoi_ctx* const* ctxs, int32_t D, int32_t k_lo, int32_t k_hi,
+                              int32_t n_chains, int32_t iters, double T0, double alpha,
+                              int32_t measure, int32_t objective, int32_t maximize,
+                              uint64_t seed, uint64_t* final_masks, double* final_values,
+                              uint64_t* best_masks, double* best_values, thoi_stats* stats,
+                              void* stream);
 
 /* Host-only sharding helpers (no device work, no CUDA calls).  Nplets are
  * independent (Methods, "Parallel and batched computation of HOI"), so one

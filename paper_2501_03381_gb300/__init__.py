@@ -30,6 +30,7 @@ THOI_F32_FIX64, THOI_F64 = 0, 1
 THOI_RED_NONE, THOI_RED_PER_ORDER = 0, 1
 THOI_DTYPE_F32, THOI_DTYPE_F64 = 0, 1
 THOI_SIGMA32_TENSORCORE, THOI_SIGMA32_FROM_F64 = 0, 1
+GROUP_OBJECTIVES = ("mean", "cohen_d")  # thoi_group_objective
 STATUS = {0: "THOI_OK", 1: "THOI_ERR_INVALID_ARG", 2: "THOI_ERR_NONFINITE_INPUT",
           3: "THOI_ERR_TOO_LARGE", 4: "THOI_ERR_NOT_PD", 5: "THOI_ERR_OOM", 6: "THOI_ERR_CUDA",
           7: "THOI_ERR_TIMEOUT", 8: "THOI_ERR_CANCELLED", 9: "THOI_ERR_WORKSPACE"}
@@ -114,6 +115,14 @@ def load(build_if_missing: bool = True):
             "thoi_anneal": (ctypes.c_int, [vp, i32, i32, i32, i32, ctypes.c_double,
                                            ctypes.c_double, i32, i32, u64, vp, vp, vp, vp,
                                            ctypes.POINTER(thoi_stats), vp]),
+            "thoi_group_measures": (ctypes.c_int, [vp, i32, vp, i32, u64, u64, i32, i32, i32,
+                                                   vp, ctypes.c_size_t,
+                                                   ctypes.POINTER(thoi_stats), vp]),
+            "thoi_group_greedy": (ctypes.c_int, [vp, i32, i32, i32, i32, i32, i32, i32, vp, vp,
+                                                 ctypes.POINTER(thoi_stats), vp]),
+            "thoi_group_anneal": (ctypes.c_int, [vp, i32, i32, i32, i32, i32, ctypes.c_double,
+                                                 ctypes.c_double, i32, i32, i32, u64, vp, vp,
+                                                 vp, vp, ctypes.POINTER(thoi_stats), vp]),
             "thoi_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -409,6 +418,78 @@ def thoi_anneal(h, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float, a
                               int(bool(maximize)), seed & ((1 << 64) - 1), _ptr(fm), _ptr(fv),
                               _ptr(bm), _ptr(bv), ctypes.byref(st), _stream_ptr(stream)),
            "thoi_anneal")
+    return fm, fv, bm, bv, st
+
+
+def _handles(handles):
+    hs = [getattr(h, "h", h) for h in handles]
+    return (ctypes.c_void_p * len(hs))(*hs), len(hs)
+
+
+def _objective(objective) -> int:
+    return objective if isinstance(objective, int) else GROUP_OBJECTIVES.index(objective)
+
+
+def thoi_group_measures(handles, orders, measure: str = "O", objective="mean",
+                        id_begin: int = 0, id_end: int | None = None, kind: int = 0, out=None,
+                        top_m: int = 256, stream=None):
+    """Group objective of one measure over the datasets of `handles` (raw
+    handles or Contexts, the same N).  kind 0: a float64 CUDA tensor with the
+    objective of every nplet in [id_begin, id_end); kind 1: per-order records
+    (records, top_hi, top_lo) with top_m = the first context's."""
+    import torch
+    arr, D = _handles(handles)
+    o = _orders_arr(orders)
+    N = thoi_n(arr[0])
+    end = thoi_count(N, o) if id_end is None else int(id_end)
+    st = thoi_stats()
+    if kind == THOI_RED_NONE:
+        if out is None:
+            out = torch.empty(max(end - id_begin, 0), dtype=torch.float64, device="cuda")
+        nbytes = out.numel() * out.element_size()
+    else:
+        if out is None:
+            out = np.zeros(thoi_records_bytes(len(o), top_m), dtype=np.uint8)
+        nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+    _check(load().thoi_group_measures(arr, D, _ptr(o), len(o), id_begin, end,
+                                      MEASURES.index(measure), _objective(objective), kind,
+                                      _ptr(out), nbytes, ctypes.byref(st), _stream_ptr(stream)),
+           "thoi_group_measures")
+    if kind == THOI_RED_NONE:
+        return out, st
+    return parse_records(out, len(o), top_m), st
+
+
+def thoi_group_greedy(handles, k0: int, k1: int, kappa: int, measure: str = "O",
+                      objective="mean", maximize: bool = True, stream=None):
+    """Greedy search on a group objective; outputs as thoi_greedy."""
+    arr, D = _handles(handles)
+    L = k1 - k0 + 1
+    masks = np.zeros((L, kappa), dtype=np.uint64)
+    values = np.zeros((L, kappa), dtype=np.float64)
+    st = thoi_stats()
+    _check(load().thoi_group_greedy(arr, D, k0, k1, kappa, MEASURES.index(measure),
+                                    _objective(objective), int(bool(maximize)), _ptr(masks),
+                                    _ptr(values), ctypes.byref(st), _stream_ptr(stream)),
+           "thoi_group_greedy")
+    return masks, values, st
+
+
+def thoi_group_anneal(handles, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float,
+                      alpha: float, measure: str = "O", objective="mean", maximize: bool = True,
+                      seed: int = 0, stream=None):
+    """Simulated annealing on a group objective; outputs as thoi_anneal."""
+    arr, D = _handles(handles)
+    fm = np.zeros(n_chains, dtype=np.uint64)
+    fv = np.zeros(n_chains, dtype=np.float64)
+    bm = np.zeros(n_chains, dtype=np.uint64)
+    bv = np.zeros(n_chains, dtype=np.float64)
+    st = thoi_stats()
+    _check(load().thoi_group_anneal(arr, D, k_lo, k_hi, n_chains, iters, T0, alpha,
+                                    MEASURES.index(measure), _objective(objective),
+                                    int(bool(maximize)), seed & ((1 << 64) - 1), _ptr(fm),
+                                    _ptr(fv), _ptr(bm), _ptr(bv), ctypes.byref(st),
+                                    _stream_ptr(stream)), "thoi_group_anneal")
     return fm, fv, bm, bv, st
 
 

@@ -18,7 +18,13 @@
 // exp(dE / Temp) (the paper prints exp(-dE / Temp), which is at least 1 for
 // dE <= 0; the sign is read as the usual Metropolis rule).  Energy = the
 // measure (maximise) or its negative (minimise); sets that are not positive
-// definite are rejected.
+// definite are rejected.  Over D > 1 datasets the value is a group objective
+// (Methods, "Heuristics": the searches take several datasets): the mean of
+// the measure, or the paired Cohen's d (datasets i and P + i paired; mean
+// and spread of the differences in two passes).  A group chain is one warp:
+// every lane runs the same schedule and draws, and the lanes share the
+// datasets of each evaluation (warp sums are butterflies, so every lane holds
+// the same bits and the warp never diverges on an acceptance).
 #include <math.h>
 
 #include "internal.cuh"
@@ -98,27 +104,18 @@ __device__ double sa_measure(unsigned long long mask, const double* sR, int ldr,
   return pick5(v, measure);
 }
 
-__global__ void __launch_bounds__(SA_NT) k_anneal(const double* __restrict__ R64,
-                                                  const double* __restrict__ ls, int N, int klo,
-                                                  int khi, const Combine* __restrict__ cmb_tab,
-                                                  int n_chains, int iters, double T0, double alpha,
-                                                  int measure, int maximize, unsigned long long seed,
-                                                  unsigned long long* __restrict__ final_mask,
-                                                  double* __restrict__ final_val,
-                                                  unsigned long long* __restrict__ best_mask,
-                                                  double* __restrict__ best_val,
-                                                  unsigned long long* __restrict__ accepted) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int ldr = row_stride(N);
-  double* sR = reinterpret_cast<double*>(smem);
-  double* sls = sR + (size_t)N * ldr;
-  Combine* scmb = reinterpret_cast<Combine*>(sls + N);
-  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sR[(q / N) * ldr + (q % N)] = R64[q];
-  for (int q = threadIdx.x; q < N; q += blockDim.x) sls[q] = ls[q];
-  for (int q = threadIdx.x; q <= khi; q += blockDim.x) scmb[q] = cmb_tab[q];
-  __syncthreads();
-  const int chain = blockIdx.x * blockDim.x + threadIdx.x;
-  if (chain >= n_chains) return;
+// The whole schedule of one chain (start, moves, Metropolis acceptance,
+// cooling); value(mask) is the measure or group objective of a set.  Every
+// caller thread of a chain runs it identically; `write` selects the one that
+// stores the results.
+template <typename F>
+__device__ __forceinline__ void sa_chain(const int chain, const int N, const int klo,
+                                         const int khi, const int iters, const double T0,
+                                         const double alpha, const int maximize,
+                                         const unsigned long long seed, F&& value,
+                                         const bool write, unsigned long long* final_mask,
+                                         double* final_val, unsigned long long* best_mask,
+                                         double* best_val, unsigned long long* accepted) {
   const unsigned long long base = (unsigned long long)chain * (unsigned long long)(iters + 1);
   auto draw = [&](int it, int slot) { return sm64(seed, (base + it) * 64ull + slot); };
   const double sgn = maximize ? 1.0 : -1.0;
@@ -136,7 +133,7 @@ __global__ void __launch_bounds__(SA_NT) k_anneal(const double* __restrict__ R64
       mask |= 1ull << perm[j];
     }
   }
-  double E = sgn * sa_measure(mask, sR, ldr, sls, scmb, measure);
+  double E = sgn * value(mask);
   double bestE = E;
   unsigned long long bmask = mask;
   double T = T0;
@@ -158,7 +155,7 @@ __global__ void __launch_bounds__(SA_NT) k_anneal(const double* __restrict__ R64
       const int w = nth_member(~mask & full, draw_int(draw(it, 2), N - size));
       prop = (mask & ~(1ull << v)) | (1ull << w);
     }
-    const double En = sgn * sa_measure(prop, sR, ldr, sls, scmb, measure);
+    const double En = sgn * value(prop);
     if (En == En) {
       const double dE = En - E;
       bool ok = dE > 0.0;
@@ -178,26 +175,126 @@ __global__ void __launch_bounds__(SA_NT) k_anneal(const double* __restrict__ R64
     }
     T *= alpha;
   }
-  final_mask[chain] = mask;
-  final_val[chain] = sgn * E;
-  best_mask[chain] = bmask;
-  best_val[chain] = sgn * bestE;
-  accepted[chain] = acc;
+  if (write) {
+    final_mask[chain] = mask;
+    final_val[chain] = sgn * E;
+    best_mask[chain] = bmask;
+    best_val[chain] = sgn * bestE;
+    accepted[chain] = acc;
+  }
 }
 
-cudaError_t launch_anneal(const double* R64, const double* ls, int N, int klo, int khi,
-                          const Combine* cmb_tab, int n_chains, int iters, double T0, double alpha,
-                          int measure, int maximize, unsigned long long seed,
+// One dataset: a thread per chain, the tables in shared memory.
+__global__ void __launch_bounds__(SA_NT) k_anneal(const double* __restrict__ R64,
+                                                  const double* __restrict__ ls, int N, int klo,
+                                                  int khi, const Combine* __restrict__ cmb_tab,
+                                                  int n_chains, int iters, double T0, double alpha,
+                                                  int measure, int maximize, unsigned long long seed,
+                                                  unsigned long long* __restrict__ final_mask,
+                                                  double* __restrict__ final_val,
+                                                  unsigned long long* __restrict__ best_mask,
+                                                  double* __restrict__ best_val,
+                                                  unsigned long long* __restrict__ accepted) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ldr = row_stride(N);
+  double* sR = reinterpret_cast<double*>(smem);
+  double* sls = sR + (size_t)N * ldr;
+  Combine* scmb = reinterpret_cast<Combine*>(sls + N);
+  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sR[(q / N) * ldr + (q % N)] = R64[q];
+  for (int q = threadIdx.x; q < N; q += blockDim.x) sls[q] = ls[q];
+  for (int q = threadIdx.x; q <= khi; q += blockDim.x) scmb[q] = cmb_tab[q];
+  __syncthreads();
+  const int chain = blockIdx.x * blockDim.x + threadIdx.x;
+  if (chain >= n_chains) return;
+  sa_chain(chain, N, klo, khi, iters, T0, alpha, maximize, seed,
+           [&](unsigned long long m) { return sa_measure(m, sR, ldr, sls, scmb, measure); }, true,
+           final_mask, final_val, best_mask, best_val, accepted);
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+constexpr int SA_GNT = 128;  // group kernel: four chains (warps) per block
+
+// D > 1 datasets: a warp per chain.  Lane L evaluates datasets L, L + 32, ...
+// For Cohen's d the datasets are taken in pair order h = 2j + side (side 0:
+// dataset j, condition A; side 1: dataset P + j), so the two sides of a pair
+// sit on neighbouring lanes and one shuffle forms the difference.
+__global__ void __launch_bounds__(SA_GNT)
+    k_anneal_group(const double* const* __restrict__ Rs, const double* const* __restrict__ lss,
+                   int D, int objective, int N, int klo, int khi,
+                   const Combine* __restrict__ cmb_tab, int n_chains, int iters, double T0,
+                   double alpha, int measure, int maximize, unsigned long long seed,
+                   unsigned long long* __restrict__ final_mask, double* __restrict__ final_val,
+                   unsigned long long* __restrict__ best_mask, double* __restrict__ best_val,
+                   unsigned long long* __restrict__ accepted) {
+  const int lane = threadIdx.x & 31;
+  const int chain = (int)(((unsigned)blockIdx.x * SA_GNT + threadIdx.x) >> 5);
+  if (chain >= n_chains) return;  // whole warps leave together
+  const int ncmb = khi + 1, rounds = (D + 31) / 32, P = D / 2;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  auto one = [&](unsigned long long m, int d) {
+    return sa_measure(m, Rs[d], N, lss[d], cmb_tab + (size_t)d * ncmb, measure);
+  };
+  auto value = [&](unsigned long long m) -> double {
+    if (objective == THOI_GROUP_MEAN) {
+      double s = 0.0;
+      for (int q = 0; q < rounds; q++) {
+        const int d = lane + 32 * q;
+        s += d < D ? one(m, d) : 0.0;
+      }
+      return warp_sum(s) / (double)D;
+    }
+    double dl[THOI_MAX_GROUP / 32];  // this lane's differences (even lanes)
+    double s = 0.0;
+    for (int q = 0; q < rounds; q++) {
+      const int h = lane + 32 * q;
+      const double v = h < D ? one(m, (h & 1) ? P + (h >> 1) : (h >> 1)) : 0.0;
+      const double w = __shfl_xor_sync(0xffffffffu, v, 1);
+      dl[q] = (h < D && !(h & 1)) ? v - w : 0.0;
+      s += dl[q];
+    }
+    const double mean = warp_sum(s) / (double)P;
+    double ss = 0.0;
+    for (int q = 0; q < rounds; q++) {
+      const int h = lane + 32 * q;
+      const double e = (h < D && !(h & 1)) ? dl[q] - mean : 0.0;
+      ss = fma(e, e, ss);
+    }
+    const double sd = sqrt(warp_sum(ss) / (double)(P - 1));
+    return sd > 0.0 ? mean / sd : nan;
+  };
+  sa_chain(chain, N, klo, khi, iters, T0, alpha, maximize, seed, value, lane == 0, final_mask,
+           final_val, best_mask, best_val, accepted);
+}
+
+cudaError_t launch_anneal(const double* const* Rs, const double* const* lss, int D,
+                          int objective, int N, int klo, int khi, const Combine* cmb_tab,
+                          const double* R0, const double* ls0, int n_chains, int iters, double T0,
+                          double alpha, int measure, int maximize, unsigned long long seed,
                           unsigned long long* final_mask, double* final_val,
                           unsigned long long* best_mask, double* best_val,
                           unsigned long long* accepted, cudaStream_t s) {
-  if (khi > SA_KMAX || klo < 1 || khi < klo || khi > N || n_chains < 1 || iters < 0)
+  if (khi > SA_KMAX || klo < 1 || khi < klo || khi > N || n_chains < 1 || iters < 0 || D < 1 ||
+      D > THOI_MAX_GROUP)
     return cudaErrorInvalidValue;
-  const size_t sm = ((size_t)N * row_stride(N) + N) * sizeof(double) + (size_t)(khi + 1) * sizeof(Combine);
-  const int grid = (n_chains + SA_NT - 1) / SA_NT;
-  k_anneal<<<grid, SA_NT, sm, s>>>(R64, ls, N, klo, khi, cmb_tab, n_chains, iters, T0, alpha,
-                                   measure, maximize, seed, final_mask, final_val, best_mask,
-                                   best_val, accepted);
+  if (D == 1) {
+    const size_t sm = ((size_t)N * row_stride(N) + N) * sizeof(double) +
+                      (size_t)(khi + 1) * sizeof(Combine);
+    const int grid = (n_chains + SA_NT - 1) / SA_NT;
+    k_anneal<<<grid, SA_NT, sm, s>>>(R0, ls0, N, klo, khi, cmb_tab, n_chains, iters, T0, alpha,
+                                     measure, maximize, seed, final_mask, final_val, best_mask,
+                                     best_val, accepted);
+    return cudaGetLastError();
+  }
+  const long long threads = (long long)n_chains * 32;
+  const int grid = (int)((threads + SA_GNT - 1) / SA_GNT);
+  k_anneal_group<<<grid, SA_GNT, 0, s>>>(Rs, lss, D, objective, N, klo, khi, cmb_tab, n_chains,
+                                         iters, T0, alpha, measure, maximize, seed, final_mask,
+                                         final_val, best_mask, best_val, accepted);
   return cudaGetLastError();
 }
 

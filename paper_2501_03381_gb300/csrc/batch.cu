@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(NT) k_refactor_batch(
   a.mode = 2;
   a.out = nullptr;
   a.out_f64 = 1;
+  a.out_sel = 0;
   a.out_n = 0;
   a.out_first = 0;
   a.part = nullptr;

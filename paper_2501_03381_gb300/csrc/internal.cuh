@@ -70,6 +70,7 @@ struct NpletArgs {
   int mode;             // 0: per-nplet SoA, 1: reduction partials
   void* out;            // mode 0: SoA base
   int out_f64;
+  int out_sel;          // mode 0: 0 = the five measures (SoA); m + 1 = measure m alone (one row)
   unsigned long long out_n;      // stride between measures in `out`
   unsigned long long out_first;  // global id stored at out index 0
   PartRec* part;        // mode 1: [gridDim.x]
@@ -192,14 +193,32 @@ cudaError_t launch_grad_pass(const NpletArgs& a, double* Gpart, int grid, int me
 cudaError_t launch_grad_finish(const double* Gpart, int nblk, const double* sig64, int N, float* out,
                                cudaStream_t s);
 
-// Simulated annealing: n_chains independent chains, one thread each (see
-// anneal.cu); cmb_tab[k] = combine constants of order k (k <= k_hi <= 32).
-cudaError_t launch_anneal(const double* R64, const double* ls, int N, int klo, int khi,
-                          const Combine* cmb_tab, int n_chains, int iters, double T0, double alpha,
-                          int measure, int maximize, unsigned long long seed,
+// Simulated annealing: n_chains independent chains (see anneal.cu).  D = 1
+// evaluates the measure of one dataset (R0, ls0; a thread per chain, tables
+// in shared memory); D > 1 a group objective (a warp per chain; Rs, lss:
+// device arrays of D device pointers).  cmb_tab: D x (khi + 1) combine
+// constants (row d, order k).
+cudaError_t launch_anneal(const double* const* Rs, const double* const* lss, int D,
+                          int objective, int N, int klo, int khi, const Combine* cmb_tab,
+                          const double* R0, const double* ls0, int n_chains, int iters, double T0,
+                          double alpha, int measure, int maximize, unsigned long long seed,
                           unsigned long long* final_mask, double* final_val,
                           unsigned long long* best_mask, double* best_val,
                           unsigned long long* accepted, cudaStream_t s);
+// Group objectives: fold one dataset's status and re-factor count; combine the
+// D x ld value matrix into the objective (per-nplet `out` and/or an FP64
+// basis with stride bstride); one measure of listed nplets from their basis;
+// copy the objective's statistics into every measure slot of the records.
+cudaError_t launch_group_fold(const int* status, const unsigned long long* flag_count,
+                              unsigned long long flag_cap, int* gstatus, unsigned long long* gnref,
+                              cudaStream_t s);
+cudaError_t launch_group_combine(const double* V, unsigned long long ld, unsigned long long n,
+                                 int D, int objective, double* out, double* basis,
+                                 unsigned long long bstride, int num_sms, cudaStream_t s);
+cudaError_t launch_group_pick(const double* b64, unsigned long long lstride,
+                              const unsigned long long* count, unsigned long long cap,
+                              Combine cmb, int measure, double* row, cudaStream_t s);
+cudaError_t launch_group_fix(thoi_order_record* recs, int n, cudaStream_t s);
 
 // ------------------------------------------------------------------ multi-dataset batch
 // Many datasets of uneven (N, T) in one graph: per order k one persistent

@@ -505,10 +505,16 @@ __device__ __forceinline__ void store_basis(const NpletArgs& a, unsigned long lo
   O[2 * a.out_n + o] = lsum;
 }
 
-// Per-nplet SoA store.
+// Per-nplet SoA store (the five measures, or one of them when out_sel > 0).
 template <typename V>
 __device__ __forceinline__ void store5(const NpletArgs& a, unsigned long long gid, const V (&v)[5]) {
   const unsigned long long o = gid - a.out_first;
+  if (a.out_sel > 0) {
+    const V x = pick5(v, a.out_sel - 1);
+    if (a.out_f64) reinterpret_cast<double*>(a.out)[o] = (double)x;
+    else reinterpret_cast<float*>(a.out)[o] = (float)x;
+    return;
+  }
   if (a.out_f64) {
     double* O = reinterpret_cast<double*>(a.out);
 #pragma unroll

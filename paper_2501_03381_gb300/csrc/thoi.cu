@@ -85,6 +85,12 @@ struct thoi_ctx {
   Shape force_shape;
   unsigned long long serial = 0;  // unique per context (keys the batch graph cache)
   int top_meas = THOI_O;          // measure ranked by the top-M lists
+  int out_sel = 0;                // per-nplet output: 0 = five measures, m + 1 = measure m alone
+  // group objectives (held by the first context of a group)
+  double* grp = nullptr;          // per-dataset values of one piece, then the basis of the objective
+  size_t grp_cap = 0;             // doubles
+  unsigned char* grp_meta = nullptr;  // dataset descriptors, status word, re-factor counters
+  size_t grp_meta_cap = 0;
 };
 
 // ------------------------------------------------------------------ occupancy cache
@@ -386,6 +392,8 @@ extern "C" void thoi_destroy(thoi_ctx* c) {
   free_ptr(c->basis);
   free_ptr(c->b64);
   free_ptr(c->seed_thr);
+  free_ptr(c->grp);
+  free_ptr(c->grp_meta);
   delete c;
 }
 
@@ -621,6 +629,7 @@ static NpletArgs base_args(thoi_ctx* c, const SlotRange& r) {
   a.rank_end = r.r1;
   a.id_base = r.off;
   a.cmb = combine_for(c, r.k);
+  a.out_sel = c->out_sel;
   a.tau_piv = c->opt.pivot_tau;
   a.tau_tr = c->opt.trace_tau;
   a.status = c->status;
@@ -661,6 +670,34 @@ static thoi_status finish_status(thoi_ctx* c, cudaStream_t s, int n_slots, thoi_
   if (hs & ST_FLAG_OVERFLOW) return THOI_ERR_WORKSPACE;
   if (hs & ST_CANCELLED) return THOI_ERR_CANCELLED;
   if (hs & ST_NOT_PD) return THOI_ERR_NOT_PD;
+  return THOI_OK;
+}
+
+// Reduction partials of n32 blocks (FP32 or FP64 path) and n64 blocks (FP64
+// re-factor), each with two top lists of top_m entries.
+static thoi_status ensure_parts(thoi_ctx* c, size_t n32, size_t n64, int top_m) {
+  if (c->part_top_m != top_m) {
+    free_ptr(c->top32); c->top32 = nullptr;
+    free_ptr(c->top64); c->top64 = nullptr;
+    free_ptr(c->part32); c->part32 = nullptr; c->part32_cap = 0;
+    free_ptr(c->part64); c->part64 = nullptr; c->part64_cap = 0;
+    c->part_top_m = top_m;
+  }
+  size_t cap32 = c->part32_cap, cap64 = c->part64_cap;
+  thoi_status st = grow(&c->part32, &c->part32_cap, n32 > 0 ? n32 : 1);
+  if (st != THOI_OK) return st;
+  if (c->part32_cap != cap32 || !c->top32) {
+    free_ptr(c->top32);
+    c->top32 = nullptr;
+    if (top_m > 0) CK(cudaMalloc(&c->top32, c->part32_cap * 2 * top_m * sizeof(TopEnt)));
+  }
+  st = grow(&c->part64, &c->part64_cap, n64 > 0 ? n64 : 1);
+  if (st != THOI_OK) return st;
+  if (c->part64_cap != cap64 || !c->top64) {
+    free_ptr(c->top64);
+    c->top64 = nullptr;
+    if (top_m > 0) CK(cudaMalloc(&c->top64, c->part64_cap * 2 * top_m * sizeof(TopEnt)));
+  }
   return THOI_OK;
 }
 
@@ -707,28 +744,8 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       if (st != THOI_OK) return st;
     }
     const size_t n64 = f64 ? 0 : slots.size() * (size_t)ref_cap;
-    if (c->part_top_m != top_m) {
-      free_ptr(c->top32); c->top32 = nullptr;
-      free_ptr(c->top64); c->top64 = nullptr;
-      free_ptr(c->part32); c->part32 = nullptr; c->part32_cap = 0;
-      free_ptr(c->part64); c->part64 = nullptr; c->part64_cap = 0;
-      c->part_top_m = top_m;
-    }
-    size_t cap32 = c->part32_cap, cap64 = c->part64_cap;
-    st = grow(&c->part32, &c->part32_cap, n32 > 0 ? n32 : 1);
+    st = ensure_parts(c, n32, n64, top_m);
     if (st != THOI_OK) return st;
-    if (c->part32_cap != cap32 || !c->top32) {
-      free_ptr(c->top32);
-      c->top32 = nullptr;
-      if (top_m > 0) CK(cudaMalloc(&c->top32, c->part32_cap * 2 * top_m * sizeof(TopEnt)));
-    }
-    st = grow(&c->part64, &c->part64_cap, n64 > 0 ? n64 : 1);
-    if (st != THOI_OK) return st;
-    if (c->part64_cap != cap64 || !c->top64) {
-      free_ptr(c->top64);
-      c->top64 = nullptr;
-      if (top_m > 0) CK(cudaMalloc(&c->top64, c->part64_cap * 2 * top_m * sizeof(TopEnt)));
-    }
   }
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(c->flag_counts, 0, MAX_SLOTS * sizeof(unsigned long long), s));
@@ -983,6 +1000,238 @@ extern "C" thoi_status thoi_measures_grad(thoi_ctx* c, const int32_t* orders, in
   CK(launch_grad_finish(c->gpart, grid, c->sig64, c->N, dL_dSigma, s));
   launches++;
   return finish_status(c, s, (int)slots.size(), stats, thoi_count(c->N, orders, n_orders), launches);
+}
+
+// ------------------------------------------------------------------ API: group objectives
+// Per order and piece of P_g ranks: every dataset's own path writes one
+// measure per nplet (FP64) into row d of a D x P_g matrix (its FP64
+// re-factor patching the row in place), a fold kernel keeps its status and
+// re-factor count, then one kernel combines the D rows into the objective:
+// the per-nplet output, or an FP64 basis piece fed to the FP64 streaming
+// reduction; one merge at the end.
+namespace {
+// The D x P_g value matrix takes at most 16 GiB and a quarter of the free
+// device memory: whole orders fit in one piece for the usual group sizes, so
+// each dataset's pass can use the prefix-shared kernels.
+constexpr unsigned long long GROUP_VALUE_BYTES = 1ull << 34;
+constexpr unsigned long long GROUP_PIECE_MIN = 1ull << 16;
+
+// Options of the group's contexts, restored on every exit (a context may
+// appear more than once: restored in reverse order).
+struct GroupSaved {
+  std::vector<std::pair<thoi_ctx*, thoi_options>> opt;
+  std::vector<int> out_sel, top_meas;
+  GroupSaved(thoi_ctx* const* ctxs, int D) {
+    for (int d = 0; d < D; d++) {
+      opt.push_back({ctxs[d], ctxs[d]->opt});
+      out_sel.push_back(ctxs[d]->out_sel);
+      top_meas.push_back(ctxs[d]->top_meas);
+    }
+  }
+  ~GroupSaved() {
+    for (int d = (int)opt.size() - 1; d >= 0; d--) {
+      opt[d].first->opt = opt[d].second;
+      opt[d].first->out_sel = out_sel[d];
+      opt[d].first->top_meas = top_meas[d];
+    }
+  }
+};
+
+Combine group_combine() {
+  Combine g;
+  g.h_c = 0.0;
+  g.tc_c = 0.0;
+  g.dtc_c = 0.0;
+  g.top = THOI_O;
+  g.pad = 0;
+  return g;
+}
+}  // namespace
+
+static thoi_status group_args_ok(thoi_ctx* const* ctxs, int32_t D, int32_t measure,
+                                 int32_t objective) {
+  if (!ctxs || D < 1 || D > THOI_MAX_GROUP) return THOI_ERR_INVALID_ARG;
+  for (int d = 0; d < D; d++)
+    if (!ctxs[d] || ctxs[d]->N != ctxs[0]->N) return THOI_ERR_INVALID_ARG;
+  if (measure < THOI_H || measure > THOI_S) return THOI_ERR_INVALID_ARG;
+  if (objective == THOI_GROUP_MEAN) return THOI_OK;
+  if (objective == THOI_GROUP_COHEN_D && D % 2 == 0 && D >= 4) return THOI_OK;
+  return THOI_ERR_INVALID_ARG;
+}
+
+// Group status word and per-slot re-factor counters in ctxs[0]'s workspace.
+static thoi_status group_meta(thoi_ctx* c0, cudaStream_t s, int** gstatus,
+                              unsigned long long** gnref) {
+  thoi_status st = grow(&c0->grp_meta, &c0->grp_meta_cap, (size_t)(1 + MAX_SLOTS) * 8);
+  if (st != THOI_OK) return st;
+  CK(cudaMemsetAsync(c0->grp_meta, 0, (size_t)(1 + MAX_SLOTS) * 8, s));
+  *gstatus = (int*)c0->grp_meta;
+  *gnref = (unsigned long long*)(c0->grp_meta + 8);
+  return THOI_OK;
+}
+
+// Queue the group pass (no synchronisation); the caller has set the
+// contexts' options (GroupSaved) and the group meta words.
+static thoi_status enqueue_group(thoi_ctx* const* ctxs, int D, const int32_t* orders,
+                                 int32_t n_orders, uint64_t id_begin, uint64_t id_end,
+                                 int measure, int objective, int32_t kind, double* out_dev,
+                                 thoi_order_record* recs_dev, TopEnt* tops_dev, int* gstatus,
+                                 unsigned long long* gnref, cudaStream_t s, int* launches_out,
+                                 uint64_t* evaluated) {
+  thoi_ctx* c0 = ctxs[0];
+  std::vector<SlotRange> slots;
+  thoi_status st = plan_slots(c0, orders, n_orders, id_begin, &id_end, &slots);
+  if (st != THOI_OK) return st;
+  const bool red = kind == THOI_RED_PER_ORDER;
+  const int top_m = red ? c0->opt.top_m : 0;
+  unsigned long long maxn = 0;
+  for (auto& r : slots) maxn = (r.r1 - r.r0) > maxn ? (r.r1 - r.r0) : maxn;
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  unsigned long long budget = GROUP_VALUE_BYTES;
+  if ((unsigned long long)free_b / 4 < budget) budget = (unsigned long long)free_b / 4;
+  unsigned long long piece = budget / (8ull * (unsigned long long)D);
+  if (piece < GROUP_PIECE_MIN) piece = GROUP_PIECE_MIN;
+  if (piece > maxn) piece = maxn > 0 ? maxn : 1;
+  const unsigned long long ld = (piece + 63) / 64 * 64;
+  st = grow(&c0->grp, &c0->grp_cap, (size_t)ld * (D + (red ? 3 : 0)));
+  if (st != THOI_OK) return st;
+  double* V = c0->grp;
+  double* gb = c0->grp + (size_t)ld * D;
+  const int blk_cap = c0->num_sms * MAX_BLOCKS_PER_SM_RED;
+  if (red) {
+    size_t n32 = 0;
+    for (auto& r : slots) n32 += (size_t)((r.r1 - r.r0 + piece - 1) / piece) * blk_cap;
+    st = ensure_parts(c0, n32, 1, top_m);
+    if (st != THOI_OK) return st;
+  }
+  for (int d = 0; d < D; d++) {
+    ctxs[d]->out_sel = measure + 1;
+    ctxs[d]->opt.out_f64 = 1;
+    ctxs[d]->opt.profile = 0;
+  }
+  const Combine cg = group_combine();
+  MergeDescs MD;
+  memset(&MD, 0, sizeof MD);
+  int p32_off = 0, launches = 0;
+  uint64_t ev = 0;
+  for (size_t si = 0; si < slots.size(); si++) {
+    const SlotRange& r = slots[si];
+    MergeDesc& md = MD.d[si];
+    md.k = r.k;
+    md.cmb = cg;
+    md.p32_off = p32_off;
+    md.refactored = gnref + si;
+    const int32_t k = r.k;
+    for (unsigned long long a0 = r.r0; a0 < r.r1; a0 += piece) {
+      const unsigned long long a1 = r.r1 - a0 > piece ? a0 + piece : r.r1;
+      const unsigned long long n = a1 - a0;
+      for (int d = 0; d < D; d++) {
+        thoi_ctx* cd = ctxs[d];
+        int nl = 0;
+        st = enqueue_measures(cd, &k, 1, a0, a1, THOI_RED_NONE, V + (size_t)d * ld, nullptr,
+                              nullptr, s, &nl);
+        if (st != THOI_OK) return st;
+        CK(launch_group_fold(cd->status, cd->flag_counts, cd->flag_cap, gstatus, gnref + si, s));
+        launches += nl + 1;
+      }
+      ev += n * (uint64_t)D;
+      CK(launch_group_combine(V, ld, n, D, objective,
+                              red ? nullptr : out_dev + (r.off + a0 - id_begin),
+                              red ? gb : nullptr, ld, c0->num_sms, s));
+      launches++;
+      if (red) {
+        int grid = 0;
+        CK(launch_reduce_basis64(gb, ld, n, r.off + a0, cg, top_m, c0->part32 + p32_off,
+                                 top_m > 0 ? c0->top32 + (size_t)p32_off * 2 * top_m : nullptr,
+                                 c0->num_sms, blk_cap, s, &grid));
+        launches++;
+        p32_off += grid;
+        md.g32 += grid;
+      }
+    }
+  }
+  if (red) {
+    CK(launch_merge(MD, (int)slots.size(), c0->part32, c0->top32, c0->part64, c0->top64, top_m,
+                    recs_dev, tops_dev, s));
+    CK(launch_group_fix(recs_dev, (int)slots.size(), s));
+    launches += 2;
+  }
+  if (launches_out) *launches_out = launches;
+  if (evaluated) *evaluated = ev;
+  return THOI_OK;
+}
+
+static thoi_status group_finish(thoi_ctx* c0, cudaStream_t s, const int* gstatus,
+                                const unsigned long long* gnref, int n_slots, thoi_stats* stats,
+                                uint64_t evaluated, int launches) {
+  int hs = 0;
+  unsigned long long nr[MAX_SLOTS];
+  CK(cudaMemcpyAsync(&hs, gstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (n_slots > 0)
+    CK(cudaMemcpyAsync(nr, gnref, (size_t)n_slots * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->nplets = evaluated;
+    for (int i = 0; i < n_slots; i++) stats->n_refactored += nr[i];
+    stats->launches = launches;
+  }
+  (void)c0;
+  if (hs & ST_FLAG_OVERFLOW) return THOI_ERR_WORKSPACE;
+  if (hs & ST_CANCELLED) return THOI_ERR_CANCELLED;
+  if (hs & ST_NOT_PD) return THOI_ERR_NOT_PD;
+  return THOI_OK;
+}
+
+extern "C" thoi_status thoi_group_measures(thoi_ctx* const* ctxs, int32_t D, const int32_t* orders,
+                                           int32_t n_orders, uint64_t id_begin, uint64_t id_end,
+                                           int32_t measure, int32_t objective, int32_t kind,
+                                           void* out, size_t out_bytes, thoi_stats* stats,
+                                           void* stream) {
+  thoi_status st = group_args_ok(ctxs, D, measure, objective);
+  if (st != THOI_OK) return st;
+  thoi_ctx* c0 = ctxs[0];
+  if (!orders_ok(c0->N, orders, n_orders)) return THOI_ERR_INVALID_ARG;
+  if (kind != THOI_RED_NONE && kind != THOI_RED_PER_ORDER) return THOI_ERR_INVALID_ARG;
+  if (!out && !(kind == THOI_RED_NONE && id_begin == id_end)) return THOI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<SlotRange> slots;
+  uint64_t end = id_end;
+  st = plan_slots(c0, orders, n_orders, id_begin, &end, &slots);
+  if (st != THOI_OK) return st;
+  const uint64_t n = end - id_begin;
+  int* gstatus = nullptr;
+  unsigned long long* gnref = nullptr;
+  st = group_meta(c0, s, &gstatus, &gnref);
+  if (st != THOI_OK) return st;
+  GroupSaved saved(ctxs, D);
+  int launches = 0;
+  uint64_t ev = 0;
+  if (kind == THOI_RED_NONE) {
+    if (out_bytes < (size_t)n * 8) return THOI_ERR_INVALID_ARG;
+    if (n > 0 && !is_device_ptr(out)) return THOI_ERR_INVALID_ARG;
+    st = enqueue_group(ctxs, D, orders, n_orders, id_begin, end, measure, objective, kind,
+                       (double*)out, nullptr, nullptr, gstatus, gnref, s, &launches, &ev);
+    if (st != THOI_OK) return st;
+  } else {
+    const size_t need = thoi_records_bytes(n_orders, c0->opt.top_m);
+    if (out_bytes < need) return THOI_ERR_INVALID_ARG;
+    const bool dev = is_device_ptr(out);
+    unsigned char* dst = (unsigned char*)out;
+    if (!dev) {
+      st = grow(&c0->rec_buf, &c0->rec_cap, need);
+      if (st != THOI_OK) return st;
+      dst = c0->rec_buf;
+    }
+    thoi_order_record* recs = (thoi_order_record*)dst;
+    TopEnt* tops = (TopEnt*)(dst + (size_t)n_orders * sizeof(thoi_order_record));
+    st = enqueue_group(ctxs, D, orders, n_orders, id_begin, end, measure, objective, kind,
+                       nullptr, recs, tops, gstatus, gnref, s, &launches, &ev);
+    if (st != THOI_OK) return st;
+    if (!dev) CK(cudaMemcpyAsync(out, dst, need, cudaMemcpyDeviceToHost, s));
+  }
+  return group_finish(c0, s, gstatus, gnref, (int)slots.size(), stats, ev, launches);
 }
 
 // ------------------------------------------------------------------ API: batch
@@ -1530,33 +1779,29 @@ static uint64_t rank_to_mask(int N, int k, uint64_t rank) {
   return m;
 }
 
-extern "C" thoi_status thoi_greedy(thoi_ctx* c, int32_t k0, int32_t k1, int32_t kappa,
-                                   int32_t measure, int32_t maximize, uint64_t* sets_out,
-                                   double* values_out, thoi_stats* stats, void* stream) {
-  if (!c || !sets_out || !values_out || k0 < 1 || k1 < k0 || k1 > c->N || kappa < 1 ||
-      kappa > THOI_MAX_TOP_M || measure < THOI_H || measure > THOI_S)
-    return THOI_ERR_INVALID_ARG;
+// Greedy search on one context's measure (objective < 0) or on a group
+// objective over D contexts.
+static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int32_t k0,
+                               int32_t k1, int32_t kappa, int32_t measure, int32_t maximize,
+                               uint64_t* sets_out, double* values_out, thoi_stats* stats,
+                               cudaStream_t s) {
+  thoi_ctx* c = ctxs[0];
+  const bool group = objective >= 0;
   const int N = c->N;
-  cudaStream_t s = (cudaStream_t)stream;
   const int side = maximize ? 0 : 1;
   const int levels = k1 - k0 + 1;
   for (size_t q = 0; q < (size_t)levels * kappa; q++) {
     sets_out[q] = 0;
     values_out[q] = NAN;
   }
-  // run the FP64 path with the requested top lists; restored on every exit
-  struct Saved {
-    thoi_ctx* c;
-    thoi_options opt;
-    int top_meas;
-    ~Saved() {
-      c->opt = opt;
-      c->top_meas = top_meas;
-    }
-  } saved{c, c->opt, c->top_meas};
-  c->opt.precision = THOI_F64;
+  // every context runs the FP64 path; the first ranks its top lists (kappa
+  // entries) by the measure, or holds the group's; restored on every exit
+  GroupSaved saved(ctxs, D);
+  for (int d = 0; d < D; d++) {
+    ctxs[d]->opt.precision = THOI_F64;
+    ctxs[d]->opt.profile = 0;
+  }
   c->opt.top_m = kappa;
-  c->opt.profile = 0;
   c->top_meas = measure;
   const size_t rec_bytes = thoi_records_bytes(1, kappa);
   std::vector<unsigned char> host(rec_bytes);
@@ -1564,6 +1809,12 @@ extern "C" thoi_status thoi_greedy(thoi_ctx* c, int32_t k0, int32_t k1, int32_t 
   if (st != THOI_OK) return st;
   thoi_order_record* recs = (thoi_order_record*)c->rec_buf;
   TopEnt* tops = (TopEnt*)(c->rec_buf + sizeof(thoi_order_record));
+  int* gstatus = nullptr;
+  unsigned long long* gnref = nullptr;
+  if (group) {
+    st = group_meta(c, s, &gstatus, &gnref);
+    if (st != THOI_OK) return st;
+  }
   std::vector<uint64_t> parents;
   uint64_t evaluated = 0;
   int launches = 0;
@@ -1587,11 +1838,17 @@ extern "C" thoi_status thoi_greedy(thoi_ctx* c, int32_t k0, int32_t k1, int32_t 
   {
     const int32_t ord = k0;
     int nl = 0;
-    st = enqueue_measures(c, &ord, 1, 0, binom_host(N, k0), THOI_RED_PER_ORDER, nullptr, recs,
-                          tops, s, &nl);
+    if (group) {
+      uint64_t ev = 0;
+      st = enqueue_group(ctxs, D, &ord, 1, 0, binom_host(N, k0), measure, objective,
+                         THOI_RED_PER_ORDER, nullptr, recs, tops, gstatus, gnref, s, &nl, &ev);
+    } else {
+      st = enqueue_measures(c, &ord, 1, 0, binom_host(N, k0), THOI_RED_PER_ORDER, nullptr, recs,
+                            tops, s, &nl);
+    }
     if (st != THOI_OK) return st;
     launches += nl;
-    evaluated += binom_host(N, k0);
+    evaluated += binom_host(N, k0) * (uint64_t)D;
     st = take(0, k0);
     if (st != THOI_OK) return st;
   }
@@ -1618,8 +1875,13 @@ extern "C" thoi_status thoi_greedy(thoi_ctx* c, int32_t k0, int32_t k1, int32_t 
   bufs.p[2] = d_ids;
   CK(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
   bufs.p[3] = d_cnt;
-  CK(cudaMalloc(&b64, 3 * lstride * sizeof(double)));
+  // FP64 basis of the list; for a group also the D x list value matrix and
+  // the objective's basis
+  CK(cudaMalloc(&b64, (3 + (group ? (size_t)D + 3 : 0)) * lstride * sizeof(double)));
   bufs.p[4] = b64;
+  double* V = b64 + 3 * lstride;
+  double* gb = V + (size_t)D * lstride;
+  const Combine cg = group_combine();
   std::vector<uint64_t> cand;
   std::vector<unsigned long long> ids;
   for (int k = k0 + 1; k <= k1; k++) {
@@ -1646,35 +1908,62 @@ extern "C" thoi_status thoi_greedy(thoi_ctx* c, int32_t k0, int32_t k1, int32_t 
     r.off = 0;
     r.r0 = 0;
     r.r1 = binom_host(N, k);
-    NpletArgs a = base_args(c, r);
-    a.mode = 2;
-    a.flag_ids = d_ids;
-    a.flag_count = d_cnt;
-    a.flag_cap = n;
-    a.cancel = c->d_cancel;
-    int grid = 0;
-    CK(launch_nplet_f64s(a, true, b64, lstride, c->num_sms, s, &grid,
-                         c->num_sms * MAX_BLOCKS_PER_SM_OUT));
+    Combine rc = group_combine();
+    for (int d = 0; d < D; d++) {
+      NpletArgs a = base_args(ctxs[d], r);
+      a.mode = 2;
+      a.flag_ids = d_ids;
+      a.flag_count = d_cnt;
+      a.flag_cap = n;
+      int grid = 0;
+      CK(launch_nplet_f64s(a, true, b64, lstride, c->num_sms, s, &grid,
+                           c->num_sms * MAX_BLOCKS_PER_SM_OUT));
+      launches++;
+      if (group) {
+        CK(launch_group_pick(b64, lstride, d_cnt, n, a.cmb, measure, V + (size_t)d * lstride, s));
+        launches++;
+      } else {
+        rc = a.cmb;
+      }
+    }
+    const double* rb = b64;
+    if (group) {
+      CK(launch_group_combine(V, lstride, n, D, objective, nullptr, gb, lstride, c->num_sms, s));
+      launches++;
+      rb = gb;
+      rc = cg;
+    }
     // few candidates per order: a few blocks, so that the merge folds few lists
     int red_blocks = (int)(n / 4096) + 1;
     if (red_blocks > ref_cap) red_blocks = ref_cap;
-    CK(launch_reduce_list64(b64, lstride, d_ids, d_cnt, n, a.cmb, kappa, part, ptop, c->num_sms,
+    int grid = 0;
+    CK(launch_reduce_list64(rb, lstride, d_ids, d_cnt, n, rc, kappa, part, ptop, c->num_sms,
                             red_blocks, s, &grid));
-    MergeDescs D;
-    memset(&D, 0, sizeof D);
-    D.d[0].p32_off = 0;
-    D.d[0].g32 = grid;
-    D.d[0].k = k;
-    D.d[0].cmb = a.cmb;
-    CK(launch_merge(D, 1, part, ptop, part, ptop, kappa, recs, tops, s));
-    launches += 3;
-    evaluated += n;
+    MergeDescs MD;
+    memset(&MD, 0, sizeof MD);
+    MD.d[0].p32_off = 0;
+    MD.d[0].g32 = grid;
+    MD.d[0].k = k;
+    MD.d[0].cmb = rc;
+    CK(launch_merge(MD, 1, part, ptop, part, ptop, kappa, recs, tops, s));
+    launches += 2;
+    evaluated += n * (uint64_t)D;
     st = take(k - k0, k);
     if (st != THOI_OK) return st;
   }
   int hs = 0;
-  CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  for (int d = 0; d < D; d++) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, ctxs[d]->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    hs |= h;
+  }
+  if (group) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, gstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    hs |= h;
+  }
   if (stats) {
     memset(stats, 0, sizeof *stats);
     stats->nplets = evaluated;
@@ -1684,19 +1973,46 @@ extern "C" thoi_status thoi_greedy(thoi_ctx* c, int32_t k0, int32_t k1, int32_t 
   return THOI_OK;  // candidates that are not positive definite are left out, not fatal
 }
 
-// ------------------------------------------------------------------ API: simulated annealing
-extern "C" thoi_status thoi_anneal(thoi_ctx* c, int32_t k_lo, int32_t k_hi, int32_t n_chains,
-                                   int32_t iters, double T0, double alpha, int32_t measure,
-                                   int32_t maximize, uint64_t seed, uint64_t* final_masks,
-                                   double* final_values, uint64_t* best_masks,
-                                   double* best_values, thoi_stats* stats, void* stream) {
-  if (!c || k_lo < 1 || k_hi < k_lo || k_hi > c->N || k_hi > 32 || n_chains < 1 || iters < 0 ||
-      !(T0 > 0.0) || !(alpha > 0.0) || measure < THOI_H || measure > THOI_S || !final_masks ||
-      !final_values || !best_masks || !best_values)
+extern "C" thoi_status thoi_greedy(thoi_ctx* c, int32_t k0, int32_t k1, int32_t kappa,
+                                   int32_t measure, int32_t maximize, uint64_t* sets_out,
+                                   double* values_out, thoi_stats* stats, void* stream) {
+  if (!c || !sets_out || !values_out || k0 < 1 || k1 < k0 || k1 > c->N || kappa < 1 ||
+      kappa > THOI_MAX_TOP_M || measure < THOI_H || measure > THOI_S)
     return THOI_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  std::vector<Combine> tab(k_hi + 1);
-  for (int k = 0; k <= k_hi; k++) tab[k] = combine_for(c, k);
+  return greedy_impl(&c, 1, -1, k0, k1, kappa, measure, maximize, sets_out, values_out, stats,
+                     (cudaStream_t)stream);
+}
+
+extern "C" thoi_status thoi_group_greedy(thoi_ctx* const* ctxs, int32_t D, int32_t k0, int32_t k1,
+                                         int32_t kappa, int32_t measure, int32_t objective,
+                                         int32_t maximize, uint64_t* sets_out, double* values_out,
+                                         thoi_stats* stats, void* stream) {
+  thoi_status st = group_args_ok(ctxs, D, measure, objective);
+  if (st != THOI_OK) return st;
+  if (!sets_out || !values_out || k0 < 1 || k1 < k0 || k1 > ctxs[0]->N || kappa < 1 ||
+      kappa > THOI_MAX_TOP_M)
+    return THOI_ERR_INVALID_ARG;
+  return greedy_impl(ctxs, D, objective, k0, k1, kappa, measure, maximize, sets_out, values_out,
+                     stats, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ API: simulated annealing
+// Simulated annealing on one context's measure (D = 1) or on a group
+// objective over D contexts.
+static thoi_status anneal_impl(thoi_ctx* const* ctxs, int D, int objective, int32_t k_lo,
+                               int32_t k_hi, int32_t n_chains, int32_t iters, double T0,
+                               double alpha, int32_t measure, int32_t maximize, uint64_t seed,
+                               uint64_t* final_masks, double* final_values, uint64_t* best_masks,
+                               double* best_values, thoi_stats* stats, cudaStream_t s) {
+  const int nc = k_hi + 1;
+  // host staging: combine tables (D x nc), then the R and log-variance pointers
+  std::vector<Combine> tab((size_t)D * nc);
+  std::vector<const double*> ptrs(2 * (size_t)D);
+  for (int d = 0; d < D; d++) {
+    for (int k = 0; k < nc; k++) tab[(size_t)d * nc + k] = combine_for(ctxs[d], k);
+    ptrs[d] = ctxs[d]->R64;
+    ptrs[D + d] = ctxs[d]->ls;
+  }
   struct Bufs {
     void* p = nullptr;
     ~Bufs() {
@@ -1704,17 +2020,22 @@ extern "C" thoi_status thoi_anneal(thoi_ctx* c, int32_t k_lo, int32_t k_hi, int3
     }
   } buf;
   const size_t n = (size_t)n_chains;
-  const size_t bytes = (k_hi + 1) * sizeof(Combine) + n * (4 * 8 + 8);
+  const size_t tab_bytes = tab.size() * sizeof(Combine), ptr_bytes = ptrs.size() * sizeof(void*);
+  const size_t bytes = tab_bytes + ptr_bytes + n * (4 * 8 + 8);
   CK(cudaMalloc(&buf.p, bytes));
-  Combine* d_tab = (Combine*)buf.p;
-  unsigned long long* fm = (unsigned long long*)(d_tab + k_hi + 1);
+  unsigned char* base = (unsigned char*)buf.p;
+  Combine* d_tab = (Combine*)base;
+  const double** d_ptrs = (const double**)(base + tab_bytes);
+  unsigned long long* fm = (unsigned long long*)(base + tab_bytes + ptr_bytes);
   double* fv = (double*)(fm + n);
   unsigned long long* bm = (unsigned long long*)(fv + n);
   double* bv = (double*)(bm + n);
   unsigned long long* acc = (unsigned long long*)(bv + n);
-  CK(cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(Combine), cudaMemcpyHostToDevice, s));
-  CK(launch_anneal(c->R64, c->ls, c->N, k_lo, k_hi, d_tab, n_chains, iters, T0, alpha, measure,
-                   maximize, seed, fm, fv, bm, bv, acc, s));
+  CK(cudaMemcpyAsync(d_tab, tab.data(), tab_bytes, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_ptrs, ptrs.data(), ptr_bytes, cudaMemcpyHostToDevice, s));
+  CK(launch_anneal(d_ptrs, d_ptrs + D, D, objective, ctxs[0]->N, k_lo, k_hi, d_tab,
+                   ctxs[0]->R64, ctxs[0]->ls, n_chains, iters, T0, alpha, measure, maximize, seed,
+                   fm, fv, bm, bv, acc, s));
   CK(cudaMemcpyAsync(final_masks, fm, n * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(final_values, fv, n * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(best_masks, bm, n * 8, cudaMemcpyDeviceToHost, s));
@@ -1724,13 +2045,49 @@ extern "C" thoi_status thoi_anneal(thoi_ctx* c, int32_t k_lo, int32_t k_hi, int3
   CK(cudaStreamSynchronize(s));
   if (stats) {
     memset(stats, 0, sizeof *stats);
-    stats->nplets = (uint64_t)n * (uint64_t)(iters + 1);  // energies evaluated
+    stats->nplets = (uint64_t)n * (uint64_t)(iters + 1) * (uint64_t)D;  // evaluations
     unsigned long long a = 0;
     for (auto x : hacc) a += x;
-    stats->n_refactored = a;  // accepted moves (this entry point evaluates in FP64 only)
+    stats->n_refactored = a;  // accepted moves (these entry points evaluate in FP64 only)
     stats->launches = 1;
   }
   return THOI_OK;
+}
+
+static bool anneal_args_ok(int N, int32_t k_lo, int32_t k_hi, int32_t n_chains, int32_t iters,
+                           double T0, double alpha, int32_t measure, const void* a, const void* b,
+                           const void* c, const void* d) {
+  return k_lo >= 1 && k_hi >= k_lo && k_hi <= N && k_hi <= 32 && n_chains >= 1 && iters >= 0 &&
+         T0 > 0.0 && alpha > 0.0 && measure >= THOI_H && measure <= THOI_S && a && b && c && d;
+}
+
+extern "C" thoi_status thoi_anneal(thoi_ctx* c, int32_t k_lo, int32_t k_hi, int32_t n_chains,
+                                   int32_t iters, double T0, double alpha, int32_t measure,
+                                   int32_t maximize, uint64_t seed, uint64_t* final_masks,
+                                   double* final_values, uint64_t* best_masks,
+                                   double* best_values, thoi_stats* stats, void* stream) {
+  if (!c || !anneal_args_ok(c->N, k_lo, k_hi, n_chains, iters, T0, alpha, measure, final_masks,
+                            final_values, best_masks, best_values))
+    return THOI_ERR_INVALID_ARG;
+  return anneal_impl(&c, 1, -1, k_lo, k_hi, n_chains, iters, T0, alpha, measure, maximize, seed,
+                     final_masks, final_values, best_masks, best_values, stats,
+                     (cudaStream_t)stream);
+}
+
+extern "C" thoi_status thoi_group_anneal(thoi_ctx* const* ctxs, int32_t D, int32_t k_lo,
+                                         int32_t k_hi, int32_t n_chains, int32_t iters, double T0,
+                                         double alpha, int32_t measure, int32_t objective,
+                                         int32_t maximize, uint64_t seed, uint64_t* final_masks,
+                                         double* final_values, uint64_t* best_masks,
+                                         double* best_values, thoi_stats* stats, void* stream) {
+  thoi_status st = group_args_ok(ctxs, D, measure, objective);
+  if (st != THOI_OK) return st;
+  if (!anneal_args_ok(ctxs[0]->N, k_lo, k_hi, n_chains, iters, T0, alpha, measure, final_masks,
+                      final_values, best_masks, best_values))
+    return THOI_ERR_INVALID_ARG;
+  return anneal_impl(ctxs, D, objective, k_lo, k_hi, n_chains, iters, T0, alpha, measure,
+                     maximize, seed, final_masks, final_values, best_masks, best_values, stats,
+                     (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------------ API: autotune
