@@ -44,10 +44,10 @@ def flops_model(k: int) -> float:
 
 # DRAM bytes per nplet of the FP32 nplet kernels, from ncu captures on this
 # workload (dram__bytes_read.sum + dram__bytes_write.sum per launch / nplets):
-# dense and one-level prefix kernels at order 16 (145,422,675 nplets), the
-# two-level prefix kernel at order 15 (155,117,520); traffic grows with the
-# nplets written.  None: not captured for the current kernel.
-TRAFFIC_BYTES_PER_NPLET = {"dense": 13.36, "prefix": 69.6, "prefix2": 51.5}
+# the dense, one-level and two-level prefix kernels at order 16 (145,422,675
+# nplets); traffic grows with the nplets written.  None: not captured for the
+# current kernel.
+TRAFFIC_BYTES_PER_NPLET = {"dense": 13.32, "prefix": 69.67, "prefix2": 51.61}
 
 
 def grad_flops_model(k: int) -> float:
