@@ -24,11 +24,14 @@
 // and spread of the differences in two passes).  A group chain is one warp:
 // every lane runs the same schedule and draws, and the lanes share the
 // datasets of each evaluation (warp sums are butterflies, so every lane holds
-// the same bits and the warp never diverges on an acceptance).
+// the same bits and the warp never diverges on an acceptance).  One dataset
+// with fewer chains than lanes can fill (below SA_WARP_CHAINS) also runs a
+// warp per chain: the 32 lanes share each factorisation, a row per lane.
 #include <math.h>
 
 #include "internal.cuh"
 #include "nplet_common.cuh"
+#include "nplet_f64.cuh"
 
 namespace thoi {
 
@@ -211,13 +214,75 @@ __global__ void __launch_bounds__(SA_NT) k_anneal(const double* __restrict__ R64
            final_mask, final_val, best_mask, best_val, accepted);
 }
 
+constexpr int SA_GNT = 128;            // warp-per-chain kernels: four chains per block
+constexpr int SA_WARP_CHAINS = 16384;  // one dataset: a warp per chain below this many chains
+
+// One dataset, a warp per chain: the chain's k x k triangle and member list
+// in shared memory, row i on lane i (k <= 32), factorised by the 32 lanes
+// together (f64g_factor); every lane ends with the same value.
+__global__ void __launch_bounds__(SA_GNT)
+    k_anneal_warp(const double* __restrict__ R64, const double* __restrict__ ls, int N, int klo,
+                  int khi, const Combine* __restrict__ cmb_tab, int n_chains, int iters, double T0,
+                  double alpha, int measure, int maximize, unsigned long long seed,
+                  unsigned long long* __restrict__ final_mask, double* __restrict__ final_val,
+                  unsigned long long* __restrict__ best_mask, double* __restrict__ best_val,
+                  unsigned long long* __restrict__ accepted) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ldr = row_stride(N);
+  double* sR = reinterpret_cast<double*>(smem);
+  double* sls = sR + (size_t)N * ldr;
+  Combine* scmb = reinterpret_cast<Combine*>(sls + N);
+  const int tri = khi * (khi + 1) / 2;
+  double* A = reinterpret_cast<double*>(scmb + khi + 1) + (size_t)(threadIdx.x >> 5) * tri;
+  int* C = reinterpret_cast<int*>(reinterpret_cast<double*>(scmb + khi + 1) +
+                                  (size_t)(SA_GNT / 32) * tri) +
+           (threadIdx.x >> 5) * khi;
+  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sR[(q / N) * ldr + (q % N)] = R64[q];
+  for (int q = threadIdx.x; q < N; q += blockDim.x) sls[q] = ls[q];
+  for (int q = threadIdx.x; q <= khi; q += blockDim.x) scmb[q] = cmb_tab[q];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int chain = (int)(((unsigned)blockIdx.x * SA_GNT + threadIdx.x) >> 5);
+  if (chain >= n_chains) return;  // whole warps leave together
+#define AG(i, j) A[((((i) * ((i) + 1)) >> 1) + (j))]
+  auto value = [&](unsigned long long mask) -> double {
+    const int k = __popcll(mask);
+    if (lane < k) C[lane] = nth_member(mask, lane);
+    __syncwarp();
+    double lsum = 0.0;
+    if (lane < k) {
+      const int ci = C[lane];
+      const double* row = sR + ci * ldr;
+      lsum = sls[ci];
+      for (int j = 0; j <= lane; j++) AG(lane, j) = row[C[j]];
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    __syncwarp();
+    double P1 = 1.0, P2 = 1.0;
+    int E1 = 0, E2 = 0;
+    bool bad = false;
+    f64g_factor<32>(A, k, lane, 0xffffffffu, P1, E1, P2, E2, bad);
+    bad = __any_sync(0xffffffffu, bad);
+    const double lr = __shfl_sync(0xffffffffu, -log_of(P1, E1), 0);
+    __syncwarp();  // the triangle is rewritten by the next evaluation
+    if (bad) return __longlong_as_double(0x7ff8000000000000ll);
+    const double sp = log_of(P2, E2);
+    const CombineV<double> cv(scmb[k]);
+    double v[5];
+    combine5<double>(lr, sp, lsum, cv, v);
+    return pick5(v, measure);
+  };
+#undef AG
+  sa_chain(chain, N, klo, khi, iters, T0, alpha, maximize, seed, value, lane == 0, final_mask,
+           final_val, best_mask, best_val, accepted);
+}
+
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
-
-constexpr int SA_GNT = 128;  // group kernel: four chains (warps) per block
 
 // D > 1 datasets: a warp per chain.  Lane L evaluates datasets L, L + 32, ...
 // For Cohen's d the datasets are taken in pair order h = 2j + side (side 0:
@@ -281,6 +346,23 @@ cudaError_t launch_anneal(const double* const* Rs, const double* const* lss, int
   if (khi > SA_KMAX || klo < 1 || khi < klo || khi > N || n_chains < 1 || iters < 0 || D < 1 ||
       D > THOI_MAX_GROUP)
     return cudaErrorInvalidValue;
+  if (D == 1 && n_chains < SA_WARP_CHAINS) {
+    const size_t sm = ((size_t)N * row_stride(N) + N) * sizeof(double) +
+                      (size_t)(khi + 1) * sizeof(Combine) +
+                      (size_t)(SA_GNT / 32) * ((size_t)khi * (khi + 1) / 2 * sizeof(double) +
+                                               (size_t)khi * sizeof(int));
+    const long long threads = (long long)n_chains * 32;
+    const int grid = (int)((threads + SA_GNT - 1) / SA_GNT);
+    if (sm > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(
+          k_anneal_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    k_anneal_warp<<<grid, SA_GNT, sm, s>>>(R0, ls0, N, klo, khi, cmb_tab, n_chains, iters, T0,
+                                           alpha, measure, maximize, seed, final_mask, final_val,
+                                           best_mask, best_val, accepted);
+    return cudaGetLastError();
+  }
   if (D == 1) {
     const size_t sm = ((size_t)N * row_stride(N) + N) * sizeof(double) +
                       (size_t)(khi + 1) * sizeof(Combine);

@@ -98,6 +98,73 @@ __device__ void f64s_body(const NpletArgs& a, double* __restrict__ b64, unsigned
 
 namespace thoi {
 
+// The factorisation steps of a group of G lanes on the k x k lower triangle
+// A (packed by rows, row i owned by lane i mod G; the lanes of gmask meet at
+// warp barriers): LDL^T (1/D_p left on the diagonal), V = L^-1 in place, and
+// the inverse diagonal p_j.  Lane 0 returns the product of the 1/D_p in
+// (P1, E1) and every lane the product of the p_j in (P2, E2); bad is set on
+// lane 0 for a pivot that is not positive and finite, and on every lane for
+// an overflowing p_j product.
+template <int G>
+__device__ __forceinline__ void f64g_factor(double* __restrict__ A, const int k, const int g,
+                                            const unsigned gmask, double& P1, int& E1,
+                                            double& P2, int& E2, bool& bad) {
+#define AG(i, j) A[((((i) * ((i) + 1)) >> 1) + (j))]
+  // LDL^T
+  for (int p = 0; p < k; p++) {
+    // the owner of row p divides once and publishes 1/D_p on the diagonal
+    // (an FP64 division is a long sequence on the narrow FP64 pipe); lane
+    // 0 keeps the product of the 1/D_p, so log det R_S = -log(product)
+    if (g == p % G) AG(p, p) = 1.0 / AG(p, p);
+    __syncwarp(gmask);
+    const double rd = AG(p, p);
+    if (g == 0) {
+      bad |= !(rd > 0.0) | !(rd < pinf<double>());  // D_p <= 0, zero, or not finite
+      P1 *= rd;
+      if ((p & 7) == 7 || p == k - 1) renorm(P1, E1, bad);
+    }
+    const int i0 = p + 1 + ((g - (p + 1) % G) + G) % G;  // first owned row > p
+    for (int i = i0; i < k; i += G) {
+      const double u = AG(i, p) * rd;
+      for (int j = p + 1; j <= i; j++) AG(i, j) = fma(-u, AG(j, p), AG(i, j));
+    }
+    __syncwarp(gmask);
+    for (int i = i0; i < k; i += G) AG(i, p) *= rd;
+    __syncwarp(gmask);
+  }
+  // V = L^-1 in place
+  for (int mm = 0; mm + 1 < k; mm++) {
+    const int i0 = mm + 1 + ((g - (mm + 1) % G) + G) % G;
+    for (int i = i0; i < k; i += G) {
+      const double l = AG(i, mm);
+      for (int c = 0; c < mm; c++) AG(i, c) = fma(-l, AG(mm, c), AG(i, c));
+      AG(i, mm) = -l;
+    }
+    __syncwarp(gmask);
+  }
+  // inverse diagonal, product of the p_j across the group
+  bool bad2 = false;
+  for (int j = g; j < k; j += G) {
+    double pj = AG(j, j);
+    for (int i = j + 1; i < k; i++) {
+      const double v = AG(i, j);
+      pj = fma(v * AG(i, i), v, pj);
+    }
+    P2 *= pj;
+    renorm(P2, E2, bad2);
+  }
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    const double q = __shfl_xor_sync(gmask, P2, o);
+    const int eq = __shfl_xor_sync(gmask, E2, o);
+    P2 *= q;
+    E2 += eq;
+    renorm(P2, E2, bad2);
+  }
+  bad |= __any_sync(gmask, bad2);
+#undef AG
+}
+
 // FP64 nplet computation with G lanes per nplet: the group's k x k matrix
 // (lower triangle) and index list live in shared memory, rows are owned
 // cyclically (row i by lane i mod G), and the lanes meet at a warp barrier
@@ -167,63 +234,10 @@ __device__ void f64g_body(const NpletArgs& a, double* __restrict__ b64, unsigned
 #pragma unroll
     for (int o = 1; o < G; o <<= 1) lsum += __shfl_xor_sync(gmask, lsum, o);
     __syncwarp(gmask);
-    // LDL^T
-    double P1 = 1.0;
-    int E1 = 0;
+    double P1 = 1.0, P2 = 1.0;
+    int E1 = 0, E2 = 0;
     bool bad = false;
-    for (int p = 0; p < k; p++) {
-      // the owner of row p divides once and publishes 1/D_p on the diagonal
-      // (an FP64 division is a long sequence on the narrow FP64 pipe); lane
-      // 0 keeps the product of the 1/D_p, so log det R_S = -log(product)
-      if (g == p % G) AG(p, p) = 1.0 / AG(p, p);
-      __syncwarp(gmask);
-      const double rd = AG(p, p);
-      if (g == 0) {
-        bad |= !(rd > 0.0) | !(rd < pinf<double>());  // D_p <= 0, zero, or not finite
-        P1 *= rd;
-        if ((p & 7) == 7 || p == k - 1) renorm(P1, E1, bad);
-      }
-      const int i0 = p + 1 + ((g - (p + 1) % G) + G) % G;  // first owned row > p
-      for (int i = i0; i < k; i += G) {
-        const double u = AG(i, p) * rd;
-        for (int j = p + 1; j <= i; j++) AG(i, j) = fma(-u, AG(j, p), AG(i, j));
-      }
-      __syncwarp(gmask);
-      for (int i = i0; i < k; i += G) AG(i, p) *= rd;
-      __syncwarp(gmask);
-    }
-    // V = L^-1 in place
-    for (int mm = 0; mm + 1 < k; mm++) {
-      const int i0 = mm + 1 + ((g - (mm + 1) % G) + G) % G;
-      for (int i = i0; i < k; i += G) {
-        const double l = AG(i, mm);
-        for (int c = 0; c < mm; c++) AG(i, c) = fma(-l, AG(mm, c), AG(i, c));
-        AG(i, mm) = -l;
-      }
-      __syncwarp(gmask);
-    }
-    // inverse diagonal, product of the p_j across the group
-    double P2 = 1.0;
-    int E2 = 0;
-    bool bad2 = false;
-    for (int j = g; j < k; j += G) {
-      double pj = AG(j, j);
-      for (int i = j + 1; i < k; i++) {
-        const double v = AG(i, j);
-        pj = fma(v * AG(i, i), v, pj);
-      }
-      P2 *= pj;
-      renorm(P2, E2, bad2);
-    }
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) {
-      const double q = __shfl_xor_sync(gmask, P2, o);
-      const int eq = __shfl_xor_sync(gmask, E2, o);
-      P2 *= q;
-      E2 += eq;
-      renorm(P2, E2, bad2);
-    }
-    bad |= __any_sync(gmask, bad2);
+    f64g_factor<G>(A, k, g, gmask, P1, E1, P2, E2, bad);
     if (g == 0) {
       const double lr = -log_of(P1, E1), sp = log_of(P2, E2);
       if (bad) atomicOr(a.status, ST_NOT_PD);

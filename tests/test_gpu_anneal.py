@@ -46,3 +46,30 @@ def test_anneal_arguments():
                     (3, 5, 4, 10, 0.0, 0.9)]:
             with pytest.raises(P.ThoiError):
                 c.anneal(*bad)
+
+
+@pytest.mark.parametrize("chains", [16384, 3])
+def test_anneal_thread_and_warp_kernels(chains):
+    # 16384 chains or more run a thread per chain, fewer a warp per chain; the
+    # first chains of each match the oracle's (chains are independent)
+    S = workloads.random_corr(np.random.default_rng(64), 20)
+    iters, T0, alpha, seed = 30, 0.4, 0.95, 2024
+    klo, khi = (3, 20) if chains == 3 else (3, 12)
+    ref = oracle.anneal(S, klo, khi, 3, iters, T0, alpha, "O", True, seed)
+    with P.Context(Sigma=S) as c:
+        fm, fv, bm, bv = c.anneal(klo, khi, chains, iters, T0, alpha, "O", True, seed)
+    assert _sets(fm[:3]) == ref[0] and _sets(bm[:3]) == ref[2]
+    np.testing.assert_allclose(fv[:3], ref[1], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(bv[:3], ref[3], rtol=0, atol=1e-10)
+    if chains > 3:
+        assert all(3 <= bin(int(m)).count("1") <= 12 for m in fm)
+
+
+def test_anneal_warp_kernel_order_32():
+    # the largest order the annealing takes: 32 members, one row per lane
+    S = workloads.random_corr(np.random.default_rng(65), 36)
+    ref = oracle.anneal(S, 28, 32, 4, 25, 0.2, 0.9, "S", False, 5)
+    with P.Context(Sigma=S) as c:
+        fm, fv, bm, bv = c.anneal(28, 32, 4, 25, 0.2, 0.9, "S", False, 5)
+    assert _sets(fm) == ref[0] and _sets(bm) == ref[2]
+    np.testing.assert_allclose(bv, ref[3], rtol=0, atol=1e-9)
