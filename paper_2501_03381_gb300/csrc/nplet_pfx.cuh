@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(RED_NT, PfxBlocks<K>::value) k_nplet_pfx(const
 #pragma unroll
         for (int r = i - 1; r >= 0; r--) {
           float s = -x[r];
+          // x[r + 1], the latest finished, enters last: each x[r] then waits one FMA for it
 #pragma unroll
-          for (int t = r + 1; t < i; t++) s = fmaf(-Lh[t][r], x[t], s);
+          for (int t = i - 1; t > r; t--) s = fmaf(-Lh[t][r], x[t], s);
           x[r] = s;
         }
 #pragma unroll
@@ -149,8 +150,9 @@ __global__ void __launch_bounds__(RED_NT, PfxBlocks<K>::value) k_nplet_pfx(const
 #pragma unroll
         for (int r = P - 1; r >= 0; r--) {
           float s = -x[r];
+          // x[r + 1], the latest finished, enters last: each x[r] then waits one FMA for it
 #pragma unroll
-          for (int t = r + 1; t < P; t++) s = fmaf(-Lh[t][r], x[t], s);
+          for (int t = P - 1; t > r; t--) s = fmaf(-Lh[t][r], x[t], s);
           x[r] = s;
         }
         bool bad = badp;
@@ -159,12 +161,14 @@ __global__ void __launch_bounds__(RED_NT, PfxBlocks<K>::value) k_nplet_pfx(const
         renorm(Pl, El, bad);
         float P2 = dn, trace = dn;
         int E2 = 0;
+        // in the order the backward solve finishes the x[r] (descending), so the
+        // product and the trace overlap with it
 #pragma unroll
-        for (int r = 0; r < P; r++) {
+        for (int r = P - 1; r >= 0; r--) {
           const float pr = fmaf(x[r] * dn, x[r], qd[r]);
           trace += pr;
           P2 *= pr;
-          if ((r & 3) == 3 || r == P - 1) renorm(P2, E2, bad);
+          if (((P - 1 - r) & 3) == 3 || r == 0) renorm(P2, E2, bad);
         }
         const float lr = log_of(Pl, El), sp = log_of(P2, E2);
         const float lsum = lsp + sls[cl];
