@@ -47,7 +47,7 @@ def flops_model(k: int) -> float:
 # the dense, one-level and two-level prefix kernels at order 16 (145,422,675
 # nplets); traffic grows with the nplets written.  None: not captured for the
 # current kernel.
-TRAFFIC_BYTES_PER_NPLET = {"dense": 13.32, "prefix": 69.67, "prefix2": 51.61}
+TRAFFIC_BYTES_PER_NPLET = {"dense": 13.32, "prefix": 69.54, "prefix2": 51.25}
 
 
 def grad_flops_model(k: int) -> float:
