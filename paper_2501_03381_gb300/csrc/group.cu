@@ -37,9 +37,11 @@ __global__ void k_group_fold(const int* status, const unsigned long long* flag_c
 }
 
 __global__ void __launch_bounds__(GRP_NT)
-    k_group_combine(const double* __restrict__ V, unsigned long long ld, unsigned long long n, int D,
-                    int objective, double* __restrict__ out, double* __restrict__ basis,
+    k_group_combine(const double* __restrict__ V, unsigned long long ld, unsigned long long n,
+                    const unsigned long long* __restrict__ count, int D, int objective,
+                    double* __restrict__ out, double* __restrict__ basis,
                     unsigned long long bstride) {
+  if (count && *count < n) n = *count;  // a list whose length is known on the device
   const unsigned long long stride = (unsigned long long)gridDim.x * GRP_NT;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   for (unsigned long long i = (unsigned long long)blockIdx.x * GRP_NT + threadIdx.x; i < n;
@@ -112,12 +114,14 @@ cudaError_t launch_group_fold(const int* status, const unsigned long long* flag_
 }
 
 cudaError_t launch_group_combine(const double* V, unsigned long long ld, unsigned long long n,
-                                 int D, int objective, double* out, double* basis,
-                                 unsigned long long bstride, int num_sms, cudaStream_t s) {
+                                 const unsigned long long* count, int D, int objective,
+                                 double* out, double* basis, unsigned long long bstride,
+                                 int num_sms, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   long long grid = (long long)((n + GRP_NT - 1) / GRP_NT);
   if (grid > (long long)num_sms * 8) grid = (long long)num_sms * 8;
-  k_group_combine<<<(unsigned)grid, GRP_NT, 0, s>>>(V, ld, n, D, objective, out, basis, bstride);
+  k_group_combine<<<(unsigned)grid, GRP_NT, 0, s>>>(V, ld, n, count, D, objective, out, basis,
+                                                    bstride);
   return cudaGetLastError();
 }
 

@@ -213,12 +213,23 @@ cudaError_t launch_group_fold(const int* status, const unsigned long long* flag_
                               unsigned long long flag_cap, int* gstatus, unsigned long long* gnref,
                               cudaStream_t s);
 cudaError_t launch_group_combine(const double* V, unsigned long long ld, unsigned long long n,
-                                 int D, int objective, double* out, double* basis,
-                                 unsigned long long bstride, int num_sms, cudaStream_t s);
+                                 const unsigned long long* count, int D, int objective,
+                                 double* out, double* basis, unsigned long long bstride,
+                                 int num_sms, cudaStream_t s);
 cudaError_t launch_group_pick(const double* b64, unsigned long long lstride,
                               const unsigned long long* count, unsigned long long cap,
                               Combine cmb, int measure, double* row, cudaStream_t s);
 cudaError_t launch_group_fix(thoi_order_record* recs, int n, cudaStream_t s);
+// Greedy expansion on the device: parents = the first min(top_count, kappa)
+// entries of `tops` (one side of the previous order's records, order kp);
+// distinct candidates of order kp + 1 appended as lexicographic ranks to ids
+// (count: device counter, zeroed by the caller; table: tsize zeroed slots,
+// tsize a power of two >= 2 kappa N).
+cudaError_t launch_greedy_expand(const thoi_order_record* rec, const TopEnt* tops, int kappa,
+                                 int N, int kp, const unsigned long long* binom,
+                                 unsigned long long* table, unsigned long long tsize,
+                                 unsigned long long* ids, unsigned long long* count,
+                                 cudaStream_t s);
 
 // ------------------------------------------------------------------ multi-dataset batch
 // Many datasets of uneven (N, T) in one graph: per order k one persistent

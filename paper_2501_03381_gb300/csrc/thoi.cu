@@ -1136,7 +1136,7 @@ static thoi_status enqueue_group(thoi_ctx* const* ctxs, int D, const int32_t* or
         launches += nl + 1;
       }
       ev += n * (uint64_t)D;
-      CK(launch_group_combine(V, ld, n, D, objective,
+      CK(launch_group_combine(V, ld, n, nullptr, D, objective,
                               red ? nullptr : out_dev + (r.off + a0 - id_begin),
                               red ? gb : nullptr, ld, c0->num_sms, s));
       launches++;
@@ -1761,14 +1761,8 @@ extern "C" thoi_status thoi_batch_measures(thoi_ctx* const* ctxs, int32_t D, int
 // evaluated, and the kappa best become the next selection.  Evaluation in the
 // FP64 path on the device (shared-memory FP64 kernels), selection on the
 // device by the per-block top lists and their merge, ranked by one measure;
-// ties go to the smallest lexicographic rank.  The host only forms and
-// de-duplicates the candidate sets (at most kappa * N per order).
-static uint64_t set_rank(int N, const int* idx, int k) {
-  uint64_t rp = 0;
-  for (int i = 0; i < k; i++) rp += binom_host(N - 1 - idx[i], k - i);
-  return binom_host(N, k) - 1 - rp;
-}
-
+// ties go to the smallest lexicographic rank.  The candidate sets (at most
+// kappa * N per order) are formed and de-duplicated on the device too.
 static uint64_t rank_to_mask(int N, int k, uint64_t rank) {
   int32_t idx[THOI_MAX_N];
   int32_t kk = 0;
@@ -1780,7 +1774,11 @@ static uint64_t rank_to_mask(int N, int k, uint64_t rank) {
 }
 
 // Greedy search on one context's measure (objective < 0) or on a group
-// objective over D contexts.
+// objective over D contexts.  Every order runs on the stream: the exhaustive
+// records of order k0, then per order the device expansion of the selected
+// sets (k_greedy_expand), the FP64 list evaluation, the list reduction and
+// the merge into that order's records; the host reads all orders' top lists
+// once at the end.
 static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int32_t k0,
                                int32_t k1, int32_t kappa, int32_t measure, int32_t maximize,
                                uint64_t* sets_out, double* values_out, thoi_stats* stats,
@@ -1803,37 +1801,57 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
   }
   c->opt.top_m = kappa;
   c->top_meas = measure;
-  const size_t rec_bytes = thoi_records_bytes(1, kappa);
-  std::vector<unsigned char> host(rec_bytes);
-  thoi_status st = grow(&c->rec_buf, &c->rec_cap, rec_bytes);
-  if (st != THOI_OK) return st;
-  thoi_order_record* recs = (thoi_order_record*)c->rec_buf;
-  TopEnt* tops = (TopEnt*)(c->rec_buf + sizeof(thoi_order_record));
   int* gstatus = nullptr;
   unsigned long long* gnref = nullptr;
+  thoi_status st = THOI_OK;
   if (group) {
     st = group_meta(c, s, &gstatus, &gnref);
     if (st != THOI_OK) return st;
   }
-  std::vector<uint64_t> parents;
-  uint64_t evaluated = 0;
-  int launches = 0;
-  auto take = [&](int level, int k) -> thoi_status {
-    CK(cudaMemcpyAsync(host.data(), c->rec_buf, rec_bytes, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const thoi_order_record* R = (const thoi_order_record*)host.data();
-    const thoi_top_entry* T =
-        (const thoi_top_entry*)(host.data() + sizeof(thoi_order_record)) + (size_t)side * kappa;
-    const int n = R->top_count < kappa ? R->top_count : kappa;
-    parents.clear();
-    for (int i = 0; i < n; i++) {
-      const uint64_t m = rank_to_mask(N, k, T[i].id);
-      sets_out[(size_t)level * kappa + i] = m;
-      values_out[(size_t)level * kappa + i] = T[i].value;
-      parents.push_back(m);
+  // device buffers of the whole search
+  const int ref_cap = c->num_sms * REFACTOR_BLOCKS_PER_SM;
+  const size_t cap = (size_t)kappa * N;
+  const size_t lstride = (cap + 63) / 64 * 64;
+  size_t tsize = 1;
+  while (tsize < 2 * cap) tsize <<= 1;
+  const size_t per_level = sizeof(thoi_order_record) + 2 * (size_t)kappa * sizeof(TopEnt);
+  struct Bufs {
+    void* p[7];
+    ~Bufs() {
+      for (void* q : p) if (q) cudaFree(q);
     }
-    return THOI_OK;
+  } bufs{{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}};
+  PartRec* part = nullptr;
+  TopEnt* ptop = nullptr;
+  unsigned long long* d_ids = nullptr;
+  unsigned long long* d_cnt = nullptr;  // candidates per order
+  double* b64 = nullptr;
+  unsigned long long* table = nullptr;
+  unsigned char* d_lv = nullptr;        // per order: record, then 2 x kappa top entries
+  CK(cudaMalloc(&part, ref_cap * sizeof(PartRec)));
+  bufs.p[0] = part;
+  CK(cudaMalloc(&ptop, (size_t)ref_cap * 2 * kappa * sizeof(TopEnt)));
+  bufs.p[1] = ptop;
+  CK(cudaMalloc(&d_ids, cap * sizeof(unsigned long long)));
+  bufs.p[2] = d_ids;
+  CK(cudaMalloc(&d_cnt, (size_t)levels * sizeof(unsigned long long)));
+  bufs.p[3] = d_cnt;
+  // FP64 basis of the list; for a group also the D x list value matrix and
+  // the objective's basis
+  CK(cudaMalloc(&b64, (3 + (group ? (size_t)D + 3 : 0)) * lstride * sizeof(double)));
+  bufs.p[4] = b64;
+  CK(cudaMalloc(&table, tsize * sizeof(unsigned long long)));
+  bufs.p[5] = table;
+  CK(cudaMalloc(&d_lv, (size_t)levels * per_level));
+  bufs.p[6] = d_lv;
+  CK(cudaMemsetAsync(d_cnt, 0, (size_t)levels * sizeof(unsigned long long), s));
+  auto rec_at = [&](int lv) { return (thoi_order_record*)(d_lv + (size_t)lv * per_level); };
+  auto tops_at = [&](int lv) {
+    return (TopEnt*)(d_lv + (size_t)lv * per_level + sizeof(thoi_order_record));
   };
+  double* V = b64 + 3 * lstride;
+  double* gb = V + (size_t)D * lstride;
+  int launches = 0;
   // order k0: exhaustive
   {
     const int32_t ord = k0;
@@ -1841,68 +1859,25 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
     if (group) {
       uint64_t ev = 0;
       st = enqueue_group(ctxs, D, &ord, 1, 0, binom_host(N, k0), measure, objective,
-                         THOI_RED_PER_ORDER, nullptr, recs, tops, gstatus, gnref, s, &nl, &ev);
+                         THOI_RED_PER_ORDER, nullptr, rec_at(0), tops_at(0), gstatus, gnref, s,
+                         &nl, &ev);
     } else {
-      st = enqueue_measures(c, &ord, 1, 0, binom_host(N, k0), THOI_RED_PER_ORDER, nullptr, recs,
-                            tops, s, &nl);
+      st = enqueue_measures(c, &ord, 1, 0, binom_host(N, k0), THOI_RED_PER_ORDER, nullptr,
+                            rec_at(0), tops_at(0), s, &nl);
     }
     if (st != THOI_OK) return st;
     launches += nl;
-    evaluated += binom_host(N, k0) * (uint64_t)D;
-    st = take(0, k0);
-    if (st != THOI_OK) return st;
   }
-  // orders k0+1 .. k1: expansion of the selection
-  const int ref_cap = c->num_sms * REFACTOR_BLOCKS_PER_SM;
-  PartRec* part = nullptr;
-  TopEnt* ptop = nullptr;
-  unsigned long long* d_ids = nullptr;
-  unsigned long long* d_cnt = nullptr;
-  double* b64 = nullptr;
-  struct Bufs {
-    void* p[5];
-    ~Bufs() {
-      for (void* q : p) if (q) cudaFree(q);
-    }
-  } bufs{{nullptr, nullptr, nullptr, nullptr, nullptr}};
-  const size_t cap = (size_t)kappa * N;
-  const size_t lstride = (cap + 63) / 64 * 64;
-  CK(cudaMalloc(&part, ref_cap * sizeof(PartRec)));
-  bufs.p[0] = part;
-  CK(cudaMalloc(&ptop, (size_t)ref_cap * 2 * kappa * sizeof(TopEnt)));
-  bufs.p[1] = ptop;
-  CK(cudaMalloc(&d_ids, cap * sizeof(unsigned long long)));
-  bufs.p[2] = d_ids;
-  CK(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
-  bufs.p[3] = d_cnt;
-  // FP64 basis of the list; for a group also the D x list value matrix and
-  // the objective's basis
-  CK(cudaMalloc(&b64, (3 + (group ? (size_t)D + 3 : 0)) * lstride * sizeof(double)));
-  bufs.p[4] = b64;
-  double* V = b64 + 3 * lstride;
-  double* gb = V + (size_t)D * lstride;
-  const Combine cg = group_combine();
-  std::vector<uint64_t> cand;
-  std::vector<unsigned long long> ids;
+  // orders k0+1 .. k1: expansion of the selection, on the device
+  int red_blocks = (int)(cap / 4096) + 1;  // few candidates: a few blocks, few lists to merge
+  if (red_blocks > ref_cap) red_blocks = ref_cap;
   for (int k = k0 + 1; k <= k1; k++) {
-    cand.clear();
-    for (uint64_t p : parents)
-      for (int v = 0; v < N; v++)
-        if (!(p >> v & 1ull)) cand.push_back(p | 1ull << v);
-    std::sort(cand.begin(), cand.end());
-    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-    if (cand.empty()) break;
-    ids.resize(cand.size());
-    for (size_t i = 0; i < cand.size(); i++) {
-      int idx[THOI_MAX_N];
-      int q = 0;
-      for (int v = 0; v < N; v++)
-        if (cand[i] >> v & 1ull) idx[q++] = v;
-      ids[i] = set_rank(N, idx, k);
-    }
-    const unsigned long long n = ids.size();
-    CK(cudaMemcpyAsync(d_ids, ids.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_cnt, &n, sizeof(n), cudaMemcpyHostToDevice, s));
+    const int lv = k - k0;
+    unsigned long long* cnt = d_cnt + lv;
+    CK(cudaMemsetAsync(table, 0, tsize * sizeof(unsigned long long), s));
+    CK(launch_greedy_expand(rec_at(lv - 1), tops_at(lv - 1) + (size_t)side * kappa, kappa, N,
+                            k - 1, c->binom, table, tsize, d_ids, cnt, s));
+    launches++;
     SlotRange r;
     r.k = k;
     r.off = 0;
@@ -1913,14 +1888,14 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
       NpletArgs a = base_args(ctxs[d], r);
       a.mode = 2;
       a.flag_ids = d_ids;
-      a.flag_count = d_cnt;
-      a.flag_cap = n;
+      a.flag_count = cnt;
+      a.flag_cap = cap;
       int grid = 0;
       CK(launch_nplet_f64s(a, true, b64, lstride, c->num_sms, s, &grid,
                            c->num_sms * MAX_BLOCKS_PER_SM_OUT));
       launches++;
       if (group) {
-        CK(launch_group_pick(b64, lstride, d_cnt, n, a.cmb, measure, V + (size_t)d * lstride, s));
+        CK(launch_group_pick(b64, lstride, cnt, cap, a.cmb, measure, V + (size_t)d * lstride, s));
         launches++;
       } else {
         rc = a.cmb;
@@ -1928,16 +1903,14 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
     }
     const double* rb = b64;
     if (group) {
-      CK(launch_group_combine(V, lstride, n, D, objective, nullptr, gb, lstride, c->num_sms, s));
+      CK(launch_group_combine(V, lstride, cap, cnt, D, objective, nullptr, gb, lstride,
+                              c->num_sms, s));
       launches++;
       rb = gb;
-      rc = cg;
+      rc = group_combine();
     }
-    // few candidates per order: a few blocks, so that the merge folds few lists
-    int red_blocks = (int)(n / 4096) + 1;
-    if (red_blocks > ref_cap) red_blocks = ref_cap;
     int grid = 0;
-    CK(launch_reduce_list64(rb, lstride, d_ids, d_cnt, n, rc, kappa, part, ptop, c->num_sms,
+    CK(launch_reduce_list64(rb, lstride, d_ids, cnt, cap, rc, kappa, part, ptop, c->num_sms,
                             red_blocks, s, &grid));
     MergeDescs MD;
     memset(&MD, 0, sizeof MD);
@@ -1945,12 +1918,14 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
     MD.d[0].g32 = grid;
     MD.d[0].k = k;
     MD.d[0].cmb = rc;
-    CK(launch_merge(MD, 1, part, ptop, part, ptop, kappa, recs, tops, s));
+    CK(launch_merge(MD, 1, part, ptop, part, ptop, kappa, rec_at(lv), tops_at(lv), s));
     launches += 2;
-    evaluated += n * (uint64_t)D;
-    st = take(k - k0, k);
-    if (st != THOI_OK) return st;
   }
+  // every order's selection, read once
+  std::vector<unsigned char> host((size_t)levels * per_level);
+  std::vector<unsigned long long> counts(levels);
+  CK(cudaMemcpyAsync(host.data(), d_lv, host.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(counts.data(), d_cnt, (size_t)levels * 8, cudaMemcpyDeviceToHost, s));
   int hs = 0;
   for (int d = 0; d < D; d++) {
     int h = 0;
@@ -1964,9 +1939,24 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
     CK(cudaStreamSynchronize(s));
     hs |= h;
   }
+  CK(cudaStreamSynchronize(s));
+  uint64_t evaluated = binom_host(N, k0);
+  for (int lv = 0; lv < levels; lv++) {
+    const int k = k0 + lv;
+    const thoi_order_record* R = (const thoi_order_record*)(host.data() + (size_t)lv * per_level);
+    const thoi_top_entry* T =
+        (const thoi_top_entry*)(host.data() + (size_t)lv * per_level + sizeof(thoi_order_record)) +
+        (size_t)side * kappa;
+    const int n = R->top_count < kappa ? R->top_count : kappa;
+    for (int i = 0; i < n; i++) {
+      sets_out[(size_t)lv * kappa + i] = rank_to_mask(N, k, T[i].id);
+      values_out[(size_t)lv * kappa + i] = T[i].value;
+    }
+    if (lv > 0) evaluated += counts[lv];
+  }
   if (stats) {
     memset(stats, 0, sizeof *stats);
-    stats->nplets = evaluated;
+    stats->nplets = evaluated * (uint64_t)D;
     stats->launches = launches;
   }
   if (hs & ST_CANCELLED) return THOI_ERR_CANCELLED;
