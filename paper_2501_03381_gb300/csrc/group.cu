@@ -74,19 +74,40 @@ __global__ void __launch_bounds__(GRP_NT)
   }
 }
 
-// One measure of each listed nplet from its FP64 basis triple (NaN = not
-// positive definite), into row `row` of the group matrix.
+// A candidate list shared by D datasets, replicated into D regions of stride
+// cap_pad (the batched FP64 kernel reads each slot's list at its own offset),
+// with the list length copied to every slot's counter.
+__global__ void k_group_replicate(const unsigned long long* __restrict__ ids,
+                                  const unsigned long long* __restrict__ count,
+                                  unsigned long long cap, unsigned long long cap_pad,
+                                  unsigned long long* __restrict__ ids_rep,
+                                  unsigned long long* __restrict__ counts_rep) {
+  const unsigned long long n = *count < cap ? *count : cap;
+  const int d = blockIdx.y;
+  if (blockIdx.x == 0 && threadIdx.x == 0) counts_rep[d] = n;
+  for (unsigned long long e = (unsigned long long)blockIdx.x * GRP_NT + threadIdx.x; e < n;
+       e += (unsigned long long)gridDim.x * GRP_NT)
+    ids_rep[(size_t)d * cap_pad + e] = ids[e];
+}
+
+// One measure of every listed nplet of every dataset (grid.y = dataset) from
+// the batched FP64 basis (dataset d's arrays at offset d * cap_pad, array
+// stride lstride), into row d of the value matrix (row stride cap_pad).
 __global__ void __launch_bounds__(GRP_NT)
-    k_group_pick(const double* __restrict__ b64, unsigned long long lstride,
-                 const unsigned long long* __restrict__ count, Combine cmb, int measure,
-                 double* __restrict__ row) {
+    k_group_pick_batch(const double* __restrict__ b64, unsigned long long lstride,
+                       unsigned long long cap_pad, const BatchSlot* __restrict__ slots,
+                       const unsigned long long* __restrict__ count, int measure,
+                       double* __restrict__ V) {
+  const int d = blockIdx.y;
   const unsigned long long n = *count;
-  const CombineV<double> cv(cmb);
+  const CombineV<double> cv(slots[d].cmb);
+  const double* B = b64 + (size_t)d * cap_pad;
+  double* row = V + (size_t)d * cap_pad;
   for (unsigned long long i = (unsigned long long)blockIdx.x * GRP_NT + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * GRP_NT) {
-    const double lr = b64[i];
+    const double lr = B[i];
     double v[5];
-    combine5<double>(lr, b64[lstride + i], b64[2 * lstride + i], cv, v);
+    combine5<double>(lr, B[lstride + i], B[2 * lstride + i], cv, v);
     row[i] = is_nan(lr) ? lr : pick5(v, measure);
   }
 }
@@ -125,13 +146,29 @@ cudaError_t launch_group_combine(const double* V, unsigned long long ld, unsigne
   return cudaGetLastError();
 }
 
-cudaError_t launch_group_pick(const double* b64, unsigned long long lstride,
-                              const unsigned long long* count, unsigned long long cap,
-                              Combine cmb, int measure, double* row, cudaStream_t s) {
-  long long grid = (long long)((cap + GRP_NT - 1) / GRP_NT);
-  if (grid < 1) grid = 1;
-  if (grid > 1024) grid = 1024;
-  k_group_pick<<<(unsigned)grid, GRP_NT, 0, s>>>(b64, lstride, count, cmb, measure, row);
+cudaError_t launch_group_replicate(const unsigned long long* ids, const unsigned long long* count,
+                                   unsigned long long cap, int D, unsigned long long cap_pad,
+                                   unsigned long long* ids_rep, unsigned long long* counts_rep,
+                                   cudaStream_t s) {
+  if (D < 1 || D > 65535) return cudaErrorInvalidValue;
+  long long bx = (long long)((cap + GRP_NT - 1) / GRP_NT);
+  if (bx < 1) bx = 1;
+  if (bx > 64) bx = 64;
+  k_group_replicate<<<dim3((unsigned)bx, (unsigned)D), GRP_NT, 0, s>>>(ids, count, cap, cap_pad,
+                                                                        ids_rep, counts_rep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_pick_batch(const double* b64, unsigned long long lstride,
+                                    unsigned long long cap_pad, int D, const BatchSlot* slots,
+                                    const unsigned long long* count, unsigned long long cap,
+                                    int measure, double* V, cudaStream_t s) {
+  if (D < 1 || D > 65535) return cudaErrorInvalidValue;
+  long long bx = (long long)((cap + GRP_NT - 1) / GRP_NT);
+  if (bx < 1) bx = 1;
+  if (bx > 64) bx = 64;
+  k_group_pick_batch<<<dim3((unsigned)bx, (unsigned)D), GRP_NT, 0, s>>>(b64, lstride, cap_pad,
+                                                                         slots, count, measure, V);
   return cudaGetLastError();
 }
 

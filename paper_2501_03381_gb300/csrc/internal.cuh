@@ -207,8 +207,8 @@ cudaError_t launch_anneal(const double* const* Rs, const double* const* lss, int
                           unsigned long long* accepted, cudaStream_t s);
 // Group objectives: fold one dataset's status and re-factor count; combine the
 // D x ld value matrix into the objective (per-nplet `out` and/or an FP64
-// basis with stride bstride); one measure of listed nplets from their basis;
-// copy the objective's statistics into every measure slot of the records.
+// basis with stride bstride; count: optional device list length); copy the
+// objective's statistics into every measure slot of the records.
 cudaError_t launch_group_fold(const int* status, const unsigned long long* flag_count,
                               unsigned long long flag_cap, int* gstatus, unsigned long long* gnref,
                               cudaStream_t s);
@@ -216,9 +216,6 @@ cudaError_t launch_group_combine(const double* V, unsigned long long ld, unsigne
                                  const unsigned long long* count, int D, int objective,
                                  double* out, double* basis, unsigned long long bstride,
                                  int num_sms, cudaStream_t s);
-cudaError_t launch_group_pick(const double* b64, unsigned long long lstride,
-                              const unsigned long long* count, unsigned long long cap,
-                              Combine cmb, int measure, double* row, cudaStream_t s);
 cudaError_t launch_group_fix(thoi_order_record* recs, int n, cudaStream_t s);
 // Greedy expansion on the device: parents = the first min(top_count, kappa)
 // entries of `tops` (one side of the previous order's records, order kp);
@@ -302,6 +299,18 @@ cudaError_t launch_reduce_list_batch(const double* b64, unsigned long long lstri
                                      const unsigned long long* flag_ids,
                                      const unsigned long long* flag_counts, int top_m,
                                      PartRec* part, TopEnt* part_top, int bx, cudaStream_t s);
+// Group searches over D datasets sharing one candidate list: replicate the
+// list into D regions of stride cap_pad with per-slot counters (for the
+// batched FP64 kernel), and pick one measure per dataset from the batched
+// basis into the D x cap_pad value matrix.
+cudaError_t launch_group_replicate(const unsigned long long* ids, const unsigned long long* count,
+                                   unsigned long long cap, int D, unsigned long long cap_pad,
+                                   unsigned long long* ids_rep, unsigned long long* counts_rep,
+                                   cudaStream_t s);
+cudaError_t launch_group_pick_batch(const double* b64, unsigned long long lstride,
+                                    unsigned long long cap_pad, int D, const BatchSlot* slots,
+                                    const unsigned long long* count, unsigned long long cap,
+                                    int measure, double* V, cudaStream_t s);
 
 // ------------------------------------------------------------------ device helpers
 #ifdef __CUDACC__

@@ -1836,9 +1836,11 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
   bufs.p[2] = d_ids;
   CK(cudaMalloc(&d_cnt, (size_t)levels * sizeof(unsigned long long)));
   bufs.p[3] = d_cnt;
-  // FP64 basis of the list; for a group also the D x list value matrix and
-  // the objective's basis
-  CK(cudaMalloc(&b64, (3 + (group ? (size_t)D + 3 : 0)) * lstride * sizeof(double)));
+  // FP64 basis of the list (for a group: of every dataset, D regions per
+  // array), then for a group the D x list value matrix and the objective's
+  // basis
+  const size_t nb64 = group ? (size_t)3 * D + D + 3 : 3;
+  CK(cudaMalloc(&b64, nb64 * lstride * sizeof(double)));
   bufs.p[4] = b64;
   CK(cudaMalloc(&table, tsize * sizeof(unsigned long long)));
   bufs.p[5] = table;
@@ -1849,9 +1851,59 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
   auto tops_at = [&](int lv) {
     return (TopEnt*)(d_lv + (size_t)lv * per_level + sizeof(thoi_order_record));
   };
-  double* V = b64 + 3 * lstride;
+  double* V = b64 + (group ? (size_t)3 * D : 3) * lstride;
   double* gb = V + (size_t)D * lstride;
   int launches = 0;
+  // a group evaluates the candidates of every dataset in one batched FP64
+  // launch: dataset descriptors, one slot per (order, dataset) with its own
+  // region of the replicated list and of the basis, and per-slot counters
+  struct GBufs {
+    void* p = nullptr;
+    ~GBufs() {
+      if (p) cudaFree(p);
+    }
+  } gbuf;
+  BatchDataset* d_ds = nullptr;
+  BatchSlot* d_slots = nullptr;
+  unsigned long long* ids_rep = nullptr;
+  unsigned long long* counts_rep = nullptr;
+  if (group) {
+    std::vector<BatchDataset> hds(D);
+    std::vector<BatchSlot> hsl((size_t)levels * D);
+    for (int d = 0; d < D; d++) {
+      hds[d].R32 = ctxs[d]->R32;
+      hds[d].R64 = ctxs[d]->R64;
+      hds[d].ls = ctxs[d]->ls;
+      hds[d].N = N;
+      hds[d].tau_piv = ctxs[d]->opt.pivot_tau;
+      hds[d].tau_tr = ctxs[d]->opt.trace_tau;
+      hds[d].pad = 0;
+      for (int lv = 0; lv < levels; lv++) {
+        BatchSlot& b = hsl[(size_t)lv * D + d];
+        memset(&b, 0, sizeof b);
+        b.d = d;
+        b.k = k0 + lv;
+        b.n = binom_host(N, k0 + lv);
+        b.id_base = 0;
+        b.flag_off = (unsigned long long)d * lstride;
+        b.flag_cap = cap;
+        b.cmb = combine_for(ctxs[d], k0 + lv);
+      }
+    }
+    const size_t bytes = hds.size() * sizeof(BatchDataset) + hsl.size() * sizeof(BatchSlot) +
+                         (size_t)D * lstride * 8 + (size_t)levels * D * 8;
+    CK(cudaMalloc(&gbuf.p, bytes));
+    unsigned char* q = (unsigned char*)gbuf.p;
+    d_ds = (BatchDataset*)q;
+    d_slots = (BatchSlot*)(q + hds.size() * sizeof(BatchDataset));
+    ids_rep = (unsigned long long*)(q + hds.size() * sizeof(BatchDataset) +
+                                    hsl.size() * sizeof(BatchSlot));
+    counts_rep = ids_rep + (size_t)D * lstride;
+    CK(cudaMemcpyAsync(d_ds, hds.data(), hds.size() * sizeof(BatchDataset),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_slots, hsl.data(), hsl.size() * sizeof(BatchSlot),
+                       cudaMemcpyHostToDevice, s));
+  }
   // order k0: exhaustive
   {
     const int32_t ord = k0;
@@ -1884,8 +1936,9 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
     r.r0 = 0;
     r.r1 = binom_host(N, k);
     Combine rc = group_combine();
-    for (int d = 0; d < D; d++) {
-      NpletArgs a = base_args(ctxs[d], r);
+    const double* rb = b64;
+    if (!group) {
+      NpletArgs a = base_args(c, r);
       a.mode = 2;
       a.flag_ids = d_ids;
       a.flag_count = cnt;
@@ -1894,20 +1947,24 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
       CK(launch_nplet_f64s(a, true, b64, lstride, c->num_sms, s, &grid,
                            c->num_sms * MAX_BLOCKS_PER_SM_OUT));
       launches++;
-      if (group) {
-        CK(launch_group_pick(b64, lstride, cnt, cap, a.cmb, measure, V + (size_t)d * lstride, s));
-        launches++;
-      } else {
-        rc = a.cmb;
-      }
-    }
-    const double* rb = b64;
-    if (group) {
+      rc = a.cmb;
+    } else {
+      // every dataset in one launch: the list replicated per slot, the batched
+      // FP64 kernel (grid.y = dataset), one measure per dataset, the objective
+      const BatchSlot* sl = d_slots + (size_t)lv * D;
+      unsigned long long* cr = counts_rep + (size_t)lv * D;
+      const unsigned long long bstride = (unsigned long long)D * lstride;
+      int bx = 2 * c->num_sms / D;
+      if (bx < 1) bx = 1;
+      if (bx > 64) bx = 64;
+      CK(launch_group_replicate(d_ids, cnt, cap, D, lstride, ids_rep, cr, s));
+      CK(launch_refactor_batch(d_ds, sl, 0, D, N, k, N > 32, c->binom, ids_rep, cr, b64, bstride,
+                               gstatus, bx, s));
+      CK(launch_group_pick_batch(b64, bstride, lstride, D, sl, cnt, cap, measure, V, s));
       CK(launch_group_combine(V, lstride, cap, cnt, D, objective, nullptr, gb, lstride,
                               c->num_sms, s));
-      launches++;
+      launches += 4;
       rb = gb;
-      rc = group_combine();
     }
     int grid = 0;
     CK(launch_reduce_list64(rb, lstride, d_ids, cnt, cap, rc, kappa, part, ptop, c->num_sms,
