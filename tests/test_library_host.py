@@ -98,3 +98,19 @@ def test_create_validation_without_gpu(lib):
                            None) == 1
     assert lib.thoi_create(ctypes.byref(h), X.ctypes.data, 10, 3, 3, 7, ctypes.byref(opt),
                            None) == 1
+
+
+def test_group_entry_points_validate_without_gpu(lib):
+    # null or empty groups, too many datasets and null contexts are rejected
+    # before any device work
+    orders = (ctypes.c_int32 * 1)(3)
+    st = P.thoi_stats()
+    null3 = (ctypes.c_void_p * 3)(None, None, None)
+    big = (ctypes.c_void_p * 1025)()
+    for ctxs, D in ((None, 3), (null3, 0), (big, 1025), (null3, 3)):
+        assert lib.thoi_group_measures(ctxs, D, orders, 1, 0, 2**64 - 1, 3, 0, 0, None, 0,
+                                       ctypes.byref(st), None) == 1
+        assert lib.thoi_group_greedy(ctxs, D, 3, 4, 8, 3, 0, 1, None, None, ctypes.byref(st),
+                                     None) == 1
+        assert lib.thoi_group_anneal(ctxs, D, 3, 4, 8, 10, 1.0, 0.9, 3, 0, 1, 0, None, None, None,
+                                     None, ctypes.byref(st), None) == 1
