@@ -41,6 +41,26 @@ def _reduce(S, orders, a, b):
     return pack(oracle.reduce_per_order(S.shape[0], orders, vals, ids, fl, top_m=TOP_M), TOP_M)
 
 
+def _group_case():
+    # four subjects x two conditions, one rank-deficient dataset
+    rng = np.random.default_rng(78)
+    Ss = [workloads.random_corr(rng, 11) for _ in range(8)]
+    Ss[5][9, :] = Ss[5][10, :]
+    Ss[5][:, 9] = Ss[5][:, 10]
+    Ss[5][9, 9] = 1.0
+    return Ss, list(range(3, 12))
+
+
+def _reduce_group(Ss, orders, a, b, objective="cohen_d"):
+    """Records of a group objective over ids [a, b), as the library lays them
+    out: every measure slot carries the objective."""
+    g, bad = oracle.group_measures(Ss, orders, "O", objective, a, b)
+    ids = np.arange(a, b, dtype=np.uint64)
+    recs = oracle.reduce_per_order(Ss[0].shape[0], orders, np.tile(g, (5, 1)), ids, bad,
+                                   top_m=TOP_M)
+    return pack(recs, TOP_M)
+
+
 # ------------------------------------------------------------------ partition
 @pytest.mark.parametrize("N,orders,R", [(13, list(range(2, 14)), 2), (10, [3, 10, 5], 7),
                                         (30, list(range(3, 31)), 8), (64, [32, 1, 2], 5),
@@ -88,6 +108,20 @@ def test_merge_of_ranges_equals_whole(R):
     assert_same(merged, whole, len(orders), TOP_M)
 
 
+@pytest.mark.parametrize("objective,R", [("cohen_d", 3), ("mean", 4)])
+def test_group_records_merge_of_ranges_equals_whole(objective, R):
+    # group objectives shard like the measures: by id ranges, merged once
+    Ss, orders = _group_case()
+    N = Ss[0].shape[0]
+    b = [int(x) for x in P.thoi_partition(N, orders, R)]
+    whole = _reduce_group(Ss, orders, 0, b[-1], objective)
+    blocks = [_reduce_group(Ss, orders, b[r], b[r + 1], objective) for r in range(R)]
+    merged = P.thoi_merge_records(blocks, len(orders), TOP_M)
+    assert_same(merged, whole, len(orders), TOP_M)
+    recs, _, _ = P.parse_records(merged, len(orders), TOP_M)
+    assert sum(int(r["n_not_pd"]) for r in recs) > 0
+
+
 def test_merge_rejects_mismatched_orders():
     S, orders = _case()
     a = _reduce(S, orders[:3], 0, 10)
@@ -115,6 +149,14 @@ def _rank_main(rank, world, port, outdir):
         dist.all_gather_object(got, mine)
         merged = P.thoi_merge_records(got, len(orders), TOP_M)
         np.save(os.path.join(outdir, f"merged{rank}.npy"), merged)
+        # a group objective over eight datasets, sharded the same way
+        Ss, gorders = _group_case()
+        gb = [int(x) for x in P.thoi_partition(Ss[0].shape[0], gorders, world)]
+        gmine = _reduce_group(Ss, gorders, gb[rank], gb[rank + 1])
+        ggot = [None] * world
+        dist.all_gather_object(ggot, gmine)
+        gmerged = P.thoi_merge_records(ggot, len(gorders), TOP_M)
+        np.save(os.path.join(outdir, f"gmerged{rank}.npy"), gmerged)
         dist.barrier()
     finally:
         dist.destroy_process_group()
@@ -126,6 +168,10 @@ def test_two_gloo_ranks_partition_and_merge(tmp_path):
     mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
     S, orders = _case()
     whole = _reduce(S, orders, 0, oracle.count(S.shape[0], orders))
+    Ss, gorders = _group_case()
+    gwhole = _reduce_group(Ss, gorders, 0, oracle.count(Ss[0].shape[0], gorders))
     for r in range(world):
         merged = np.load(tmp_path / f"merged{r}.npy")
         assert_same(merged, whole, len(orders), TOP_M)
+        gmerged = np.load(tmp_path / f"gmerged{r}.npy")
+        assert_same(gmerged, gwhole, len(gorders), TOP_M)
