@@ -46,8 +46,9 @@ def flops_model(k: int) -> float:
 # workload (dram__bytes_read.sum + dram__bytes_write.sum per launch / nplets):
 # the dense, one-level and two-level prefix kernels at order 16 (145,422,675
 # nplets); traffic grows with the nplets written.  None: not captured for the
-# current kernel.
-TRAFFIC_BYTES_PER_NPLET = {"dense": 13.32, "prefix": 69.54, "prefix2": 51.25}
+# current kernel (the paired two-level variant has no capture yet).
+TRAFFIC_BYTES_PER_NPLET = {"dense": 13.32, "prefix": 69.54, "prefix2": 51.25,
+                           "prefix2_pair": None}
 
 
 def grad_flops_model(k: int) -> float:
@@ -85,7 +86,9 @@ def prefix2_order_flops(N: int, k: int) -> float:
 
 
 def order_flops(N: int, k: int, prefix: int) -> float:
-    if prefix == 2:
+    # prefix 3 is the two-level kernel with the last variables two at a time:
+    # the same algorithmic work as prefix 2
+    if prefix in (2, 3):
         return prefix2_order_flops(N, k)
     return prefix_order_flops(N, k) if prefix else math.comb(N, k) * flops_model(k)
 
@@ -377,7 +380,8 @@ def run_ours(args, rank, world, local_rank):
     f_dense = total_flops()
     traffic = 0.0
     for k in ORDERS:
-        b = TRAFFIC_BYTES_PER_NPLET[("dense", "prefix", "prefix2")[int(shapes.get(k, [1, 8, 0])[2])]]
+        b = TRAFFIC_BYTES_PER_NPLET[("dense", "prefix", "prefix2", "prefix2_pair")[
+            int(shapes.get(k, [1, 8, 0])[2])]]
         traffic = None if (traffic is None or b is None) else traffic + b * math.comb(N_VARS, k)
     kern_s = sum(nplet_ms) / len(nplet_ms) / 1e3
     achieved = f_total / kern_s / 1e12

@@ -94,7 +94,8 @@ struct Shape {
   int chunk;          // nplets (prefixes for the prefix-shared kernel) per thread per round, 1..8
   int lanes;          // lanes per nplet: 1 (one-thread kernel), 2 or 4 (lane-group kernel)
   int prefix;         // prefix-shared kernels (whole orders, KPFX_MIN <= k <= KPFX_MAX):
-                      // 1 shares a (k-1)-prefix, 2 a (k-2)-prefix; 0 dense
+                      // 1 shares a (k-1)-prefix, 2 a (k-2)-prefix, 3 a (k-2)-prefix with
+                      // the last variables two at a time; 0 dense
 };
 constexpr int KPFX_MIN = 3;   // orders with a prefix-shared kernel
 constexpr int KPFX_MAX = 20;

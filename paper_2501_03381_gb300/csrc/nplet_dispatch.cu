@@ -53,7 +53,7 @@ cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, c
     switch (a.k) {
 #define CASE_P(KK)                                                                  \
   case KK:                                                                          \
-    return sh.prefix == 2 ? launch_pfx2_k<KK>(a, sh, num_sms, s, grid_out, max_blocks) \
+    return sh.prefix >= 2 ? launch_pfx2_k<KK>(a, sh, num_sms, s, grid_out, max_blocks) \
                           : launch_pfx_k<KK>(a, sh, num_sms, s, grid_out, max_blocks);
       CASE_P(3) CASE_P(4) CASE_P(5) CASE_P(6) CASE_P(7) CASE_P(8) CASE_P(9) CASE_P(10)
       CASE_P(11) CASE_P(12) CASE_P(13) CASE_P(14) CASE_P(15) CASE_P(16) CASE_P(17) CASE_P(18)

@@ -21,7 +21,7 @@ struct Pfx2Blocks {
   static constexpr int value = K <= 14 ? 3 : 1;
 };
 
-template <int K, typename M>
+template <int K, typename M, bool PAIR>
 __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(const NpletArgs a,
                                                                             const int chunk) {
   constexpr int P = K - 1;   // variables before the last one
@@ -146,8 +146,10 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
         level(GP, am);
         const unsigned long long r0 =
             rbase - binom_s(sb, bs, N - 1 - am, 2) - (unsigned long long)(N - 2 - am);
-        // ---- last variables: one final bordered step each
-        for (int cl = am + 1; cl < N; cl++) {
+        // ---- last variables: one final bordered step each (two at a time
+        // when PAIR: the two steps are independent, so their dependency
+        // chains interleave)
+        auto last = [&](const int cl, float& lr, float& sp, float& lsum, bool& bad) {
           const float* rowc = sR + cl * ldr;
           float x[P];
 #pragma unroll
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
             for (int t = P - 1; t > r; t--) s = fmaf(-Lh[t][r], x[t], s);
             x[r] = s;
           }
-          bool bad = badp;
+          bad = badp;
           float Pl = P1 * Dn;
           int El = E1;
           renorm(Pl, El, bad);
@@ -187,9 +189,13 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
             P2 *= pr;
             if (((P - 1 - r) & 3) == 3 || r == 0) renorm(P2, E2, bad);
           }
-          const float lr = log_of(Pl, El), sp = log_of(P2, E2);
-          const float lsum = lsp + sls[cl];
+          lr = log_of(Pl, El);
+          sp = log_of(P2, E2);
+          lsum = lsp + sls[cl];
           bad |= !(fminf(pmin, Dn) >= tau_piv) | !(trace <= tau_tr);
+        };
+        auto emit = [&](const int cl, const float lr, const float sp, const float lsum,
+                        const bool bad) {
           const unsigned long long gid = a.id_base + r0 + (unsigned long long)(cl - am - 1);
           if (basis) {
             store_basis(a, gid, lr, sp, lsum, bad);
@@ -199,6 +205,25 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
             store5<float>(a, gid, v);
           }
           flag_append(a, bad, gid);
+        };
+        if constexpr (PAIR) {
+          for (int cl = am + 1; cl < N; cl += 2) {
+            // an odd count repeats the last variable and drops the copy
+            const int cl2 = cl + 1 < N ? cl + 1 : cl;
+            float lr1, sp1, ls1, lr2, sp2, ls2;
+            bool b1, b2;
+            last(cl, lr1, sp1, ls1, b1);
+            last(cl2, lr2, sp2, ls2, b2);
+            emit(cl, lr1, sp1, ls1, b1);
+            if (cl2 != cl) emit(cl2, lr2, sp2, ls2, b2);
+          }
+        } else {
+          for (int cl = am + 1; cl < N; cl++) {
+            float lr, sp, lsum;
+            bool bad;
+            last(cl, lr, sp, lsum, bad);
+            emit(cl, lr, sp, lsum, bad);
+          }
         }
       }
       if (jn + 1 < cnt) {
@@ -217,11 +242,11 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
   }
 }
 
-template <int K, typename M>
+template <int K, typename M, bool PAIR>
 static cudaError_t launch_pfx2_t(const NpletArgs& a, const Shape& sh, int num_sms,
                                  cudaStream_t s, int* grid_out, int max_blocks) {
   const SmemLayout L = smem_layout(a.N, K, row_stride(a.N), sizeof(float), sizeof(unsigned), 0);
-  void (*fn)(const NpletArgs, const int) = k_nplet_pfx2<K, M>;
+  void (*fn)(const NpletArgs, const int) = k_nplet_pfx2<K, M, PAIR>;
   int occ = 0;
   cudaError_t e = occupancy_cached((const void*)fn, RED_NT, L.total, &occ);
   if (e != cudaSuccess) return e;
@@ -242,11 +267,16 @@ static cudaError_t launch_pfx2_t(const NpletArgs& a, const Shape& sh, int num_sm
   return cudaGetLastError();
 }
 
+// sh.prefix == 3: the last variables two at a time
 template <int K>
 cudaError_t launch_pfx2_k(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                           int* grid_out, int max_blocks) {
-  if (a.N <= 32) return launch_pfx2_t<K, unsigned>(a, sh, num_sms, s, grid_out, max_blocks);
-  return launch_pfx2_t<K, unsigned long long>(a, sh, num_sms, s, grid_out, max_blocks);
+  if (sh.prefix == 3) {
+    if (a.N <= 32) return launch_pfx2_t<K, unsigned, true>(a, sh, num_sms, s, grid_out, max_blocks);
+    return launch_pfx2_t<K, unsigned long long, true>(a, sh, num_sms, s, grid_out, max_blocks);
+  }
+  if (a.N <= 32) return launch_pfx2_t<K, unsigned, false>(a, sh, num_sms, s, grid_out, max_blocks);
+  return launch_pfx2_t<K, unsigned long long, false>(a, sh, num_sms, s, grid_out, max_blocks);
 }
 
 }  // namespace thoi

@@ -2162,7 +2162,7 @@ static void tune_load(const char* path, const char* gpu, int sms) {
     sh.lanes = lanes;
     sh.chunk = chunk;
     sh.blocks_per_sm = bps;
-    sh.prefix = (prefix >= 0 && prefix <= 2) ? prefix : 0;
+    sh.prefix = (prefix >= 0 && prefix <= 3) ? prefix : 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(gpu, sms, k, wide)] = sh;
     g_tune_gen++;
@@ -2263,13 +2263,14 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
     // when that is affordable (up to 2^28 nplets)
     if (pfx_candidate) {
       // (k-1)-prefix kernel with 1, 2, 4 prefixes per thread per round, then
-      // the (k-2)-prefix kernel with 1, 2
-      for (int v = 0; v < 5; v++) {
+      // the (k-2)-prefix kernel with 1, 2, then that kernel with the last
+      // variables two at a time, with 1, 2
+      for (int v = 0; v < 7; v++) {
         Shape sh;
         sh.lanes = 1;
-        sh.chunk = v < 3 ? 1 << v : 1 << (v - 3);
+        sh.chunk = v < 3 ? 1 << v : 1 << ((v - 3) & 1);
         sh.blocks_per_sm = 0;
-        sh.prefix = v < 3 ? 1 : 2;
+        sh.prefix = v < 3 ? 1 : (v < 5 ? 2 : 3);
         const double ms = time_shape(c, k, total, sh, s);
         if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
           best_ms = ms;

@@ -484,11 +484,12 @@ def test_virtual_ranks_partition_and_merge():
 
 
 # ------------------------------------------------------------------ prefix-shared kernel
-@pytest.mark.parametrize("variant,chunk", [(1, 1), (1, 3), (2, 1), (2, 3)])
+@pytest.mark.parametrize("variant,chunk", [(1, 1), (1, 3), (2, 1), (2, 3), (3, 1), (3, 2)])
 def test_prefix_kernel_every_order_matches_oracle(variant, chunk, tmp_path):
     # the prefix-shared kernels (bordered steps over a shared (k-1)-prefix,
-    # variant 1, or (k-2)-prefix, variant 2) on every order of the
-    # fMRI-shaped workload, every nplet against the oracle
+    # variant 1, or (k-2)-prefix, variant 2, the latter with the last variables
+    # two at a time, variant 3) on every order of the fMRI-shaped workload
+    # (odd and even numbers of last variables), every nplet against the oracle
     X, orders = workloads.fmri_like()
     S = oracle.copula_cov(X)
     with _ctx(X, out_f64=True) as c:
@@ -506,7 +507,7 @@ def test_prefix_kernel_wide_masks_and_records(tmp_path):
     orders = [3, 4]
     with _ctx(Sigma=S, out_f64=True, top_m=16) as c:
         for k in orders:
-            _force_shape(c.h, k, 1, 1, 2, str(tmp_path / f"w{k}.json"), prefix=k - 2)
+            _force_shape(c.h, k, 1, 1, 2, str(tmp_path / f"w{k}.json"), prefix=k - 1)
         for k in orders:
             ref, _ = _refs(S, [k])
             got, _ = c.measures([k])
