@@ -8,6 +8,12 @@
 // Thread order: the (k-2)-prefixes are grouped by their largest index g;
 // every prefix of a group runs the same nested loops (a over g+1 .. N-2, b
 // over a+1 .. N-1), so the lanes of a warp stay together.
+//
+// PAIR: the final steps of two last indices b, b+1 run in one iteration.
+// They share nothing but the factored (k-1)-prefix, so their dependency
+// chains (forward solve, pivot, backward solve, products) interleave; with a
+// thread's few warps per scheduler that is the latency the single step
+// leaves exposed.
 #pragma once
 #include "nplet_common.cuh"
 
