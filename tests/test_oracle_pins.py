@@ -650,3 +650,30 @@ def test_group_anneal_of_copies_matches_single():
     assert one[0] == grp[0] and one[2] == grp[2]
     np.testing.assert_allclose(grp[1], one[1], rtol=1e-14)
     np.testing.assert_allclose(grp[3], one[3], rtol=1e-14)
+
+
+def test_greedy_on_concatenated_r_and_s_systems():
+    # the paper's redundant (R) and synergistic (S) systems side by side
+    # (independent blocks): the largest O of each order lies in the R block
+    # and the smallest in the S block with its common child; both values
+    # have closed forms (the block measures of test_r_and_s_systems)
+    import scipy.linalg
+    n, c = 5, 1.0
+    R, S = _rsys(n, c), _ssys(n, c)
+    M = scipy.linalg.block_diag(R, S)
+    r_ld = lambda idx: 0.0 if n in idx else math.log(1 + len(idx) * c * c)
+    r_var = lambda i: 1.0 if i == n else c * c + 1
+    s_ld = lambda idx: math.log(1 + (n - (len(idx) - 1)) * c * c) if n in idx else 0.0
+    s_var = lambda i: n * c * c + 1 if i == n else 1.0
+    hi = oracle.greedy(M, 3, n + 1, 4, "O", True)
+    lo = oracle.greedy(M, 3, n + 1, 4, "O", False)
+    for lvl, k in enumerate(range(3, n + 2)):
+        blk = [list(t) for t in itertools.combinations(range(n + 1), k)]
+        best_r = max(_closed_measures(r_ld, r_var, idx)[2] for idx in blk)
+        best_s = min(_closed_measures(s_ld, s_var, idx)[2] for idx in blk)
+        sets, vals = hi[lvl]
+        assert max(sets[0]) <= n
+        np.testing.assert_allclose(vals[0], best_r, rtol=0, atol=1e-12)
+        sets, vals = lo[lvl]
+        assert min(sets[0]) > n and 2 * n + 1 in sets[0]
+        np.testing.assert_allclose(vals[0], best_s, rtol=0, atol=1e-12)
