@@ -345,7 +345,8 @@ thoi_status thoi_anneal(thoi_ctx* ctx, int32_t k_lo, int32_t k_hi, int32_t n_cha
  * all coincide (sd = 0), has no value: NaN per nplet, and in the records it is
  * left out and counted in n_not_pd.
  *  ctxs    : D contexts (1 <= D <= THOI_MAX_GROUP, 4 <= D even for Cohen's d)
- *            with the same N; a context may appear more than once.  Each
+ *            with the same N, all on the current device; a context may appear
+ *            more than once.  Each
  *            dataset is evaluated by its own path (precision, thresholds,
  *            bias correction of its context); ctxs[0] holds the workspace
  *            and gives top_m.
