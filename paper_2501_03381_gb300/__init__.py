@@ -586,6 +586,23 @@ class Context:
         return thoi_measures_grad(self.h, orders, measure, out, stream)
 
 
+def measures(X, orders, reduction: str = "none", stream=None, **options):
+    """One call over a T x N sample matrix (a tensor on the device, or a host
+    array): a context is created, evaluated and freed.  Returns what
+    Context.measures returns: (SoA tensor, stats) for reduction "none",
+    ((records, top_hi, top_lo), stats) for "per_order"."""
+    with Context(X, stream=stream, **options) as c:
+        return c.measures(orders, reduction=reduction, stream=stream)
+
+
+def measure_sum(Sigma, orders, measure: str = "O", T_for_bias: int = 0):
+    """L = sum over every nplet of the listed orders of one measure, as a
+    differentiable function of the covariance Sigma (MeasureSum)."""
+    if MeasureSum is None:
+        raise RuntimeError("measure_sum needs torch")
+    return MeasureSum.apply(Sigma, orders, measure, T_for_bias)
+
+
 def _measure_total(recs, measure: str) -> float:
     m = MEASURES.index(measure)
     return float(sum(float(r["mean"][m]) * (int(r["count"]) - int(r["n_not_pd"])) for r in recs))

@@ -519,3 +519,31 @@ def test_prefix_kernel_wide_masks_and_records(tmp_path):
         n3 = math.comb(40, 3)
         _check_records(recs, hi, lo, ref_recs, TOL32, S, orders, 16,
                        o_ref=[vals[3, :n3], vals[3, n3:]])
+
+
+# ------------------------------------------------------------------ one-call API
+def test_module_level_measures_and_measure_sum():
+    # P.measures: create, evaluate, free in one call (device tensor or host
+    # array); P.measure_sum: the autograd function
+    X, orders = workloads.small()
+    S = oracle.copula_cov(X)
+    ref, _ = _refs(S, orders)
+    out, st = P.measures(torch.as_tensor(X, device="cuda"), orders, out_f64=True)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL32)
+    (recs, hi, lo), _ = P.measures(X, orders, reduction="per_order", top_m=8)
+    assert int(recs["count"].sum()) == ref.shape[1]
+    np.testing.assert_allclose(recs["min"][:, 3], [ref[3, o].min() for o in _order_slices(orders)],
+                               rtol=0, atol=TOL32)
+    rng = np.random.default_rng(81)
+    A = rng.standard_normal((7, 7))
+    Sg = A @ A.T + np.eye(7)
+    St = torch.tensor(Sg, device="cuda", requires_grad=True)
+    L = P.measure_sum(St, [3, 4], "S")
+    L.backward()
+    G = oracle.grad(Sg, [3, 4], "S")
+    np.testing.assert_allclose(St.grad.cpu().numpy(), G, rtol=2e-4, atol=2e-4 * np.abs(G).max())
+
+
+def _order_slices(orders, N=10):
+    offs = np.cumsum([0] + [math.comb(N, k) for k in orders])
+    return [slice(int(offs[i]), int(offs[i + 1])) for i in range(len(orders))]
