@@ -114,3 +114,21 @@ def test_group_entry_points_validate_without_gpu(lib):
                                      None) == 1
         assert lib.thoi_group_anneal(ctxs, D, 3, 4, 8, 10, 1.0, 0.9, 3, 0, 1, 0, None, None, None,
                                      None, ctypes.byref(st), None) == 1
+
+
+def test_search_and_measure_entry_points_validate_without_gpu(lib):
+    # a null context is rejected before any device work by every entry point
+    st = P.thoi_stats()
+    orders = (ctypes.c_int32 * 1)(3)
+    masks = np.zeros(8, dtype=np.uint64)
+    vals = np.zeros(8)
+    assert lib.thoi_greedy(None, 3, 4, 4, 3, 1, masks.ctypes.data, vals.ctypes.data,
+                           ctypes.byref(st), None) == 1
+    assert lib.thoi_anneal(None, 3, 4, 4, 10, 1.0, 0.9, 3, 1, 0, masks.ctypes.data,
+                           vals.ctypes.data, masks.ctypes.data, vals.ctypes.data,
+                           ctypes.byref(st), None) == 1
+    assert lib.thoi_measures(None, orders, 1, 0, 2**64 - 1, 0, None, 0, ctypes.byref(st),
+                             None) == 1
+    assert lib.thoi_measures_grad(None, orders, 1, 3, None, ctypes.byref(st), None) == 1
+    assert lib.thoi_set_cancel(None, 1) == 1
+    assert lib.thoi_n(None) == 0
