@@ -689,6 +689,49 @@ def run_extra(args, dev, stream, flush, peak, rank):
              "value": n_eval / (sms / 1e3), "unit": "evaluations/s", "ms_per_call": sms,
              "best_d": float(np.nanmax(bv)), "accepted": int(sst.n_refactored)}
     out["group_anneal_paired55"] = entry
+
+    # per-nplet output (FP32 SoA, 20 B per nplet) at small orders, where the
+    # stores outweigh the arithmetic (F(k) / 20 B is below the FP32 : HBM
+    # balance of about 12 FLOP/B for k <= 5): N = 64, orders 3..5, the nplet
+    # kernels' CUDA-event time against the measured HBM bandwidth
+    try:
+        Nv, orders_o = 64, [3, 4, 5]
+        rng = np.random.default_rng(7)
+        Xo = rng.standard_normal((2000, Nv)) @ np.linalg.cholesky(
+            workloads.random_corr(rng, Nv)).T
+        n = total_nplets(Nv, orders_o)
+        out_t = torch.empty((5, n), dtype=torch.float32, device=dev)
+        with P.Context(torch.as_tensor(Xo, device=dev), profile=True) as c:
+            for _ in range(3):
+                c.measures(orders_o, out=out_t)
+            kms = []
+            for _ in range(steps):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                _, st = c.measures(orders_o, out=out_t)
+                kms.append(st.nplet_ms)
+        kms_avg = sum(kms) / len(kms)
+        hbm = 6800.0
+        basis = "fallback 6.8 TB/s"
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                hbm = float(json.load(fh)["hbm_gbs"])
+            basis = "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+        except Exception:
+            pass
+        byts = 20.0 * n
+        ach = byts / (kms_avg / 1e3) / 1e9
+        entry = {"workload": f"N=64, T=2000 random-correlation Gaussian (seed 7), per-nplet FP32 "
+                             f"output of orders 3..5 ({n:,} nplets, {byts / 1e6:.0f} MB)",
+                 "value": n / (kms_avg / 1e3), "unit": "nplets/s",
+                 "nplet_kernel_ms": kms_avg,
+                 "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                              "frac": ach / hbm, "bytes_per_call": byts,
+                              "peak_basis": basis,
+                              "bytes_model": "20 B written per nplet (five FP32 measures)"}}
+    except Exception as e:  # an extra line never takes the headline down
+        entry = {"error": f"{type(e).__name__}: {e}"}
+    out["per_nplet_output_n64"] = entry
     return out
 
 
