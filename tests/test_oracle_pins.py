@@ -257,6 +257,34 @@ def test_padding_identity():
     assert abs(h_pad - (h + 3 * LOG2PIE_HALF)) < 1e-12
 
 
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                key, val = line.split()
+                vals[key] = float(val)
+    return vals
+
+
+def test_padding_constant_as_printed():
+    # the printed 1.4189 (four decimals) against the oracle's entropy of one
+    # unit-variance normal, and the padding identity with the printed value
+    # within its rounding
+    h1 = _golden("padding_entropy.txt")["h_unit_normal"]
+    assert round(oracle.entropy(np.eye(1), [0]), 4) == h1
+    rng = np.random.default_rng(8)
+    A = rand_spd(rng, 3)
+    for n_pad in (1, 4, 9):
+        P = np.eye(3 + n_pad)
+        P[:3, :3] = A
+        err = oracle.entropy(P, range(3 + n_pad)) - (oracle.entropy(A, range(3)) + n_pad * h1)
+        assert abs(err) <= n_pad * 5e-5
+
+
 def test_not_pd_marked():
     S = np.eye(5)
     S[0, 1] = S[1, 0] = 1.0  # duplicated variable: singular
