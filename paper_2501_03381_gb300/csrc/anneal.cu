@@ -1,8 +1,9 @@
 // Simulated annealing over nplets (Methods, "Heuristics", "Simulated
-// Annealing Algorithm").  Every chain is one thread that runs the whole
-// schedule on the device: propose a neighbour of its current set, evaluate
-// its energy in FP64, accept by the Metropolis rule, cool.  Chains are
-// independent, so the kernel needs no communication and no host round trip.
+// Annealing Algorithm").  Every chain runs the whole schedule on the device
+// (a thread, or a warp, per chain; see below): propose a neighbour of its
+// current set, evaluate its energy in FP64, accept by the Metropolis rule,
+// cool.  Chains are independent, so the kernels need no communication
+// between chains and no host round trip.
 //
 // Random numbers: draw (chain, iteration, slot) is output number
 // c = (chain * (iters + 1) + iteration) * 64 + slot of the SplitMix64
