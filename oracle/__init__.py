@@ -355,15 +355,19 @@ def splitmix64(seed: int, c: int) -> int:
 
 def anneal(Sigma, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float,
            alpha: float, measure: str = "O", maximize: bool = True, seed: int = 0,
-           objective: str | None = None):
+           objective: str | None = None, patience: int = 0):
     """Simulated annealing (Methods, "Heuristics", "Simulated Annealing
     Algorithm"), chain by chain, with the moves, draws and acceptance rule
     stated for thoi_anneal: draw (chain, step, slot) is SplitMix64 output
     ((chain * (iters+1) + step) * 64 + slot); integers (z * n) >> 64; uniforms
     (z >> 11) * 2^-53; accept when the energy rises, else with probability
-    exp(dE / Temp).  With a list of covariances and a group objective the
-    energy is that objective over the datasets.  Returns (final sets, final
-    values, best sets, best values) with sets as sorted tuples."""
+    exp(dE / Temp); Temp = T0 at step 1 and is multiplied by alpha after
+    every step.  Termination ("Termination Criteria"): after `iters` steps,
+    or, when patience > 0, after the first step t with t - t_best >= patience,
+    t_best being the last step that raised the best energy (0 at the start).
+    With a list of covariances and a group objective the energy is that
+    objective over the datasets.  Returns (final sets, final values, best
+    sets, best values) with sets as sorted tuples."""
     _, by_ids, N = _evaluator(Sigma, measure, objective)
     sgn = 1.0 if maximize else -1.0
 
@@ -388,6 +392,7 @@ def anneal(Sigma, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float,
         E = sgn * value(cur)
         best, bestE = cur, E
         T = T0
+        t_best = 0
         for it in range(1, iters + 1):
             members = list(cur)
             size = len(members)
@@ -417,7 +422,10 @@ def anneal(Sigma, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float,
                     cur, E = prop, En
                     if E > bestE:
                         best, bestE = cur, E
+                        t_best = it
             T *= alpha
+            if patience > 0 and it - t_best >= patience:
+                break
         out[0].append(cur)
         out[1].append(sgn * E)
         out[2].append(best)

@@ -558,6 +558,108 @@ def test_anneal_start_and_ranges():
                                                                    False, seed=1)[1]))
 
 
+# Three-state system for the acceptance and cooling pins: N = 3 variables and
+# sets of exactly two (k_lo = k_hi = 2), so the states are the three pairs.
+# The energy is TC, which for a pair is the mutual information
+# -1/2 log(1 - rho^2).  A swap replaces one of the two members (probability
+# 1/2 each) by the one variable left out, so the proposal is symmetric, and
+# the law of a chain after n steps follows from the 3 x 3 Metropolis
+# transition matrices alone: a move is taken when the energy does not fall,
+# else with probability exp(dE / Temp), Temp = T0 alpha^(t-1) at step t.
+RHO3 = {(0, 1): 0.8, (0, 2): 0.5, (1, 2): 0.3}
+STATES3 = [(0, 1), (0, 2), (1, 2)]
+
+
+def _sigma3():
+    S = np.eye(3)
+    for (a, b), r in RHO3.items():
+        S[a, b] = S[b, a] = r
+    return S
+
+
+def _energies3():
+    return np.array([-0.5 * math.log(1.0 - RHO3[s] ** 2) for s in STATES3])
+
+
+def _law3(temps, accept=lambda dE, T: 1.0 if dE >= 0 else math.exp(dE / T)):
+    E = _energies3()
+    p = np.full(3, 1.0 / 3.0)  # the start: a uniformly drawn pair
+    for T in temps:
+        M = np.zeros((3, 3))
+        for a in range(3):
+            for b in range(3):
+                if a != b:
+                    M[a, b] = 0.5 * accept(E[b] - E[a], T)
+            M[a, a] = 1.0 - M[a].sum()
+        p = p @ M
+    return p
+
+
+def _final_freq3(chains, iters, T0, alpha, seed):
+    fin, _, _, _ = oracle.anneal(_sigma3(), 2, 2, chains, iters, T0, alpha, "TC", True, seed=seed)
+    return np.array([sum(1 for s in fin if s == st) for st in STATES3]) / chains
+
+
+def _band_dev(freq, p, n):
+    # largest deviation in standard errors of a multinomial proportion
+    return float(np.max(np.abs(freq - p) / np.sqrt(p * (1.0 - p) / n)))
+
+
+def test_anneal_constant_temperature_reaches_boltzmann_law():
+    # alpha = 1: the chain's law tends to exp(E / Temp) / Z (detailed balance
+    # of the Metropolis rule with a symmetric proposal); after 30 steps the
+    # exact law is that one to rounding, and the oracle's chains follow it
+    T, iters, chains = 0.2, 30, 3000
+    E = _energies3()
+    boltz = np.exp(E / T) / np.exp(E / T).sum()
+    law = _law3([T] * iters)
+    np.testing.assert_allclose(law, boltz, rtol=0, atol=1e-9)
+    freq = _final_freq3(chains, iters, T, 1.0, seed=2025)
+    assert _band_dev(freq, law, chains) < 4.5
+    # the acceptance as printed, exp(-dE / Temp) >= 1, takes every move: the
+    # law would be uniform, far outside the band
+    printed = _law3([T] * iters, accept=lambda dE, T: min(1.0, math.exp(-dE / T)))
+    assert _band_dev(printed, law, chains) > 9.0
+
+
+def test_anneal_cooling_schedule():
+    # alpha < 1: step t runs at T0 alpha^(t-1).  Cooling before the first
+    # step, or not cooling, gives laws many standard errors away.
+    T0, alpha, iters, chains = 0.5, 0.4, 3, 4000
+    law = _law3([T0 * alpha ** t for t in range(iters)])
+    freq = _final_freq3(chains, iters, T0, alpha, seed=77)
+    assert _band_dev(freq, law, chains) < 4.5
+    early = _law3([T0 * alpha ** (t + 1) for t in range(iters)])
+    flat = _law3([T0] * iters)
+    assert _band_dev(early, law, chains) > 9.0 and _band_dev(flat, law, chains) > 9.0
+
+
+def test_anneal_patience_stops_after_no_improvement():
+    # Termination Criteria: with patience p the chain stops after the first
+    # step t at which the best energy has not risen for p steps.  Chain 0's
+    # draws do not depend on the step count, so its best value after t steps
+    # comes from fixed-length runs; the stopping step follows, and the early
+    # stopped run must equal the fixed run of that length.
+    S = workloads.random_corr(np.random.default_rng(53), 8)
+    iters, p, stopped = 40, 4, 0
+    for seed in range(8):
+        runs = [oracle.anneal(S, 3, 5, 1, t, 0.05, 0.97, "O", True, seed=seed)
+                for t in range(iters + 1)]
+        best = [r[3][0] for r in runs]
+        t_best, stop = 0, iters
+        for t in range(1, iters + 1):
+            if best[t] > best[t - 1]:
+                t_best = t
+            if t - t_best >= p:
+                stop = t
+                break
+        stopped += stop < iters
+        got = oracle.anneal(S, 3, 5, 1, iters, 0.05, 0.97, "O", True, seed=seed, patience=p)
+        assert got[0] == runs[stop][0] and got[2] == runs[stop][2]
+        assert got[1] == runs[stop][1] and got[3] == runs[stop][3]
+    assert stopped >= 4
+
+
 # ------------------------------------------------------------------ group objectives (Results,
 # "Leveraging Gaussian entropy estimators with batch processing"; Methods, "fMRI analysis")
 def _equicorr(N, rho):
