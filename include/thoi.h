@@ -280,8 +280,10 @@ thoi_status thoi_set_cancel(thoi_ctx* ctx, int32_t flag);
  * (1 MiB per device, held from library load until process exit) is one
  * static device array shared by all calls: calls whose work overlaps on the
  * GPU (different streams, or different host threads) race on it and must be
- * serialised by the caller.  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  Returns
+ * serialised by the caller.  The call cannot be used while `stream` is being
+ * captured into a graph: it queries pointer attributes, copies the status word
+ * to host memory and synchronises `stream`.  Sigma, rec_out and top_out must
+ * be memory of the current device (THOI_ERR_INVALID_ARG otherwise).  Returns
  * THOI_ERR_TOO_LARGE for N > 64, top_m > 16 or C(N, k) >= 2^32; synchronises
  * `stream`; THOI_ERR_NOT_PD when a nplet is not positive definite. */
 thoi_status thoi_order_record_noalloc(const double* Sigma, int64_t N, int32_t k, int32_t top_m,
@@ -307,7 +309,11 @@ thoi_status thoi_greedy(thoi_ctx* ctx, int32_t k0, int32_t k1, int32_t kappa, in
 
 /* Simulated annealing (Methods, "Heuristics", "Simulated Annealing
  * Algorithm").  n_chains independent chains, each a set of k_lo..k_hi
- * variables (k_hi <= 32), run `iters` steps on the device:
+ * variables (k_hi <= 32), run on the device until one of the paper's two
+ * termination criteria holds: `iters` steps done, or (patience > 0) no rise
+ * of the chain's best energy over the last `patience` steps (the chain stops
+ * after the first step t with t - t_best >= patience, t_best the last step
+ * that raised the best energy, 0 at the start; patience = 0: off):
  *  - start: a random set (size uniform in k_lo..k_hi, members by a partial
  *    Fisher-Yates shuffle);
  *  - move: within one order (k_lo == k_hi) swap a member for a non-member;
@@ -318,7 +324,8 @@ thoi_status thoi_greedy(thoi_ctx* ctx, int32_t k0, int32_t k1, int32_t kappa, in
  *  - acceptance: always if E rises, else with probability exp(dE / Temp)
  *    (the usual Metropolis rule; the paper's printed exp(-dE / Temp) would
  *    accept every worse move);
- *  - cooling: Temp = T0 * alpha^step.
+ *  - cooling: Temp = T0 at step 1, multiplied by alpha after every step
+ *    (step t runs at T0 * alpha^(t-1)).
  * Random numbers: draw (chain, step, slot) is the
  * ((chain * (iters+1) + step) * 64 + slot)-th output of SplitMix64 seeded with
  * `seed` (integers in [0, n): (z * n) >> 64; uniforms: (z >> 11) * 2^-53), so a
@@ -327,7 +334,8 @@ thoi_status thoi_greedy(thoi_ctx* ctx, int32_t k0, int32_t k1, int32_t kappa, in
  * bit masks and their measure values.  stats->nplets = energies evaluated,
  * stats->n_refactored = accepted moves.  Synchronises `stream`. */
 thoi_status thoi_anneal(thoi_ctx* ctx, int32_t k_lo, int32_t k_hi, int32_t n_chains, int32_t iters,
-                        double T0, double alpha, int32_t measure, int32_t maximize, uint64_t seed,
+                        double T0, double alpha, int32_t patience, int32_t measure,
+                        int32_t maximize, uint64_t seed,
                         uint64_t* final_masks, double* final_values, uint64_t* best_masks,
                         double* best_values, thoi_stats* stats, void* stream);
 
@@ -388,7 +396,8 @@ thoi_status thoi_group_greedy(thoi_ctx* const* ctxs, int32_t D, int32_t k0, int3
  * thoi_anneal. */
 thoi_status thoi_group_anneal(thoi_ctx* const* ctxs, int32_t D, int32_t k_lo, int32_t k_hi,
                               int32_t n_chains, int32_t iters, double T0, double alpha,
-                              int32_t measure, int32_t objective, int32_t maximize,
+                              int32_t patience, int32_t measure, int32_t objective,
+                              int32_t maximize,
                               uint64_t seed, uint64_t* final_masks, double* final_values,
                               uint64_t* best_masks, double* best_values, thoi_stats* stats,
                               void* stream);

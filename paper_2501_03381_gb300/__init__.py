@@ -113,7 +113,7 @@ def load(build_if_missing: bool = True):
                                            ctypes.POINTER(thoi_stats), vp]),
             "thoi_merge_records": (ctypes.c_int, [vp, i32, i32, i32, vp]),
             "thoi_anneal": (ctypes.c_int, [vp, i32, i32, i32, i32, ctypes.c_double,
-                                           ctypes.c_double, i32, i32, u64, vp, vp, vp, vp,
+                                           ctypes.c_double, i32, i32, i32, u64, vp, vp, vp, vp,
                                            ctypes.POINTER(thoi_stats), vp]),
             "thoi_group_measures": (ctypes.c_int, [vp, i32, vp, i32, u64, u64, i32, i32, i32,
                                                    vp, ctypes.c_size_t,
@@ -121,8 +121,8 @@ def load(build_if_missing: bool = True):
             "thoi_group_greedy": (ctypes.c_int, [vp, i32, i32, i32, i32, i32, i32, i32, vp, vp,
                                                  ctypes.POINTER(thoi_stats), vp]),
             "thoi_group_anneal": (ctypes.c_int, [vp, i32, i32, i32, i32, i32, ctypes.c_double,
-                                                 ctypes.c_double, i32, i32, i32, u64, vp, vp,
-                                                 vp, vp, ctypes.POINTER(thoi_stats), vp]),
+                                                 ctypes.c_double, i32, i32, i32, i32, u64, vp,
+                                                 vp, vp, vp, ctypes.POINTER(thoi_stats), vp]),
             "thoi_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -406,16 +406,19 @@ def thoi_greedy(h, k0: int, k1: int, kappa: int, measure: str = "O", maximize: b
 
 
 def thoi_anneal(h, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float, alpha: float,
-                measure: str = "O", maximize: bool = True, seed: int = 0, stream=None):
-    """Simulated annealing chains on the device.  Returns (final_masks,
-    final_values, best_masks, best_values, stats), n_chains entries each."""
+                measure: str = "O", maximize: bool = True, seed: int = 0, stream=None,
+                patience: int = 0):
+    """Simulated annealing chains on the device (patience > 0: a chain also
+    stops after `patience` steps without a better set).  Returns
+    (final_masks, final_values, best_masks, best_values, stats), n_chains
+    entries each."""
     fm = np.zeros(n_chains, dtype=np.uint64)
     fv = np.zeros(n_chains, dtype=np.float64)
     bm = np.zeros(n_chains, dtype=np.uint64)
     bv = np.zeros(n_chains, dtype=np.float64)
     st = thoi_stats()
-    _check(load().thoi_anneal(h, k_lo, k_hi, n_chains, iters, T0, alpha, MEASURES.index(measure),
-                              int(bool(maximize)), seed & ((1 << 64) - 1), _ptr(fm), _ptr(fv),
+    _check(load().thoi_anneal(h, k_lo, k_hi, n_chains, iters, T0, alpha, patience,
+                              MEASURES.index(measure), int(bool(maximize)), seed & ((1 << 64) - 1), _ptr(fm), _ptr(fv),
                               _ptr(bm), _ptr(bv), ctypes.byref(st), _stream_ptr(stream)),
            "thoi_anneal")
     return fm, fv, bm, bv, st
@@ -477,7 +480,7 @@ def thoi_group_greedy(handles, k0: int, k1: int, kappa: int, measure: str = "O",
 
 def thoi_group_anneal(handles, k_lo: int, k_hi: int, n_chains: int, iters: int, T0: float,
                       alpha: float, measure: str = "O", objective="mean", maximize: bool = True,
-                      seed: int = 0, stream=None):
+                      seed: int = 0, stream=None, patience: int = 0):
     """Simulated annealing on a group objective; outputs as thoi_anneal."""
     arr, D = _handles(handles)
     fm = np.zeros(n_chains, dtype=np.uint64)
@@ -485,7 +488,7 @@ def thoi_group_anneal(handles, k_lo: int, k_hi: int, n_chains: int, iters: int, 
     bm = np.zeros(n_chains, dtype=np.uint64)
     bv = np.zeros(n_chains, dtype=np.float64)
     st = thoi_stats()
-    _check(load().thoi_group_anneal(arr, D, k_lo, k_hi, n_chains, iters, T0, alpha,
+    _check(load().thoi_group_anneal(arr, D, k_lo, k_hi, n_chains, iters, T0, alpha, patience,
                                     MEASURES.index(measure), _objective(objective),
                                     int(bool(maximize)), seed & ((1 << 64) - 1), _ptr(fm),
                                     _ptr(fv), _ptr(bm), _ptr(bv), ctypes.byref(st),
@@ -506,22 +509,38 @@ def thoi_order_record_noalloc(Sigma, k: int, top_m: int = 0, rec_out=None, top_o
                               stream=None):
     """Per-order record of order k from a device covariance, allocating no
     device memory inside the library (for callers that cannot call
-    cudaMalloc/cudaFree).  Sigma, rec_out and top_out are CUDA tensors
-    (uint8 buffers of 240 and 2*top_m*16 bytes when given).  Calls that
-    overlap on the GPU share one scratch array and must be serialised."""
+    cudaMalloc/cudaFree).  Sigma, rec_out and top_out are CUDA tensors on one
+    device (uint8 buffers of at least 240 and 2*top_m*16 bytes when given);
+    the call runs with that device current, on `stream` or its current
+    stream.  Calls that overlap on the GPU share one scratch array and must
+    be serialised."""
     import torch
     S = Sigma if Sigma.dtype == torch.float64 else Sigma.double()
     S = S.contiguous()
+    if not S.is_cuda:
+        raise ValueError("Sigma must be a CUDA tensor")
     N = S.shape[0]
-    if rec_out is None:
-        rec_out = torch.zeros(RECORD_DTYPE.itemsize, dtype=torch.uint8, device=S.device)
-    if top_out is None and top_m > 0:
-        top_out = torch.zeros(2 * top_m * TOP_DTYPE.itemsize, dtype=torch.uint8, device=S.device)
-    _check(load().thoi_order_record_noalloc(_ptr(S), N, k, top_m, _ptr(rec_out),
-                                            _ptr(top_out) if top_m > 0 else None,
-                                            _stream_ptr(stream)), "thoi_order_record_noalloc")
-    rec = rec_out.cpu().numpy().view(RECORD_DTYPE)[0].copy()
-    tops = (top_out.cpu().numpy().view(TOP_DTYPE).reshape(2, top_m).copy() if top_m > 0
+    with torch.cuda.device(S.device):
+        if rec_out is None:
+            rec_out = torch.zeros(RECORD_DTYPE.itemsize, dtype=torch.uint8, device=S.device)
+        if top_out is None and top_m > 0:
+            top_out = torch.zeros(2 * top_m * TOP_DTYPE.itemsize, dtype=torch.uint8,
+                                  device=S.device)
+        need = [(rec_out, RECORD_DTYPE.itemsize, "rec_out")]
+        if top_m > 0:
+            need.append((top_out, 2 * top_m * TOP_DTYPE.itemsize, "top_out"))
+        for buf, nbytes, name in need:
+            if not torch.is_tensor(buf) or buf.device != S.device or not buf.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous tensor on {S.device}")
+            if buf.numel() * buf.element_size() < nbytes:
+                raise ValueError(f"{name} holds fewer than {nbytes} bytes")
+        _check(load().thoi_order_record_noalloc(_ptr(S), N, k, top_m, _ptr(rec_out),
+                                                _ptr(top_out) if top_m > 0 else None,
+                                                _stream_ptr(stream)),
+               "thoi_order_record_noalloc")
+    rec = rec_out.cpu().numpy().view(np.uint8)[:RECORD_DTYPE.itemsize].view(RECORD_DTYPE)[0].copy()
+    tops = (top_out.cpu().numpy().view(np.uint8)[:2 * top_m * TOP_DTYPE.itemsize]
+            .view(TOP_DTYPE).reshape(2, top_m).copy() if top_m > 0
             else np.zeros((2, 0), dtype=TOP_DTYPE))
     return rec, tops[0], tops[1]
 
@@ -573,9 +592,9 @@ class Context:
                              top_m=self.opt.top_m, stream=stream)
 
     def anneal(self, k_lo, k_hi, n_chains, iters, T0, alpha, measure="O", maximize=True, seed=0,
-               stream=None):
+               stream=None, patience=0):
         fm, fv, bm, bv, _ = thoi_anneal(self.h, k_lo, k_hi, n_chains, iters, T0, alpha, measure,
-                                        maximize, seed, stream)
+                                        maximize, seed, stream, patience)
         return fm, fv, bm, bv
 
     def greedy(self, k0, k1, kappa, measure="O", maximize=True, stream=None):

@@ -17,7 +17,10 @@
 // removed (if present and the set is above k_lo), else the move is a swap.
 // Acceptance: always if the energy rises, else with probability
 // exp(dE / Temp) (the paper prints exp(-dE / Temp), which is at least 1 for
-// dE <= 0; the sign is read as the usual Metropolis rule).  Energy = the
+// dE <= 0; the sign is read as the usual Metropolis rule).  Temp = T0 at step
+// 1, multiplied by alpha after every step.  Termination (the paper's two
+// criteria): after `iters` steps, or, with patience > 0, after the first step
+// t with no rise of the best energy since step t - patience.  Energy = the
 // measure (maximise) or its negative (minimise); sets that are not positive
 // definite are rejected.  Over D > 1 datasets the value is a group objective
 // (Methods, "Heuristics": the searches take several datasets): the mean of
@@ -115,7 +118,8 @@ __device__ double sa_measure(unsigned long long mask, const double* sR, int ldr,
 template <typename F>
 __device__ __forceinline__ void sa_chain(const int chain, const int N, const int klo,
                                          const int khi, const int iters, const double T0,
-                                         const double alpha, const int maximize,
+                                         const double alpha, const int patience,
+                                         const int maximize,
                                          const unsigned long long seed, F&& value,
                                          const bool write, unsigned long long* final_mask,
                                          double* final_val, unsigned long long* best_mask,
@@ -141,6 +145,7 @@ __device__ __forceinline__ void sa_chain(const int chain, const int N, const int
   double bestE = E;
   unsigned long long bmask = mask;
   double T = T0;
+  int t_best = 0;  // last step that raised the best energy
   unsigned long long acc = 0;
   const unsigned long long full = N >= 64 ? ~0ull : ((1ull << N) - 1ull);
   for (int it = 1; it <= iters; it++) {
@@ -174,10 +179,14 @@ __device__ __forceinline__ void sa_chain(const int chain, const int N, const int
         if (E > bestE) {
           bestE = E;
           bmask = mask;
+          t_best = it;
         }
       }
     }
     T *= alpha;
+    // early stop: no improvement of the best energy for `patience` steps
+    // (every thread of a chain holds the same t_best, so a warp stops together)
+    if (patience > 0 && it - t_best >= patience) break;
   }
   if (write) {
     final_mask[chain] = mask;
@@ -193,7 +202,8 @@ __global__ void __launch_bounds__(SA_NT) k_anneal(const double* __restrict__ R64
                                                   const double* __restrict__ ls, int N, int klo,
                                                   int khi, const Combine* __restrict__ cmb_tab,
                                                   int n_chains, int iters, double T0, double alpha,
-                                                  int measure, int maximize, unsigned long long seed,
+                                                  int patience, int measure, int maximize,
+                                                  unsigned long long seed,
                                                   unsigned long long* __restrict__ final_mask,
                                                   double* __restrict__ final_val,
                                                   unsigned long long* __restrict__ best_mask,
@@ -210,7 +220,7 @@ __global__ void __launch_bounds__(SA_NT) k_anneal(const double* __restrict__ R64
   __syncthreads();
   const int chain = blockIdx.x * blockDim.x + threadIdx.x;
   if (chain >= n_chains) return;
-  sa_chain(chain, N, klo, khi, iters, T0, alpha, maximize, seed,
+  sa_chain(chain, N, klo, khi, iters, T0, alpha, patience, maximize, seed,
            [&](unsigned long long m) { return sa_measure(m, sR, ldr, sls, scmb, measure); }, true,
            final_mask, final_val, best_mask, best_val, accepted);
 }
@@ -224,7 +234,7 @@ constexpr int SA_WARP_CHAINS = 16384;  // one dataset: a warp per chain below th
 __global__ void __launch_bounds__(SA_GNT)
     k_anneal_warp(const double* __restrict__ R64, const double* __restrict__ ls, int N, int klo,
                   int khi, const Combine* __restrict__ cmb_tab, int n_chains, int iters, double T0,
-                  double alpha, int measure, int maximize, unsigned long long seed,
+                  double alpha, int patience, int measure, int maximize, unsigned long long seed,
                   unsigned long long* __restrict__ final_mask, double* __restrict__ final_val,
                   unsigned long long* __restrict__ best_mask, double* __restrict__ best_val,
                   unsigned long long* __restrict__ accepted) {
@@ -275,7 +285,7 @@ __global__ void __launch_bounds__(SA_GNT)
     return pick5(v, measure);
   };
 #undef AG
-  sa_chain(chain, N, klo, khi, iters, T0, alpha, maximize, seed, value, lane == 0, final_mask,
+  sa_chain(chain, N, klo, khi, iters, T0, alpha, patience, maximize, seed, value, lane == 0, final_mask,
            final_val, best_mask, best_val, accepted);
 }
 
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(SA_GNT)
     k_anneal_group(const double* const* __restrict__ Rs, const double* const* __restrict__ lss,
                    int D, int objective, int N, int klo, int khi,
                    const Combine* __restrict__ cmb_tab, int n_chains, int iters, double T0,
-                   double alpha, int measure, int maximize, unsigned long long seed,
+                   double alpha, int patience, int measure, int maximize, unsigned long long seed,
                    unsigned long long* __restrict__ final_mask, double* __restrict__ final_val,
                    unsigned long long* __restrict__ best_mask, double* __restrict__ best_val,
                    unsigned long long* __restrict__ accepted) {
@@ -333,19 +343,20 @@ __global__ void __launch_bounds__(SA_GNT)
     const double sd = sqrt(warp_sum(ss) / (double)(P - 1));
     return sd > 0.0 ? mean / sd : nan;
   };
-  sa_chain(chain, N, klo, khi, iters, T0, alpha, maximize, seed, value, lane == 0, final_mask,
+  sa_chain(chain, N, klo, khi, iters, T0, alpha, patience, maximize, seed, value, lane == 0, final_mask,
            final_val, best_mask, best_val, accepted);
 }
 
 cudaError_t launch_anneal(const double* const* Rs, const double* const* lss, int D,
                           int objective, int N, int klo, int khi, const Combine* cmb_tab,
                           const double* R0, const double* ls0, int n_chains, int iters, double T0,
-                          double alpha, int measure, int maximize, unsigned long long seed,
+                          double alpha, int patience, int measure, int maximize,
+                          unsigned long long seed,
                           unsigned long long* final_mask, double* final_val,
                           unsigned long long* best_mask, double* best_val,
                           unsigned long long* accepted, cudaStream_t s) {
   if (khi > SA_KMAX || klo < 1 || khi < klo || khi > N || n_chains < 1 || iters < 0 || D < 1 ||
-      D > THOI_MAX_GROUP)
+      D > THOI_MAX_GROUP || patience < 0)
     return cudaErrorInvalidValue;
   if (D == 1 && n_chains < SA_WARP_CHAINS) {
     const size_t sm = ((size_t)N * row_stride(N) + N) * sizeof(double) +
@@ -360,7 +371,7 @@ cudaError_t launch_anneal(const double* const* Rs, const double* const* lss, int
       if (e != cudaSuccess) return e;
     }
     k_anneal_warp<<<grid, SA_GNT, sm, s>>>(R0, ls0, N, klo, khi, cmb_tab, n_chains, iters, T0,
-                                           alpha, measure, maximize, seed, final_mask, final_val,
+                                           alpha, patience, measure, maximize, seed, final_mask, final_val,
                                            best_mask, best_val, accepted);
     return cudaGetLastError();
   }
@@ -369,14 +380,15 @@ cudaError_t launch_anneal(const double* const* Rs, const double* const* lss, int
                       (size_t)(khi + 1) * sizeof(Combine);
     const int grid = (n_chains + SA_NT - 1) / SA_NT;
     k_anneal<<<grid, SA_NT, sm, s>>>(R0, ls0, N, klo, khi, cmb_tab, n_chains, iters, T0, alpha,
-                                     measure, maximize, seed, final_mask, final_val, best_mask,
+                                     patience, measure, maximize, seed, final_mask, final_val, best_mask,
                                      best_val, accepted);
     return cudaGetLastError();
   }
   const long long threads = (long long)n_chains * 32;
   const int grid = (int)((threads + SA_GNT - 1) / SA_GNT);
   k_anneal_group<<<grid, SA_GNT, 0, s>>>(Rs, lss, D, objective, N, klo, khi, cmb_tab, n_chains,
-                                         iters, T0, alpha, measure, maximize, seed, final_mask,
+                                         iters, T0, alpha, patience, measure, maximize, seed,
+                                         final_mask,
                                          final_val, best_mask, best_val, accepted);
   return cudaGetLastError();
 }

@@ -202,7 +202,8 @@ cudaError_t launch_grad_finish(const double* Gpart, int nblk, const double* sig6
 cudaError_t launch_anneal(const double* const* Rs, const double* const* lss, int D,
                           int objective, int N, int klo, int khi, const Combine* cmb_tab,
                           const double* R0, const double* ls0, int n_chains, int iters, double T0,
-                          double alpha, int measure, int maximize, unsigned long long seed,
+                          double alpha, int patience, int measure, int maximize,
+                          unsigned long long seed,
                           unsigned long long* final_mask, double* final_val,
                           unsigned long long* best_mask, double* best_val,
                           unsigned long long* accepted, cudaStream_t s);

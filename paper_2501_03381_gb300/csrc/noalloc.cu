@@ -36,30 +36,8 @@ static_assert(NA_END <= NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the stati
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-// Device address of the scratch array per device.  In host code the symbol
-// name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress with the device current.
-constexpr int NOALLOC_MAX_DEVICES = 64;
-static void* g_scratch_addr[NOALLOC_MAX_DEVICES];
-static std::mutex g_scratch_mu;
-
-static cudaError_t scratch_for_current_device(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = (unsigned char*)g_scratch_addr[dev];
-  return cudaSuccess;
-}
-
 // Pascal's triangle into the scratch binomial table (one thread; 4225 adds).
+// The table never changes, so it is filled once per device (below).
 __global__ void k_fill_binom(unsigned long long* b) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   for (int n = 0; n < NB; n++) {
@@ -68,17 +46,46 @@ __global__ void k_fill_binom(unsigned long long* b) {
   }
 }
 
+// Device address of the scratch array per device.  In host code the symbol
+// name is only a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress with the device current.  The first call on a device
+// also fills the binomial table in the array and waits for it, under the
+// same lock, so later calls find it complete.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_scratch_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_scratch_mu;
+
+static cudaError_t scratch_for_device(int dev, cudaStream_t s, unsigned char** out) {
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    k_fill_binom<<<1, 1, 0, s>>>((unsigned long long*)((unsigned char*)p + NA_BINOM));
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
 }  // namespace thoi
 
 using namespace thoi;
 
-static bool dev_ptr(const void* p) {
+// Device (or managed) memory of device `dev`: the kernels run on the
+// current device and must not touch another GPU's memory.
+static bool dev_ptr(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) &&
+         at.device == dev;
 }
 
 extern "C" thoi_status thoi_order_record_noalloc(const double* Sigma, int64_t N, int32_t k,
@@ -87,7 +94,9 @@ extern "C" thoi_status thoi_order_record_noalloc(const double* Sigma, int64_t N,
   if (N > THOI_MAX_N || top_m > NOALLOC_MAX_TOP_M) return THOI_ERR_TOO_LARGE;
   if (!Sigma || !rec_out || N < 1 || k < 1 || k > N || top_m < 0) return THOI_ERR_INVALID_ARG;
   if (top_m > 0 && !top_out) return THOI_ERR_INVALID_ARG;
-  if (!dev_ptr(Sigma) || !dev_ptr(rec_out) || (top_m > 0 && !dev_ptr(top_out)))
+  int dev = 0, num_sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return THOI_ERR_CUDA;
+  if (!dev_ptr(Sigma, dev) || !dev_ptr(rec_out, dev) || (top_m > 0 && !dev_ptr(top_out, dev)))
     return THOI_ERR_INVALID_ARG;
   // C(N, k) by Pascal's rule on one row (no allocation); one launch indexes
   // its nplets with 32-bit offsets
@@ -98,7 +107,7 @@ extern "C" thoi_status thoi_order_record_noalloc(const double* Sigma, int64_t N,
   if (n_nplets > 0xffffffffull) return THOI_ERR_TOO_LARGE;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* base = nullptr;
-  if (scratch_for_current_device(&base) != cudaSuccess) return THOI_ERR_CUDA;
+  if (scratch_for_device(dev, s, &base) != cudaSuccess) return THOI_ERR_CUDA;
   int* status = (int*)(base + NA_STATUS);
   unsigned long long* binom = (unsigned long long*)(base + NA_BINOM);
   double* R64 = (double*)(base + NA_R64);
@@ -106,13 +115,11 @@ extern "C" thoi_status thoi_order_record_noalloc(const double* Sigma, int64_t N,
   double* ls = (double*)(base + NA_LS);
   PartRec* part = (PartRec*)(base + NA_PART);
   TopEnt* top = (TopEnt*)(base + NA_TOP);
-  int dev = 0, num_sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return THOI_ERR_CUDA;
   if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return THOI_ERR_CUDA;
   // the status word must start at zero; everything else is fully rewritten
+  // (the binomial table was filled by the device's first call)
   if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return THOI_ERR_CUDA;
-  k_fill_binom<<<1, 1, 0, s>>>(binom);
   if (launch_normalise(Sigma, nullptr, (int)N, R64, R32, ls, nullptr, status, s) != cudaSuccess)
     return THOI_ERR_CUDA;
   NpletArgs a;

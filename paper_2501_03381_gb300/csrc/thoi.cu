@@ -2048,7 +2048,7 @@ extern "C" thoi_status thoi_group_greedy(thoi_ctx* const* ctxs, int32_t D, int32
 // objective over D contexts.
 static thoi_status anneal_impl(thoi_ctx* const* ctxs, int D, int objective, int32_t k_lo,
                                int32_t k_hi, int32_t n_chains, int32_t iters, double T0,
-                               double alpha, int32_t measure, int32_t maximize, uint64_t seed,
+                               double alpha, int32_t patience, int32_t measure, int32_t maximize, uint64_t seed,
                                uint64_t* final_masks, double* final_values, uint64_t* best_masks,
                                double* best_values, thoi_stats* stats, cudaStream_t s) {
   const int nc = k_hi + 1;
@@ -2081,7 +2081,8 @@ static thoi_status anneal_impl(thoi_ctx* const* ctxs, int D, int objective, int3
   CK(cudaMemcpyAsync(d_tab, tab.data(), tab_bytes, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_ptrs, ptrs.data(), ptr_bytes, cudaMemcpyHostToDevice, s));
   CK(launch_anneal(d_ptrs, d_ptrs + D, D, objective, ctxs[0]->N, k_lo, k_hi, d_tab,
-                   ctxs[0]->R64, ctxs[0]->ls, n_chains, iters, T0, alpha, measure, maximize, seed,
+                   ctxs[0]->R64, ctxs[0]->ls, n_chains, iters, T0, alpha, patience, measure,
+                   maximize, seed,
                    fm, fv, bm, bv, acc, s));
   CK(cudaMemcpyAsync(final_masks, fm, n * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(final_values, fv, n * 8, cudaMemcpyDeviceToHost, s));
@@ -2102,39 +2103,41 @@ static thoi_status anneal_impl(thoi_ctx* const* ctxs, int D, int objective, int3
 }
 
 static bool anneal_args_ok(int N, int32_t k_lo, int32_t k_hi, int32_t n_chains, int32_t iters,
-                           double T0, double alpha, int32_t measure, const void* a, const void* b,
+                           double T0, double alpha, int32_t patience, int32_t measure, const void* a, const void* b,
                            const void* c, const void* d) {
   return k_lo >= 1 && k_hi >= k_lo && k_hi <= N && k_hi <= 32 && n_chains >= 1 && iters >= 0 &&
-         T0 > 0.0 && alpha > 0.0 && measure >= THOI_H && measure <= THOI_S && a && b && c && d;
+         T0 > 0.0 && alpha > 0.0 && patience >= 0 && measure >= THOI_H && measure <= THOI_S && a && b && c && d;
 }
 
 extern "C" thoi_status thoi_anneal(thoi_ctx* c, int32_t k_lo, int32_t k_hi, int32_t n_chains,
-                                   int32_t iters, double T0, double alpha, int32_t measure,
-                                   int32_t maximize, uint64_t seed, uint64_t* final_masks,
-                                   double* final_values, uint64_t* best_masks,
-                                   double* best_values, thoi_stats* stats, void* stream) {
-  if (!c || !anneal_args_ok(c->N, k_lo, k_hi, n_chains, iters, T0, alpha, measure, final_masks,
-                            final_values, best_masks, best_values))
+                                   int32_t iters, double T0, double alpha, int32_t patience,
+                                   int32_t measure, int32_t maximize, uint64_t seed,
+                                   uint64_t* final_masks, double* final_values,
+                                   uint64_t* best_masks, double* best_values, thoi_stats* stats,
+                                   void* stream) {
+  if (!c || !anneal_args_ok(c->N, k_lo, k_hi, n_chains, iters, T0, alpha, patience, measure,
+                            final_masks, final_values, best_masks, best_values))
     return THOI_ERR_INVALID_ARG;
-  return anneal_impl(&c, 1, -1, k_lo, k_hi, n_chains, iters, T0, alpha, measure, maximize, seed,
-                     final_masks, final_values, best_masks, best_values, stats,
+  return anneal_impl(&c, 1, -1, k_lo, k_hi, n_chains, iters, T0, alpha, patience, measure,
+                     maximize, seed, final_masks, final_values, best_masks, best_values, stats,
                      (cudaStream_t)stream);
 }
 
 extern "C" thoi_status thoi_group_anneal(thoi_ctx* const* ctxs, int32_t D, int32_t k_lo,
                                          int32_t k_hi, int32_t n_chains, int32_t iters, double T0,
-                                         double alpha, int32_t measure, int32_t objective,
-                                         int32_t maximize, uint64_t seed, uint64_t* final_masks,
-                                         double* final_values, uint64_t* best_masks,
-                                         double* best_values, thoi_stats* stats, void* stream) {
+                                         double alpha, int32_t patience, int32_t measure,
+                                         int32_t objective, int32_t maximize, uint64_t seed,
+                                         uint64_t* final_masks, double* final_values,
+                                         uint64_t* best_masks, double* best_values,
+                                         thoi_stats* stats, void* stream) {
   thoi_status st = group_args_ok(ctxs, D, measure, objective);
   if (st != THOI_OK) return st;
-  if (!anneal_args_ok(ctxs[0]->N, k_lo, k_hi, n_chains, iters, T0, alpha, measure, final_masks,
-                      final_values, best_masks, best_values))
+  if (!anneal_args_ok(ctxs[0]->N, k_lo, k_hi, n_chains, iters, T0, alpha, patience, measure,
+                      final_masks, final_values, best_masks, best_values))
     return THOI_ERR_INVALID_ARG;
-  return anneal_impl(ctxs, D, objective, k_lo, k_hi, n_chains, iters, T0, alpha, measure,
-                     maximize, seed, final_masks, final_values, best_masks, best_values, stats,
-                     (cudaStream_t)stream);
+  return anneal_impl(ctxs, D, objective, k_lo, k_hi, n_chains, iters, T0, alpha, patience,
+                     measure, maximize, seed, final_masks, final_values, best_masks, best_values,
+                     stats, (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------------ API: autotune

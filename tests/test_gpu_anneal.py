@@ -46,6 +46,8 @@ def test_anneal_arguments():
                     (3, 5, 4, 10, 0.0, 0.9)]:
             with pytest.raises(P.ThoiError):
                 c.anneal(*bad)
+        with pytest.raises(P.ThoiError):
+            c.anneal(3, 5, 4, 10, 1.0, 0.9, patience=-1)
 
 
 @pytest.mark.parametrize("chains", [16384, 3])
@@ -73,3 +75,19 @@ def test_anneal_warp_kernel_order_32():
         fm, fv, bm, bv = c.anneal(28, 32, 4, 25, 0.2, 0.9, "S", False, 5)
     assert _sets(fm) == ref[0] and _sets(bm) == ref[2]
     np.testing.assert_allclose(bv, ref[3], rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("chains", [24, 16384])
+def test_anneal_patience_matches_oracle(chains):
+    # early stop after `patience` steps without a better set (the paper's
+    # second termination criterion), on the warp and the thread kernels
+    S = workloads.random_corr(np.random.default_rng(66), 16)
+    iters, T0, alpha, seed, p = 120, 0.05, 0.97, 31, 6
+    ref = oracle.anneal(S, 3, 9, 24, iters, T0, alpha, "O", True, seed, patience=p)
+    full = oracle.anneal(S, 3, 9, 24, iters, T0, alpha, "O", True, seed)
+    assert ref[0] != full[0]  # some chains stopped early and ended elsewhere
+    with P.Context(Sigma=S) as c:
+        fm, fv, bm, bv = c.anneal(3, 9, chains, iters, T0, alpha, "O", True, seed, patience=p)
+    assert _sets(fm[:24]) == ref[0] and _sets(bm[:24]) == ref[2]
+    np.testing.assert_allclose(fv[:24], ref[1], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(bv[:24], ref[3], rtol=0, atol=1e-10)

@@ -304,3 +304,19 @@ def test_group_anneal_matches_oracle(objective, klo, khi):
     np.testing.assert_allclose(fv, ref[1], rtol=0, atol=1e-9)
     np.testing.assert_allclose(bv, ref[3], rtol=0, atol=1e-9)
     assert st.nplets == 6 * 41 * 4
+
+
+def test_group_anneal_patience_matches_oracle():
+    rng = np.random.default_rng(74)
+    Ss = [workloads.random_corr(rng, 10) for _ in range(4)]
+    ref = oracle.anneal(Ss, 3, 6, 6, 60, 0.05, 0.95, "O", True, seed=12, objective="mean",
+                        patience=5)
+    cs = [P.Context(Sigma=S) for S in Ss]
+    try:
+        fm, fv, bm, bv, _ = P.thoi_group_anneal(cs, 3, 6, 6, 60, 0.05, 0.95, "O", "mean", True,
+                                                12, patience=5)
+    finally:
+        _close(cs)
+    assert [_members(x) for x in fm] == ref[0]
+    assert [_members(x) for x in bm] == ref[2]
+    np.testing.assert_allclose(bv, ref[3], rtol=0, atol=1e-9)

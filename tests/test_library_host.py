@@ -112,8 +112,8 @@ def test_group_entry_points_validate_without_gpu(lib):
                                        ctypes.byref(st), None) == 1
         assert lib.thoi_group_greedy(ctxs, D, 3, 4, 8, 3, 0, 1, None, None, ctypes.byref(st),
                                      None) == 1
-        assert lib.thoi_group_anneal(ctxs, D, 3, 4, 8, 10, 1.0, 0.9, 3, 0, 1, 0, None, None, None,
-                                     None, ctypes.byref(st), None) == 1
+        assert lib.thoi_group_anneal(ctxs, D, 3, 4, 8, 10, 1.0, 0.9, 0, 3, 0, 1, 0, None, None,
+                                     None, None, ctypes.byref(st), None) == 1
 
 
 def test_search_and_measure_entry_points_validate_without_gpu(lib):
@@ -124,7 +124,7 @@ def test_search_and_measure_entry_points_validate_without_gpu(lib):
     vals = np.zeros(8)
     assert lib.thoi_greedy(None, 3, 4, 4, 3, 1, masks.ctypes.data, vals.ctypes.data,
                            ctypes.byref(st), None) == 1
-    assert lib.thoi_anneal(None, 3, 4, 4, 10, 1.0, 0.9, 3, 1, 0, masks.ctypes.data,
+    assert lib.thoi_anneal(None, 3, 4, 4, 10, 1.0, 0.9, 0, 3, 1, 0, masks.ctypes.data,
                            vals.ctypes.data, masks.ctypes.data, vals.ctypes.data,
                            ctypes.byref(st), None) == 1
     assert lib.thoi_measures(None, orders, 1, 0, 2**64 - 1, 0, None, 0, ctypes.byref(st),

@@ -61,3 +61,53 @@ def test_noalloc_rejects_sizes_beyond_limits():
     st = lib.thoi_order_record_noalloc(ctypes.c_void_p(S.data_ptr()), 65, 3, 0,
                                        ctypes.c_void_p(rec.data_ptr()), None, None)
     assert st == 3  # N above 64
+
+
+def test_noalloc_status_after_the_device_work():
+    # errors found on the device come back as statuses: a zero variance is
+    # an invalid argument; two identical variables make the pair singular
+    S = np.eye(6)
+    S[2, 2] = 0.0
+    with pytest.raises(P.ThoiError) as e:
+        P.thoi_order_record_noalloc(torch.as_tensor(S, device="cuda"), 3)
+    assert e.value.code == 1  # THOI_ERR_INVALID_ARG
+    S = workloads.random_corr(np.random.default_rng(81), 6)
+    S[:, 4] = S[:, 1]
+    S[4, :] = S[1, :]
+    S[4, 4] = S[1, 1]
+    with pytest.raises(P.ThoiError) as e:
+        P.thoi_order_record_noalloc(torch.as_tensor(S, device="cuda"), 2)
+    assert e.value.code == 4  # THOI_ERR_NOT_PD
+    # and the next valid call is unaffected by the failed ones
+    X, _ = workloads.small()
+    S = oracle.copula_cov(X)
+    ref, _, _ = _regular(S, 4, 0)
+    rec, _, _ = P.thoi_order_record_noalloc(torch.as_tensor(S, device="cuda"), 4)
+    np.testing.assert_allclose(rec["mean"], ref["mean"], rtol=0, atol=TOL64)
+
+
+def test_noalloc_rejects_short_or_foreign_buffers():
+    S = torch.eye(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        P.thoi_order_record_noalloc(S, 3, 4, rec_out=torch.zeros(239, dtype=torch.uint8,
+                                                                 device="cuda"))
+    with pytest.raises(ValueError):
+        P.thoi_order_record_noalloc(S, 3, 4, top_out=torch.zeros(2 * 4 * 16 - 1,
+                                                                 dtype=torch.uint8,
+                                                                 device="cuda"))
+    with pytest.raises(ValueError):
+        P.thoi_order_record_noalloc(S, 3, 0, rec_out=torch.zeros(240, dtype=torch.uint8))
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs two GPUs")
+def test_noalloc_rejects_memory_of_another_device():
+    # the library runs on the current device: a covariance on another GPU is
+    # an invalid argument, checked before any device work
+    lib = P.load()
+    S = torch.eye(8, dtype=torch.float64, device="cuda:1")
+    rec = torch.zeros(240, dtype=torch.uint8, device="cuda:0")
+    with torch.cuda.device(0):
+        st = lib.thoi_order_record_noalloc(ctypes.c_void_p(S.data_ptr()), 8, 3, 0,
+                                           ctypes.c_void_p(rec.data_ptr()), None, None)
+    assert st == 1
