@@ -207,9 +207,31 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle baseline
-def cpu_baseline(seconds: float, seed: int = 0):
+def cpu_model() -> str:
+    """The host CPU's model as /proc/cpuinfo names it (x86: "model name"; Arm:
+    implementer and part numbers, with the part named where it is known)."""
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        return "unknown"
+    if "model name" in fields:
+        return fields["model name"]
+    parts = {"0xd4f": "Neoverse V2 (Grace)", "0xd40": "Neoverse V1", "0xd0c": "Neoverse N1"}
+    imp, part = fields.get("CPU implementer", "?"), fields.get("CPU part", "?")
+    return f"Arm implementer {imp} part {part}" + (f" = {parts[part]}" if part in parts else "")
+
+
+def cpu_baseline(seconds: float, seed: int = 0, one_thread_seconds: float = 0.0):
     """The FP64 oracle as it stands, on a uniform random sample of the
-    workload's nplet ids, on every host core."""
+    workload's nplet ids, on every host core (and, when one_thread_seconds >
+    0, on one thread over a smaller sample of the same draw).  The rate of
+    the whole workload is extrapolated from the sample: ids are drawn
+    uniformly, so the sample's mix of orders is the workload's."""
     import numpy as np
 
     import oracle
@@ -228,10 +250,22 @@ def cpu_baseline(seconds: float, seed: int = 0):
     oracle.measures_ids(S, orders, ids)
     dt = time.perf_counter() - t0
     cores = os.cpu_count()
-    return {"value": n / dt, "unit": "nplets/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} nplet ids drawn uniformly (seed {seed}) from the "
-                      f"{total:,} nplets; FP64 LU per subset and per leave-one-out subset; "
-                      f"{dt:.1f} s on {cores} OpenMP threads"}
+    out = {"value": n / dt, "unit": "nplets/s", "cores": cores, "kind": "oracle",
+           "cpu_model": cpu_model(), "extrapolated": True,
+           "sample": f"{n} nplet ids drawn uniformly (seed {seed}) from the "
+                     f"{total:,} nplets; FP64 LU per subset and per leave-one-out subset; "
+                     f"{dt:.1f} s on {cores} OpenMP threads; the rate of the whole workload "
+                     f"is this sample's rate"}
+    if one_thread_seconds > 0:
+        n1 = int(max(500, min(n, n / dt / cores * one_thread_seconds)))
+        ids1 = ids[rng.permutation(n)[:n1]]
+        ids1.sort()
+        t0 = time.perf_counter()
+        oracle.measures_ids(S, orders, ids1, nthreads=1)
+        d1 = time.perf_counter() - t0
+        out["one_thread"] = {"value": n1 / d1, "unit": "nplets/s", "sample": f"{n1} of those ids",
+                             "seconds": d1}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -247,12 +281,16 @@ def run_reference(args, rank, world):
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "nplets/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_nplets() / v * 1e3, "higher_is_better": True,
+            "ms_per_step": total_nplets() / v * 1e3, "ms_per_step_extrapolated": True,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N_VARS, "T": T_SAMPLES, "orders": "3..30",
                        "top_m": TOP_M},
             "cpu_baseline": {"value": v, "unit": "nplets/s", "cores": os.cpu_count(),
-                             "kind": "oracle", "sample": cb["sample"]},
+                             "kind": "oracle", "cpu_model": cb["cpu_model"],
+                             "extrapolated": True,
+                             "sample": cb["sample"] + "; each step a bounded sample, its time "
+                                       "scaled to the whole workload"},
             "e2e": {"value": v, "unit": "nplets/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -329,6 +367,11 @@ def run_ours(args, rank, world, local_rank):
                   for e in json.load(open(tune_path))}
     except Exception:
         shapes = {}
+    # measured FFMA and DFMA peaks of this GPU (self-written multiply-add
+    # chains): the FP32 one cross-checks the derived peak below, the FP64 one
+    # is the denominator of the FP64 rooflines
+    fma32, _ = P.thoi_fma_peak(False)
+    fma64, _ = P.thoi_fma_peak(True)
     sampler = ClockSampler(local_rank)
     sampler.start()
     ms, nplet_ms, ref_ms, launches, nref = timed(opt32, args.steps, args.warmup)
@@ -411,7 +454,9 @@ def run_ours(args, rank, world, local_rank):
                                     "one build per (k-2)-prefix, one stored step per "
                                     "(k-1)-prefix, one final step per nplet",
                      "dense_equivalent_tflops": f_dense / kern_s / 1e12,
-                     "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
+                     "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                     "peak_measured_ffma_tflops": fma32,
+                     "peak_measured_dfma_tflops": fma64},
         "e2e": {"value": n_total / e2e_s, "unit": "nplets/s",
                 "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(nb)},
         "gpu_launches": int(launches),
@@ -421,9 +466,9 @@ def run_ours(args, rank, world, local_rank):
         "fp64_path": fp64,
     }
     if not args.no_extra:
-        line["other_workloads"] = run_extra(args, dev, stream, flush, peak, rank)
+        line["other_workloads"] = run_extra(args, dev, stream, flush, peak, rank, fma64)
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, one_thread_seconds=3.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -431,7 +476,7 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 # ------------------------------------------------------------------ adjoint and batching
-def run_extra(args, dev, stream, flush, peak, rank):
+def run_extra(args, dev, stream, flush, peak, rank, fp64_peak):
     """The adjoint (N=60, T=2000, orders 3..5), the 64-dataset batch
     (N ~ U{10..40}, T ~ U{200..2000}, orders 3..min(N,8)) and the greedy
     search (N=60, orders 3..20), each timed with CUDA events after warm-up,
@@ -544,7 +589,6 @@ def run_extra(args, dev, stream, flush, peak, rank):
     rest = n_eval - math.comb(Nv, k0)
     per_order = rest / (k1 - k0) if k1 > k0 else 0
     fl += sum(per_order * flops_model(k) for k in range(k0 + 1, k1 + 1))
-    fp64_peak = 1.25  # TFLOP/s, nominal GB300 FP64 (no measured figure for it)
     ach = fl / (ms / 1e3) / 1e12
     entry = {"workload": f"N=60, T=2000 random-correlation Gaussian; greedy search maximising O "
                          f"from the exhaustive top-{kappa} of order {k0} to order {k1} "
@@ -553,7 +597,7 @@ def run_extra(args, dev, stream, flush, peak, rank):
              "best_O_at_k1": float(values[-1][0]),
              "roofline": {"bound": "fp64", "achieved": ach, "peak": fp64_peak,
                           "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                          "peak_basis": "nominal GB300 FP64 (1.25 TFLOP/s)",
+                          "peak_basis": "measured DFMA peak (thoi_fma_peak)",
                           "flops_model": "2/3k^3+2k^2 per evaluated nplet (evaluations "
                                          "spread evenly over the expanded orders)"}}
     if rank == 0 and not args.no_cpu:
@@ -587,9 +631,9 @@ def run_extra(args, dev, stream, flush, peak, rank):
                          f"({n_eval:,} FP64 energies)",
              "value": n_eval / (ms / 1e3), "unit": "nplets/s", "ms_per_call": ms,
              "best_O": float(max(bv)), "accepted": int(st.n_refactored),
-             "roofline": {"bound": "fp64", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",
-                          "frac": ach / 1.25,
-                          "peak_basis": "nominal GB300 FP64 (1.25 TFLOP/s)",
+             "roofline": {"bound": "fp64", "achieved": ach, "peak": fp64_peak,
+                          "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                          "peak_basis": "measured DFMA peak (thoi_fma_peak)",
                           "flops_model": f"2/3k^3+2k^2 per energy at the mean final order "
                                          f"{kbar:.1f}"}}
     if rank == 0 and not args.no_cpu:
@@ -692,10 +736,10 @@ def run_extra(args, dev, stream, flush, peak, rank):
 
     # per-nplet output (FP32 SoA, 20 B per nplet) at small orders, where the
     # stores outweigh the arithmetic (F(k) / 20 B is below the FP32 : HBM
-    # balance of about 12 FLOP/B for k <= 5): N = 64, orders 3..5, the nplet
+    # balance of about 12 FLOP/B for k <= 6): N = 64, orders 3..6, the nplet
     # kernels' CUDA-event time against the measured HBM bandwidth
     try:
-        Nv, orders_o = 64, [3, 4, 5]
+        Nv, orders_o = 64, [3, 4, 5, 6]
         rng = np.random.default_rng(7)
         Xo = rng.standard_normal((2000, Nv)) @ np.linalg.cholesky(
             workloads.random_corr(rng, Nv)).T
@@ -722,7 +766,7 @@ def run_extra(args, dev, stream, flush, peak, rank):
         byts = 20.0 * n
         ach = byts / (kms_avg / 1e3) / 1e9
         entry = {"workload": f"N=64, T=2000 random-correlation Gaussian (seed 7), per-nplet FP32 "
-                             f"output of orders 3..5 ({n:,} nplets, {byts / 1e6:.0f} MB)",
+                             f"output of orders 3..6 ({n:,} nplets, {byts / 1e6:.0f} MB)",
                  "value": n / (kms_avg / 1e3), "unit": "nplets/s",
                  "nplet_kernel_ms": kms_avg,
                  "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",

@@ -166,8 +166,14 @@ thoi_status thoi_create(thoi_ctx** out, const void* X, int64_t T, int64_t N, int
                         int32_t dtype, const thoi_options* opt, void* stream);
 
 /* Create a context from an explicit N x N covariance (host or device,
- * row-major FP64).  T_for_bias is the sample count used by the bias
- * corrector (ignored unless opt->bias_correct).  Synchronises `stream`. */
+ * row-major FP64): the Sigma the paper's estimators start from once the
+ * copula covariance is known (Methods, "Efficient computation of HOI via
+ * Gaussian copulas": the covariance is computed once and every entropy is a
+ * function of its submatrices, Supp. eq. gaussian_differential_entropy).
+ * Every diagonal entry must be positive and finite (THOI_ERR_INVALID_ARG
+ * otherwise).  T_for_bias is the sample count used by the bias corrector
+ * (Supp. eq. bias_corrector; ignored unless opt->bias_correct).  The caller
+ * may free Sigma once the call returns; synchronises `stream`. */
 thoi_status thoi_create_from_cov(thoi_ctx** out, const double* Sigma, int64_t N,
                                  int64_t T_for_bias, const thoi_options* opt, void* stream);
 
@@ -184,17 +190,26 @@ thoi_status thoi_get_ranks(thoi_ctx* ctx, int32_t* ranks, void* stream);
 /* Number of variables of the context. */
 int64_t thoi_n(const thoi_ctx* ctx);
 
-/* Exact number of nplets over the listed orders (host). */
+/* Exact number of nplets over the listed orders (host): the sum of the
+ * binomial coefficients C(N, k) of Supp. eq. comb ("The combinatorial
+ * explosion"), each exact in 64 bits for N <= 64.  An order outside 0..N
+ * adds nothing; returns 0 for N outside 1..THOI_MAX_N, a null list or
+ * n_orders < 1. */
 uint64_t thoi_count(int64_t N, const int32_t* orders, int32_t n_orders);
 
-/* Subset of a global id (host): writes k indices c_0 < ... < c_{k-1} to
- * idx_out (room for THOI_MAX_N) and k to *k_out. */
+/* Subset of a global id (host), in the enumeration order of Supp. eq. comb:
+ * the id picks the order by the prefix sums of C(N, k) over the listed
+ * orders, then the lexicographic rank r within order k gives the indices by
+ * the combinatorial number system, r = C(N,k) - 1 - sum_i C(N-1-c_i, k-i).
+ * Writes k indices c_0 < ... < c_{k-1} to idx_out (host, room for
+ * THOI_MAX_N) and k to *k_out.  THOI_ERR_INVALID_ARG for an id beyond the
+ * count, a bad order list or a null pointer. */
 thoi_status thoi_unrank(int64_t N, const int32_t* orders, int32_t n_orders, uint64_t id,
                         int32_t* idx_out, int32_t* k_out);
 
 /* Subsets of n global ids computed on the device with the kernels' own
- * unranking (combinatorial number system) -- exposed so the enumeration can
- * be checked.  ids: device u64[n]; idx_out: device int8[n * kmax], each row
+ * unranking (combinatorial number system of Supp. eq. comb, as in
+ * thoi_unrank) -- exposed so the enumeration can be checked.  ids: device u64[n]; idx_out: device int8[n * kmax], each row
  * holding the indices then -1 padding; kmax >= the largest listed order. */
 thoi_status thoi_unrank_device(int64_t N, const int32_t* orders, int32_t n_orders,
                                const uint64_t* ids, int64_t n, int32_t kmax, int8_t* idx_out,
@@ -207,7 +222,12 @@ thoi_status thoi_unrank_device(int64_t N, const int32_t* orders, int32_t n_order
 size_t thoi_records_bytes(int32_t n_orders, int32_t top_m);
 
 /* Evaluate the five measures of every nplet with global id in
- * [id_begin, id_end) (id_end = UINT64_MAX means all).
+ * [id_begin, id_end) (id_end = UINT64_MAX means all): H from Supp. eq.
+ * gaussian_differential_entropy on the submatrix Sigma_S, and TC, DTC, O,
+ * S from Methods eqs. TC, DTC, O-info, S-info, for all nplets in batches
+ * (Methods, "Parallel and batched computation of HOI"); with
+ * THOI_RED_PER_ORDER each order is reduced on the device instead of stored
+ * (Fig. 1A caption: a function applied per batch, e.g. the minimum O).
  *  orders  : host int32[n_orders], each 1 <= k <= N
  *  kind    : THOI_RED_NONE -- `out` is a device array of 5 x n values (SoA,
  *            out[m * n + (id - id_begin)]), FP32 or FP64 per opt.out_f64;
@@ -401,6 +421,16 @@ thoi_status thoi_group_anneal(thoi_ctx* const* ctxs, int32_t D, int32_t k_lo, in
                               uint64_t seed, uint64_t* final_masks, double* final_values,
                               uint64_t* best_masks, double* best_values, thoi_stats* stats,
                               void* stream);
+
+/* Measured multiply-add peak of the CUDA cores of the current device (not part
+ * of the method: it gives the roofline denominators of the FP32 nplet kernels
+ * and of the FP64 re-factor).  fp64 = 0 times FFMA, fp64 = 1 DFMA: every
+ * thread of a grid of 8 blocks of 256 threads per SM runs 8 independent
+ * multiply-add chains of 16 * iters steps; the second of two launches is
+ * timed with CUDA events on `stream`.  *tflops = 2 FLOP per multiply-add /
+ * time; *ms (optional) = that launch's time.  Allocates a few KB; synchronises
+ * `stream`.  THOI_ERR_INVALID_ARG for iters < 1 or a null tflops. */
+thoi_status thoi_fma_peak(int32_t fp64, int32_t iters, double* tflops, double* ms, void* stream);
 
 /* Host-only sharding helpers (no device work, no CUDA calls).  Nplets are
  * independent (Methods, "Parallel and batched computation of HOI"), so one

@@ -123,6 +123,8 @@ def load(build_if_missing: bool = True):
             "thoi_group_anneal": (ctypes.c_int, [vp, i32, i32, i32, i32, i32, ctypes.c_double,
                                                  ctypes.c_double, i32, i32, i32, i32, u64, vp,
                                                  vp, vp, vp, ctypes.POINTER(thoi_stats), vp]),
+            "thoi_fma_peak": (ctypes.c_int, [i32, i32, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), vp]),
             "thoi_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -499,6 +501,16 @@ def thoi_group_anneal(handles, k_lo: int, k_hi: int, n_chains: int, iters: int, 
 def thoi_autotune(h, kmin: int, kmax: int, cache_path: str | None = None, stream=None):
     _check(load().thoi_autotune(h, kmin, kmax, cache_path.encode() if cache_path else None,
                                 _stream_ptr(stream)), "thoi_autotune")
+
+
+def thoi_fma_peak(fp64: bool = False, iters: int | None = None, stream=None):
+    """Measured FFMA (fp64=False) or DFMA (fp64=True) peak of the current
+    device in TFLOP/s, and the timed launch's milliseconds."""
+    iters = iters or (50 if fp64 else 2000)
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().thoi_fma_peak(int(bool(fp64)), iters, ctypes.byref(t), ctypes.byref(ms),
+                                _stream_ptr(stream)), "thoi_fma_peak")
+    return t.value, ms.value
 
 
 def thoi_set_cancel(h, flag: bool):

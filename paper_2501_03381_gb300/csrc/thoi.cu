@@ -31,6 +31,10 @@ static thread_local char g_last_cuda[256];
 
 static thoi_status cuda_fail(cudaError_t e) {
   snprintf(g_last_cuda, sizeof g_last_cuda, "%s", cudaGetErrorString(e));
+  // reset the thread's last-error state, so that a failed call which leaves
+  // the context usable (an allocation refused) is not reported again by the
+  // cudaGetLastError check after a later launch
+  cudaGetLastError();
   if (e == cudaErrorMemoryAllocation) return THOI_ERR_OOM;
   return THOI_ERR_CUDA;
 }

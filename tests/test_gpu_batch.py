@@ -240,3 +240,72 @@ def test_batch_sequential_paths_match_single(case):
     finally:
         for c in ctxs:
             c.close()
+
+
+# ------------------------------------------------------------------ the 64-dataset workload at full size
+def _records_by_ids(S, N, orders, recs, hi, lo, tol):
+    """Every reported extreme and top-list id of every order re-evaluated by
+    the oracle at its id: the value stored beside it must match within tol."""
+    ids, want = [], []
+    for q, k in enumerate(orders):
+        r = recs[q]
+        for m in range(5):
+            ids += [int(r["argmin"][m]), int(r["argmax"][m])]
+            want += [(m, float(r["min"][m])), (m, float(r["max"][m]))]
+        n = int(r["top_count"])
+        for lst in (hi[q][:n], lo[q][:n]):
+            ids += [int(x) for x in lst["id"]]
+            want += [(3, float(v)) for v in lst["value"]]
+    vals, fl = oracle.measures_ids(S, orders, np.array(ids, dtype=np.uint64))
+    assert not fl.any()
+    got = np.array([v for _, v in want])
+    ref = np.array([vals[m, j] for j, (m, _) in enumerate(want)])
+    err = np.abs(got - ref).max()
+    assert err <= tol, err
+
+
+def test_multi64_full_size_matches_single_contexts_and_oracle():
+    # the 64-dataset workload exactly as the bench runs it (N ~ U{10..40},
+    # T ~ U{200..2000}, orders 3..min(N, 8), top-256 lists, one replayed
+    # graph): records identical to one context at a time with the built-in
+    # (dense) kernels, which share the batch kernel's arithmetic, and every
+    # reported id's value confirmed by the oracle
+    Xs, ords = workloads.multi64()
+    kmin, kmax, top_m = 3, 8, 256
+    ctxs = [_ctx(X, top_m=top_m, autotune=False) for X in Xs]
+    try:
+        res, st = P.thoi_batch_measures([c.h for c in ctxs], kmin, kmax, top_m=top_m)
+        assert st.nplets == sum(oracle.count(X.shape[1], o) for X, o in zip(Xs, ords))
+        for X, o, c, got in zip(Xs, ords, ctxs, res):
+            (recs, hi, lo), _ = c.measures(o, reduction="per_order")
+            nq = len(o)
+            _records_equal((got[0][:nq], got[1][:nq], got[2][:nq]), (recs, hi, lo))
+            for q in range(nq, kmax - kmin + 1):  # orders above N_d
+                assert int(got[0][q]["count"]) == 0
+            S = oracle.copula_cov(X)
+            _records_by_ids(S, X.shape[1], o, got[0][:nq], got[1][:nq], got[2][:nq], TOL32)
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_multi64_full_size_forced_refactor():
+    # every nplet of the 64 datasets flagged (trace_tau below 1): all values
+    # from the batched FP64 re-factor, confirmed by the oracle at 1e-10
+    Xs, ords = workloads.multi64()
+    kmin, kmax, top_m = 3, 8, 16
+    ctxs = [_ctx(X, top_m=top_m, trace_tau=0.5,
+                 flag_capacity=max(math.comb(X.shape[1], k) for k in o))
+            for X, o in zip(Xs, ords)]
+    try:
+        res, st = P.thoi_batch_measures([c.h for c in ctxs], kmin, kmax, top_m=top_m)
+        assert st.n_refactored == st.nplets
+        for X, o, (recs, hi, lo) in zip(Xs, ords, res):
+            nq = len(o)
+            for q, k in enumerate(o):
+                assert int(recs[q]["n_refactored"]) == math.comb(X.shape[1], k)
+            S = oracle.copula_cov(X)
+            _records_by_ids(S, X.shape[1], o, recs[:nq], hi[:nq], lo[:nq], TOL64)
+    finally:
+        for c in ctxs:
+            c.close()

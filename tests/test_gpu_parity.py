@@ -65,6 +65,25 @@ def test_nonfinite_input_rejected():
     assert e.value.name == "THOI_ERR_NONFINITE_INPUT"
 
 
+def test_failed_allocation_returns_oom_and_device_stays_usable():
+    # a re-factor list of 2^40 entries (8 TiB) cannot be allocated: cudaMalloc
+    # refuses it at once and the call returns THOI_ERR_OOM with nothing
+    # queued; the context still answers, and a context with an automatic
+    # list then evaluates normally
+    X, orders = workloads.small()
+    S = oracle.copula_cov(X)
+    ref, _ = oracle.measures(S, orders)
+    with _ctx(X, flag_capacity=1 << 40) as c:
+        with pytest.raises(P.ThoiError) as e:
+            c.measures(orders)
+        assert e.value.name == "THOI_ERR_OOM"
+        S64, _ = c.cov()
+        assert np.abs(S64 - S).max() < 1e-12
+    with _ctx(X) as c:
+        out, _ = c.measures(orders)
+        assert np.abs(out.double().cpu().numpy() - ref).max() < TOL32
+
+
 # ------------------------------------------------------------------ enumeration
 @pytest.mark.parametrize("N", [1, 6, 13, 20])
 def test_device_unrank_all_ids(N):
