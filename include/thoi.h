@@ -84,6 +84,20 @@ typedef enum {
   THOI_SIGMA32_FROM_F64 = 1    /* FP32 rounding of the FP64 covariance */
 } thoi_sigma32_source;
 
+/* How the FP32 path forms per-order records (thoi_measures with
+ * THOI_RED_PER_ORDER).  Fused: the nplet kernels keep the sums and the count
+ * of O < 0 per thread and list only the nplets beyond bounds taken from a
+ * sample of the order, so no per-nplet value reaches device memory; the
+ * merge certifies every extreme and top list against the bounds, and an
+ * uncertified record repeats the request with stored values (the result is
+ * the same either way).  Stored: every nplet's three basis values are
+ * written and reduced by a streaming kernel. */
+typedef enum {
+  THOI_RECORDS_AUTO = 0,   /* fused for orders of at least 2^20 nplets (k <= 32), else stored */
+  THOI_RECORDS_FUSED = 1,  /* fused for every order with k <= 32 */
+  THOI_RECORDS_STORED = 2  /* always stored basis values */
+} thoi_records_mode;
+
 /* Options; fill with thoi_default_options() and change what you need. */
 typedef struct {
   int32_t precision;     /* thoi_precision; default THOI_F32_FIX64 */
@@ -104,7 +118,7 @@ typedef struct {
   uint64_t flag_capacity;/* entries of the FP64 re-factor list; 0 = automatic */
   int32_t profile;       /* 1: time the kernels with CUDA events on `stream` and report
                             the times in thoi_stats; default 0 */
-  int32_t reserved;
+  int32_t records_mode;  /* thoi_records_mode; default THOI_RECORDS_AUTO */
 } thoi_options;
 
 /* Per-order reduction record (Fig. 1A caption: a function applied to every
@@ -144,7 +158,12 @@ typedef struct {
   double nplet_ms;
   double refactor_ms;
   double merge_ms;
-  double reduce_ms;      /* the streaming per-order reduction of the FP32 path */
+  double reduce_ms;      /* the per-order reduction kernels of the FP32 path (streaming
+                            reduction, or the sample bounds and candidate list of
+                            fused records) */
+  int32_t fused_retries; /* 1 when fused records could not be certified and the
+                            request was repeated with stored values */
+  int32_t pad2;
 } thoi_stats;
 
 /* Fill `opt` with the defaults listed above. */

@@ -30,6 +30,7 @@ THOI_F32_FIX64, THOI_F64 = 0, 1
 THOI_RED_NONE, THOI_RED_PER_ORDER = 0, 1
 THOI_DTYPE_F32, THOI_DTYPE_F64 = 0, 1
 THOI_SIGMA32_TENSORCORE, THOI_SIGMA32_FROM_F64 = 0, 1
+RECORDS_MODES = ("auto", "fused", "stored")  # thoi_records_mode
 GROUP_OBJECTIVES = ("mean", "cohen_d")  # thoi_group_objective
 STATUS = {0: "THOI_OK", 1: "THOI_ERR_INVALID_ARG", 2: "THOI_ERR_NONFINITE_INPUT",
           3: "THOI_ERR_TOO_LARGE", 4: "THOI_ERR_NOT_PD", 5: "THOI_ERR_OOM", 6: "THOI_ERR_CUDA",
@@ -49,7 +50,7 @@ class thoi_options(ctypes.Structure):
                 ("top_m", ctypes.c_int32), ("out_f64", ctypes.c_int32),
                 ("sigma32_source", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("flag_capacity", ctypes.c_uint64), ("profile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("records_mode", ctypes.c_int32)]
 
 
 class thoi_stats(ctypes.Structure):
@@ -57,7 +58,8 @@ class thoi_stats(ctypes.Structure):
                 ("n_not_pd", ctypes.c_uint64), ("launches", ctypes.c_int32),
                 ("pad", ctypes.c_int32), ("nplet_ms", ctypes.c_double),
                 ("refactor_ms", ctypes.c_double), ("merge_ms", ctypes.c_double),
-                ("reduce_ms", ctypes.c_double)]
+                ("reduce_ms", ctypes.c_double), ("fused_retries", ctypes.c_int32),
+                ("pad2", ctypes.c_int32)]
 
 
 RECORD_DTYPE = np.dtype([("k", "<i4"), ("top_count", "<i4"), ("count", "<u8"),
@@ -176,7 +178,8 @@ def make_options(precision: str | int = "f32_fix64", pivot_tau: float | None = N
                  trace_tau: float | None = None, bias_correct: bool = False,
                  top_m: int | None = None, out_f64: bool | None = None,
                  sigma32_source: str | int = "from_f64", autotune: bool = True,
-                 flag_capacity: int = 0, profile: bool = False) -> thoi_options:
+                 flag_capacity: int = 0, profile: bool = False,
+                 records_mode: str | int = "auto") -> thoi_options:
     o = thoi_options()
     load().thoi_default_options(ctypes.byref(o))
     if isinstance(precision, str):
@@ -198,6 +201,8 @@ def make_options(precision: str | int = "f32_fix64", pivot_tau: float | None = N
     o.autotune = int(bool(autotune))
     o.flag_capacity = flag_capacity
     o.profile = int(bool(profile))
+    o.records_mode = (records_mode if isinstance(records_mode, int)
+                      else RECORDS_MODES.index(records_mode))
     return o
 
 

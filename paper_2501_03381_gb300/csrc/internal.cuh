@@ -21,8 +21,18 @@ enum : int {
   ST_NONFINITE = 4,
   ST_CANCELLED = 8,
   ST_TIMEOUT = 16,
-  ST_BAD_ARG = 32
+  ST_BAD_ARG = 32,
+  ST_CAND_OVERFLOW = 64,  // fused records: more candidates than the list holds
+  ST_INEXACT = 128        // fused records: a reduced value could not be certified
 };
+
+// Fused per-order records (nplet mode 3): ten thresholds per order slot, kept
+// as order-preserving 32-bit keys.  Slot m (0..4) bounds measure m from
+// above ("a nplet with a value at or below it is a candidate for the
+// minimum"), slot 5 + m from below (candidates for the maximum); for the
+// measure the top lists rank, slot m and 5 + m bound the smallest and the
+// largest top lists instead.  A key of 0 means "no bound".
+constexpr int FUSE_NTHR = 10;
 
 // One block's partial reduction over one launch (one order).  Values are
 // widened to double; ids are global ids.
@@ -73,9 +83,17 @@ struct NpletArgs {
   int out_sel;          // mode 0: 0 = the five measures (SoA); m + 1 = measure m alone (one row)
   unsigned long long out_n;      // stride between measures in `out`
   unsigned long long out_first;  // global id stored at out index 0
-  PartRec* part;        // mode 1: [gridDim.x]
+  PartRec* part;        // mode 1 and 3: [gridDim.x]
   TopEnt* part_top;     // mode 1: [gridDim.x][2][top_m]
   int top_m;
+  // mode 3 (fused records): thresholds of this order slot (FUSE_NTHR keys),
+  // and the candidate list the kernel appends to (ids; three FP32 arrays of
+  // log det R_S, sum_j log p_j, sum_i log Sigma_ii at cand_b[m * cand_cap + e])
+  const unsigned* thr_keys;
+  unsigned long long* cand_ids;
+  float* cand_b;
+  unsigned long long* cand_count;
+  unsigned long long cand_cap;
   // FP64 re-factor list (FP32 kernels append; the re-factor kernel reads)
   unsigned long long* flag_ids;
   unsigned long long* flag_count;
@@ -142,6 +160,16 @@ cudaError_t launch_reduce_basis64(const double* basis, unsigned long long stride
                                   unsigned long long n, unsigned long long id0, Combine cmb,
                                   int top_m, PartRec* part, TopEnt* part_top, int num_sms,
                                   int max_blocks, cudaStream_t s, int* grid_out);
+// Fused records of one order slot: the starting thresholds from a sample of
+// the slot's nplets (FP32, every sampled nplet evaluated directly; keys added
+// with atomicMax into thr_keys, which must be zero beforehand) ...
+cudaError_t launch_fused_sample(const NpletArgs& a, int num_sms, cudaStream_t s);
+// ... and, after the nplet launch, the reduction of the candidate list into
+// per-block partials holding the extremes and top lists only; block 0 also
+// carries the count of FP32 nplets (rank range minus the flagged ones).
+cudaError_t launch_reduce_candidates(const NpletArgs& a, int num_sms, int max_blocks,
+                                     PartRec* part, TopEnt* part_top, cudaStream_t s,
+                                     int* grid_out);
 cudaError_t launch_reduce_list64(const double* basis, unsigned long long stride_elems,
                                  const unsigned long long* ids, const unsigned long long* count,
                                  unsigned long long cap, Combine cmb, int top_m, PartRec* part,
@@ -171,6 +199,10 @@ struct MergeDesc {
   int pad;
   Combine cmb;
   const unsigned long long* refactored;  // device counter of re-factored nplets (or null)
+  // fused records: the slot's threshold keys (null otherwise); the merge
+  // certifies the record against them and raises ST_INEXACT in *status
+  const unsigned* thr_keys;
+  int* status;
 };
 constexpr int MAX_SLOTS = 64;
 struct MergeDescs {

@@ -429,9 +429,53 @@ __device__ void top_write(const TopBuf<V, I>& tb, int M, unsigned long long id_o
   }
 }
 
+// ---------------------------------------------------------------- fused records (mode 3)
+// The per-order reduction done inside the nplet kernels.  Before the order's
+// nplet launch a sample kernel bounds every extreme from a sample of the
+// order's nplets (the sample's minimum and maximum of each measure, and for
+// the ranked measure the smallest block maximum and the largest block
+// minimum, so that at least one sampled nplet per sample block lies beyond
+// each top-list bound).  The nplet kernel then keeps per thread only the
+// compensated sums and the count of O < 0, and appends to a candidate list
+// the nplets that lie beyond a bound; the list is reduced like a re-factor
+// list.  Every bound is widened by a margin above the FP32 error of a nplet,
+// and the merge certifies the final record against the bounds (an extreme
+// inside a bound, or a full top list ending beyond it, shows that no nplet
+// left off the list could change the record); a record that cannot be
+// certified makes the host repeat the order with stored basis values.
+__device__ __forceinline__ unsigned fkey32(float v) {
+  unsigned u = __float_as_uint(v);
+  if ((u << 1) == 0) u = 0;
+  return (u >> 31) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey32_value(unsigned k) {
+  return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
+}
+// Whether threshold slot j stores the complement of its key (so that every
+// slot is aggregated with atomicMax): the minima of the measures and the
+// largest-side top bound (a minimum over sample blocks).
+__host__ __device__ __forceinline__ bool fused_slot_negated(int j, int top) {
+  return j < 5 ? (j != top) : (j - 5 == top);
+}
+// Margin added to a bound: a sampled nplet evaluated by another FP32 kernel
+// than the one that evaluates it in the order's pass may differ by twice the
+// FP32 error of a nplet (at most 1e-4 nats each for the nplets the FP32 path
+// keeps), so 5e-4 plus a relative 4e-6 keeps the sampled witnesses beyond
+// the bound.
+__host__ __device__ __forceinline__ float fused_margin(float t) {
+  return 5e-4f + 4e-6f * fabsf(t);
+}
+// Slot j's bound as a float, widened; a missing bound admits everything.
+__device__ __forceinline__ float fused_threshold(unsigned key, int j, int top) {
+  const bool le = j < 5;
+  if (key == 0u) return le ? pinf<float>() : -pinf<float>();
+  const float t = fkey32_value(fused_slot_negated(j, top) ? ~key : key);
+  return le ? t + fused_margin(t) : t - fused_margin(t);
+}
+
 // ---------------------------------------------------------------- shared memory layout
 struct SmemLayout {
-  size_t binom, R, ls, tv0, tv1, ti0, ti1, total;
+  size_t binom, R, ls, thr, tv0, tv1, ti0, ti1, total;
 };
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline SmemLayout smem_layout(int N, int k, int ldr, size_t vsz, size_t isz,
@@ -441,6 +485,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int k, int ldr, size_t 
   L.binom = o; o = align16(o + (size_t)(N + 1) * (size_t)(k + 1) * 8);
   L.R = o;     o = align16(o + (size_t)N * (size_t)ldr * vsz);
   L.ls = o;    o = align16(o + (size_t)N * vsz);
+  L.thr = o;   o = align16(o + (size_t)FUSE_NTHR * sizeof(float));
   if (with_top) {
     L.tv0 = o; o = align16(o + TOP_CAP * vsz);
     L.tv1 = o; o = align16(o + TOP_CAP * vsz);
@@ -467,6 +512,9 @@ __device__ void load_tables(const NpletArgs& a, unsigned char* smem, const SmemL
     sb[q] = a.binom[(q / bs) * NB + (q % bs)];
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) sR[(q / N) * ldr + (q % N)] = Rg[q];
   for (int q = threadIdx.x; q < N; q += blockDim.x) sls[q] = (V)a.ls[q];
+  if (a.mode == 3 && threadIdx.x < FUSE_NTHR)
+    reinterpret_cast<float*>(smem + L.thr)[threadIdx.x] =
+        fused_threshold(a.thr_keys[threadIdx.x], threadIdx.x, a.cmb.top);
   __syncthreads();
 }
 
@@ -523,6 +571,119 @@ __device__ __forceinline__ void store5(const NpletArgs& a, unsigned long long gi
     float* O = reinterpret_cast<float*>(a.out);
 #pragma unroll
     for (int m = 0; m < 5; m++) O[(size_t)m * a.out_n + o] = (float)v[m];
+  }
+}
+
+// ---------------------------------------------------------------- fused records: per nplet
+// Per-thread state of the fused records: compensated FP32 sums of the three
+// basis values and the count of O < 0 over the nplets the FP32 path keeps.
+struct FusedAcc {
+  float slr, ssp, sls, clr, csp, cls;
+  unsigned neg;
+  __device__ __forceinline__ void init() {
+    slr = ssp = sls = clr = csp = cls = 0.f;
+    neg = 0;
+  }
+  __device__ __forceinline__ static void kahan(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// Warp-aggregated append of one nplet (id and basis values) to the
+// candidate list; overflow raises ST_CAND_OVERFLOW (the order is then redone
+// with stored basis values).
+__device__ __forceinline__ void cand_append(const NpletArgs& a, bool cand, unsigned long long gid,
+                                            float lr, float sp, float lsum) {
+  const unsigned act = __activemask();
+  const unsigned fl = __ballot_sync(act, cand);
+  if (!fl) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(fl) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(a.cand_count, (unsigned long long)__popc(fl));
+  if (cand) {
+    base = __shfl_sync(fl, base, leader);
+    const unsigned long long pos = base + __popc(fl & ((1u << lane) - 1u));
+    if (pos < a.cand_cap) {
+      a.cand_ids[pos] = gid;
+      a.cand_b[pos] = lr;
+      a.cand_b[a.cand_cap + pos] = sp;
+      a.cand_b[2 * a.cand_cap + pos] = lsum;
+    } else {
+      atomicOr(a.status, ST_CAND_OVERFLOW);
+    }
+  }
+}
+
+// One nplet in mode 3: sums and count of O < 0 when the FP32 value is kept,
+// candidate test against the block's bounds (sthr, shared memory), and the
+// FP64 re-factor list for a flagged nplet.
+__device__ __forceinline__ void fused_emit(const NpletArgs& a, FusedAcc& acc, const float* sthr,
+                                           const CombineV<float>& cv, unsigned long long gid,
+                                           float lr, float sp, float lsum, bool bad) {
+  bool cand = false;
+  if (!bad) {
+    float v[5];
+    combine5<float>(lr, sp, lsum, cv, v);
+    FusedAcc::kahan(acc.slr, acc.clr, lr);
+    FusedAcc::kahan(acc.ssp, acc.csp, sp);
+    FusedAcc::kahan(acc.sls, acc.cls, lsum);
+    acc.neg += v[3] < 0.f ? 1u : 0u;
+#pragma unroll
+    for (int m = 0; m < 5; m++) cand |= (v[m] <= sthr[m]) | (v[m] >= sthr[5 + m]);
+  }
+  cand_append(a, cand, gid, lr, sp, lsum);
+  flag_append(a, bad, gid);
+}
+
+// End of a mode-3 kernel (every thread of the block): the block's sums and
+// count of O < 0 into its partial record; extremes and top lists stay empty
+// (they come from the candidate list) and the count is carried by the
+// candidate reduction.
+__device__ inline void fused_block_end(const NpletArgs& a, const FusedAcc& acc) {
+  __shared__ double s_sum[RED_NT / 32][3];
+  __shared__ unsigned s_neg[RED_NT / 32];
+  double x0 = (double)acc.slr - (double)acc.clr, x1 = (double)acc.ssp - (double)acc.csp,
+         x2 = (double)acc.sls - (double)acc.cls;
+  unsigned ng = acc.neg;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x0 += __shfl_xor_sync(0xffffffffu, x0, o);
+    x1 += __shfl_xor_sync(0xffffffffu, x1, o);
+    x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+    ng += __shfl_xor_sync(0xffffffffu, ng, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_sum[w][0] = x0;
+    s_sum[w][1] = x1;
+    s_sum[w][2] = x2;
+    s_neg[w] = ng;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    PartRec r;
+    for (int m = 0; m < 5; m++) {
+      r.vmin[m] = pinf<double>();
+      r.vmax[m] = -pinf<double>();
+      r.imin[m] = r.imax[m] = ~0ull;
+    }
+    r.s_lr = r.s_sp = r.s_ls = 0.0;
+    unsigned long long neg = 0;
+    for (int q = 0; q < RED_NT / 32; q++) {
+      r.s_lr += s_sum[q][0];
+      r.s_sp += s_sum[q][1];
+      r.s_ls += s_sum[q][2];
+      neg += s_neg[q];
+    }
+    r.count = 0;
+    r.neg = neg;
+    r.notpd = 0;
+    r.top_hi = r.top_lo = 0;
+    a.part[blockIdx.x] = r;
   }
 }
 

@@ -187,6 +187,125 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_gen(const NpletArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- fused records: sample bounds
+// Bounds of one order slot's extremes from a sample of its nplets (see the
+// fused-records notes in nplet_common.cuh).  Sample i of S = min(n, grid *
+// FS_NT * FS_PER) is the nplet of rank rank_begin + floor(i n / S); block b
+// takes samples b, b + grid, b + 2 grid, ..., so every block spreads over the
+// whole range.  Each sample is evaluated in FP32 by the generic routine; a
+// sample the FP32 path would flag is skipped.  Block minima and maxima go
+// into the slot's keys with atomicMax (complemented keys where the slot wants
+// a minimum): the measures' global minima and maxima, and for the ranked
+// measure the largest block minimum and the smallest block maximum.
+constexpr int FS_NT = 128;
+constexpr int FS_PER = 8;
+
+template <int KMAX, typename M>
+__global__ void __launch_bounds__(FS_NT) k_fused_sample(const NpletArgs a, unsigned long long S,
+                                                        unsigned* __restrict__ keys) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float s_mn[FS_NT / 32][5], s_mx[FS_NT / 32][5];
+  __shared__ unsigned s_valid[FS_NT / 32];
+  const int N = a.N, k = a.k, ldr = row_stride(N);
+  const SmemLayout L = smem_layout(N, k, ldr, sizeof(float), sizeof(unsigned), 0);
+  load_tables<float>(a, smem, L, a.R32);
+  const unsigned long long* sb = reinterpret_cast<const unsigned long long*>(smem + L.binom);
+  const float* sR = reinterpret_cast<const float*>(smem + L.R);
+  const float* sls = reinterpret_cast<const float*>(smem + L.ls);
+  const unsigned long long n = a.rank_end - a.rank_begin;
+  const unsigned long long q = n / S, rem = n % S;
+  const CombineV<float> cv(a.cmb);
+  float mn[5], mx[5];
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    mn[m] = pinf<float>();
+    mx[m] = -pinf<float>();
+  }
+  unsigned valid = 0;
+  float A[KMAX * (KMAX + 1) / 2];
+  for (int e = 0; e < FS_PER; e++) {
+    const unsigned long long i =
+        ((unsigned long long)threadIdx.x * FS_PER + e) * gridDim.x + blockIdx.x;
+    if (i >= S) continue;
+    const unsigned long long r = a.rank_begin + i * q + (i * rem) / S;
+    const M mask = unrank_s<M>(r, k, N, sb, k + 1);
+    float lsum, lr, sp, pmin, trace;
+    bool bad = false;
+    gather_gen<float, M>(mask, k, N, sR, ldr, sls, A, lsum);
+    chol_loo_gen<float>(A, k, lr, sp, pmin, trace, bad);
+    bad |= !(pmin >= a.tau_piv) | !(trace <= a.tau_tr);
+    if (bad) continue;
+    float v[5];
+    combine5<float>(lr, sp, lsum, cv, v);
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+      mn[m] = fminf(mn[m], v[m]);
+      mx[m] = fmaxf(mx[m], v[m]);
+    }
+    valid++;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+      mn[m] = fminf(mn[m], __shfl_xor_sync(0xffffffffu, mn[m], o));
+      mx[m] = fmaxf(mx[m], __shfl_xor_sync(0xffffffffu, mx[m], o));
+    }
+    valid += __shfl_xor_sync(0xffffffffu, valid, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+      s_mn[w][m] = mn[m];
+      s_mx[w][m] = mx[m];
+    }
+    s_valid[w] = valid;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned nv = 0;
+    for (int q2 = 0; q2 < FS_NT / 32; q2++) {
+      nv += s_valid[q2];
+      for (int m = 0; m < 5; m++) {
+        mn[m] = fminf(mn[m], s_mn[q2][m]);
+        mx[m] = fmaxf(mx[m], s_mx[q2][m]);
+      }
+    }
+    if (nv > 0) {
+      const int top = a.cmb.top;
+      for (int m = 0; m < 5; m++) {
+        const unsigned klo = fkey32(mn[m]), khi = fkey32(mx[m]);
+        atomicMax(&keys[m], fused_slot_negated(m, top) ? ~klo : klo);
+        atomicMax(&keys[5 + m], fused_slot_negated(5 + m, top) ? ~khi : khi);
+      }
+    }
+  }
+}
+
+cudaError_t launch_fused_sample(const NpletArgs& a0, int num_sms, cudaStream_t s) {
+  (void)num_sms;
+  NpletArgs a = a0;
+  a.mode = 0;  // the sample kernel reads no bounds
+  const unsigned long long n = a.rank_end - a.rank_begin;
+  if (n == 0) return cudaSuccess;
+  const int grid = a.top_m > 256 ? a.top_m : 256;
+  const unsigned long long cap = (unsigned long long)grid * FS_NT * FS_PER;
+  const unsigned long long S = n < cap ? n : cap;
+  const SmemLayout L = smem_layout(a.N, a.k, row_stride(a.N), sizeof(float), sizeof(unsigned), 0);
+  void (*fn)(const NpletArgs, unsigned long long, unsigned*);
+  const bool wide = a.N > 32;
+  if (a.k <= 8) fn = wide ? k_fused_sample<8, unsigned long long> : k_fused_sample<8, unsigned>;
+  else if (a.k <= 16) fn = wide ? k_fused_sample<16, unsigned long long> : k_fused_sample<16, unsigned>;
+  else if (a.k <= 32) fn = wide ? k_fused_sample<32, unsigned long long> : k_fused_sample<32, unsigned>;
+  else return cudaErrorInvalidValue;
+  int occ = 0;
+  cudaError_t e = occupancy_cached((const void*)fn, FS_NT, L.total, &occ);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, FS_NT, L.total, s>>>(a, S, const_cast<unsigned*>(a0.thr_keys));
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- merge
 // One block per order slot: fold the FP32 partials and the FP64 partials (in
 // block order), merge the sorted top lists pairwise by (value, id), and
@@ -305,7 +424,8 @@ __device__ void merge_slot(const MergeDesc& d, const PartRec* __restrict__ p32ba
   for (int b = threadIdx.x; b < G; b += MERGE_NT) {
     const PartRec& P = b < g32 ? p32[b] : p64[b - g32];
     npd += P.notpd;
-    if (P.count == 0) continue;
+    // a partial without nplets holds +-inf extremes with id ~0, which never
+    // win; the candidate partials of fused records carry extremes only
     for (int m = 0; m < 5; m++) {
       kpick_min(vmn[m], imn[m], P.vmin[m], P.imin[m]);
       kpick_max(vmx[m], imx[m], P.vmax[m], P.imax[m]);
@@ -368,6 +488,16 @@ __device__ void merge_slot(const MergeDesc& d, const PartRec* __restrict__ p32ba
       if (!total) R.mean[m] = 0.0;
     }
     *rec = R;
+    if (d.thr_keys && total) {
+      // fused records: every extreme must lie within its bound, so that no
+      // nplet left off the candidate list could have replaced it
+      bool ok = true;
+      for (int m = 0; m < 5; m++) {
+        ok &= R.min[m] <= (double)fused_threshold(d.thr_keys[m], m, cmb.top);
+        ok &= R.max[m] >= (double)fused_threshold(d.thr_keys[5 + m], 5 + m, cmb.top);
+      }
+      if (!ok) atomicOr(d.status, ST_INEXACT);
+    }
   }
   // 2) top lists
   if (top_m <= 0) return;
@@ -513,6 +643,25 @@ __device__ void merge_slot(const MergeDesc& d, const PartRec* __restrict__ p32ba
       top_out[(size_t)side * top_m + q] = e;
     }
     __syncthreads();
+  }
+  if (d.thr_keys && threadIdx.x == 0) {
+    // fused records: a list must hold min(count, M) entries, and a list of
+    // M entries must end beyond its bound (every nplet off the candidate list
+    // lies strictly inside the bound, so it could not have entered)
+    const unsigned long long want = total < (unsigned long long)top_m ? total : top_m;
+    bool ok = true;
+    for (int side = 0; side < 2; side++) {
+      const TopEnt* Lst = top_out + (size_t)side * top_m;
+      unsigned long long have = 0;
+      for (int q = 0; q < top_m; q++) have += Lst[q].id != ~0ull ? 1ull : 0ull;
+      ok &= have >= want;
+      if (total > (unsigned long long)top_m && have >= (unsigned long long)top_m) {
+        const int j = side == 0 ? 5 + cmb.top : cmb.top;
+        const double t = (double)fused_threshold(d.thr_keys[j], j, cmb.top);
+        ok &= side == 0 ? Lst[top_m - 1].v >= t : Lst[top_m - 1].v <= t;
+      }
+    }
+    if (!ok) atomicOr(d.status, ST_INEXACT);
   }
 }
 

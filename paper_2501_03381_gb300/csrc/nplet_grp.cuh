@@ -119,6 +119,10 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_grp(const NpletArgs a, const i
   const float* sR = reinterpret_cast<const float*>(smem + L.R);
   const float* sls = reinterpret_cast<const float*>(smem + L.ls);
   const bool basis = a.mode == 2;
+  const bool fused = a.mode == 3;
+  const float* sthr = reinterpret_cast<const float*>(smem + L.thr);
+  FusedAcc acc;
+  acc.init();
   const int lane = threadIdx.x & 31;
   const int g = lane % G;
   const int gbase = lane - g;
@@ -182,18 +186,23 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_grp(const NpletArgs a, const i
       bad |= !(pmin >= tau_piv) | !(trace <= tau_tr);
       if (leader) {
         const unsigned long long gid = a.id_base + r0 + jn;
-        if (basis) {
-          store_basis(a, gid, lr, sp, lsum, bad);
+        if (fused) {
+          fused_emit(a, acc, sthr, cmbv, gid, lr, sp, lsum, bad);
         } else {
-          float v[5];
-          combine5<float>(lr, sp, lsum, cmbv, v);
-          store5<float>(a, gid, v);
+          if (basis) {
+            store_basis(a, gid, lr, sp, lsum, bad);
+          } else {
+            float v[5];
+            combine5<float>(lr, sp, lsum, cmbv, v);
+            store5<float>(a, gid, v);
+          }
+          flag_append(a, bad, gid);
         }
-        flag_append(a, bad, gid);
       }
       if (jn + 1 < cnt) mask = lex_succ(mask, full);
     }
   }
+  if (fused) fused_block_end(a, acc);
 }
 
 template <int K, int G, typename M>

@@ -43,6 +43,10 @@ __global__ void __launch_bounds__(RED_NT, PfxBlocks<K>::value) k_nplet_pfx(const
   const float* sls = reinterpret_cast<const float*>(smem + L.ls);
   constexpr int bs = K + 1;
   const bool basis = a.mode == 2;
+  const bool fused = a.mode == 3;
+  const float* sthr = reinterpret_cast<const float*>(smem + L.thr);
+  FusedAcc acc;
+  acc.init();
   const unsigned long long T = binom_s(sb, bs, N - 1, P);  // prefixes (largest index <= N-2)
   const unsigned long long NK = binom_s(sb, bs, N, K);
   const unsigned long long nch = (T + chunk - 1) / chunk;
@@ -174,14 +178,18 @@ __global__ void __launch_bounds__(RED_NT, PfxBlocks<K>::value) k_nplet_pfx(const
         const float lsum = lsp + sls[cl];
         bad |= !(fminf(pmin, Dn) >= tau_piv) | !(trace <= tau_tr);
         const unsigned long long gid = a.id_base + r0 + (unsigned long long)(cl - m - 1);
-        if (basis) {
-          store_basis(a, gid, lr, sp, lsum, bad);
+        if (fused) {
+          fused_emit(a, acc, sthr, cmbv, gid, lr, sp, lsum, bad);
         } else {
-          float v[5];
-          combine5<float>(lr, sp, lsum, cmbv, v);
-          store5<float>(a, gid, v);
+          if (basis) {
+            store_basis(a, gid, lr, sp, lsum, bad);
+          } else {
+            float v[5];
+            combine5<float>(lr, sp, lsum, cmbv, v);
+            store5<float>(a, gid, v);
+          }
+          flag_append(a, bad, gid);
         }
-        flag_append(a, bad, gid);
       }
       // next prefix: lexicographic successor inside the group, or the first
       // prefix of the next group
@@ -199,6 +207,7 @@ __global__ void __launch_bounds__(RED_NT, PfxBlocks<K>::value) k_nplet_pfx(const
       }
     }
   }
+  if (fused) fused_block_end(a, acc);
 }
 
 template <int K, typename M>

@@ -42,6 +42,10 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
   const float* sls = reinterpret_cast<const float*>(smem + L.ls);
   constexpr int bs = K + 1;
   const bool basis = a.mode == 2;
+  const bool fused = a.mode == 3;
+  const float* sthr = reinterpret_cast<const float*>(smem + L.thr);
+  FusedAcc acc;
+  acc.init();
   const unsigned long long T = binom_s(sb, bs, N - 2, GP);  // grand prefixes (largest <= N-3)
   const unsigned long long NK = binom_s(sb, bs, N, K);
   const unsigned long long nch = (T + chunk - 1) / chunk;
@@ -203,6 +207,10 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
         auto emit = [&](const int cl, const float lr, const float sp, const float lsum,
                         const bool bad) {
           const unsigned long long gid = a.id_base + r0 + (unsigned long long)(cl - am - 1);
+          if (fused) {
+            fused_emit(a, acc, sthr, cmbv, gid, lr, sp, lsum, bad);
+            return;
+          }
           if (basis) {
             store_basis(a, gid, lr, sp, lsum, bad);
           } else {
@@ -246,6 +254,7 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
       }
     }
   }
+  if (fused) fused_block_end(a, acc);
 }
 
 template <int K, typename M, bool PAIR>

@@ -92,7 +92,8 @@ __device__ __forceinline__ void nplet_reg_one(M mask, int N, const float* sR, in
 // neighbouring threads hold neighbouring nplets, which share most indices,
 // so their shared-memory gathers mostly hit the same words.  Output: mode 0
 // writes the five measures per nplet, mode 2 the three basis values that the
-// streaming reduction consumes; flagged nplets go to the FP64 re-factor list.
+// streaming reduction consumes, mode 3 reduces in place (fused records);
+// flagged nplets go to the FP64 re-factor list.
 // Minimum resident blocks per SM, picked per order by timing: orders up to
 // 16 are held to three blocks (at most 168 registers a thread), 18..20 to two;
 // order 17 keeps the allocation the compiler picks on its own (three blocks
@@ -114,6 +115,10 @@ __global__ void __launch_bounds__(RED_NT, RegBlocks<K>::value) k_nplet_reg(const
   const float* sR = reinterpret_cast<const float*>(smem + L.R);
   const float* sls = reinterpret_cast<const float*>(smem + L.ls);
   const bool basis = a.mode == 2;
+  const bool fused = a.mode == 3;
+  const float* sthr = reinterpret_cast<const float*>(smem + L.thr);
+  FusedAcc acc;
+  acc.init();
   const M full = (N >= (int)(8 * sizeof(M))) ? ~(M)0 : (((M)1 << N) - 1);
   const unsigned long long n = a.rank_end - a.rank_begin;
   const unsigned long long nch = (n + chunk - 1) / chunk;
@@ -138,17 +143,22 @@ __global__ void __launch_bounds__(RED_NT, RegBlocks<K>::value) k_nplet_reg(const
       nplet_reg_one<K, M>(mask, N, sR, ldr, sls, lr, sp, lsum, pmin, trace, bad);
       bad |= !(pmin >= tau_piv) | !(trace <= tau_tr);
       const unsigned long long gid = a.id_base + r0 + j;
-      if (basis) {
-        store_basis(a, gid, lr, sp, lsum, bad);
+      if (fused) {
+        fused_emit(a, acc, sthr, cmbv, gid, lr, sp, lsum, bad);
       } else {
-        float v[5];
-        combine5<float>(lr, sp, lsum, cmbv, v);
-        store5<float>(a, gid, v);
+        if (basis) {
+          store_basis(a, gid, lr, sp, lsum, bad);
+        } else {
+          float v[5];
+          combine5<float>(lr, sp, lsum, cmbv, v);
+          store5<float>(a, gid, v);
+        }
+        flag_append(a, bad, gid);
       }
-      flag_append(a, bad, gid);
       if (j + 1 < cnt) mask = lex_succ(mask, full);
     }
   }
+  if (fused) fused_block_end(a, acc);
 }
 
 template <int K, typename M>

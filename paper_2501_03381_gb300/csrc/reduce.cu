@@ -249,6 +249,62 @@ static cudaError_t launch_reduce_t(const V* basis, unsigned long long stride_ele
   return cudaGetLastError();
 }
 
+// Candidate list of a fused-records order slot: the FP32 list reduction,
+// seeded with the slot's top-list bounds (every nplet of the final top lists
+// lies beyond them once the merge certifies the record).  The partials carry
+// the extremes and the top lists only: the sums and the count of O < 0 came
+// from the nplet kernel, and block 0 carries the count of FP32 nplets (the
+// rank range less the nplets flagged for the FP64 re-factor).
+constexpr int CAND_MAX_BLOCKS = 64;
+
+__global__ void __launch_bounds__(RED_NT, 6) k_reduce_candidates(
+    const float* __restrict__ cb, unsigned long long cap, const unsigned long long* __restrict__ ids,
+    const unsigned long long* cand_count, const unsigned* __restrict__ keys, Combine cmb, int top_m,
+    unsigned long long n_range, const unsigned long long* flag_count, unsigned long long flag_cap,
+    PartRec* __restrict__ part, TopEnt* __restrict__ part_top) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ RedScratch sc;
+  __shared__ int s_tcnt[2];
+  __shared__ float s_seed[2];
+  if (threadIdx.x == 0) {
+    s_seed[0] = fused_threshold(keys[5 + cmb.top], 5 + cmb.top, cmb.top);
+    s_seed[1] = fused_threshold(keys[cmb.top], cmb.top, cmb.top);
+  }
+  __syncthreads();
+  reduce_core<float, true>((unsigned long long)blockIdx.x * RED_NT + threadIdx.x,
+                           (unsigned long long)gridDim.x * RED_NT, cb, cb + cap, cb + 2 * cap, 0,
+                           ids, cand_count, cap, 0, cmb, top_m, 0, s_seed, part + blockIdx.x,
+                           part_top + (size_t)blockIdx.x * 2 * top_m, smem, sc, s_tcnt);
+  if (threadIdx.x == 0) {
+    // same thread as the partial's writer in reduce_core
+    PartRec* r = part + blockIdx.x;
+    const unsigned long long fc = *flag_count;
+    r->s_lr = r->s_sp = r->s_ls = 0.0;
+    r->neg = 0;
+    r->notpd = 0;
+    r->count = blockIdx.x == 0 ? n_range - (fc < flag_cap ? fc : flag_cap) : 0ull;
+  }
+}
+
+cudaError_t launch_reduce_candidates(const NpletArgs& a, int num_sms, int max_blocks,
+                                     PartRec* part, TopEnt* part_top, cudaStream_t s,
+                                     int* grid_out) {
+  const size_t sm =
+      a.top_m > 0 ? (size_t)RTOP_CAP * 2 * (sizeof(float) + sizeof(unsigned long long)) : 0;
+  int occ = 0;
+  cudaError_t e = occupancy_cached((const void*)k_reduce_candidates, RED_NT, sm, &occ);
+  if (e != cudaSuccess) return e;
+  long long grid = (long long)num_sms * occ;
+  if (grid > CAND_MAX_BLOCKS) grid = CAND_MAX_BLOCKS;
+  if (grid > max_blocks) grid = max_blocks;
+  if (grid < 1) grid = 1;
+  k_reduce_candidates<<<(unsigned)grid, RED_NT, sm, s>>>(
+      a.cand_b, a.cand_cap, a.cand_ids, a.cand_count, a.thr_keys, a.cmb, a.top_m,
+      a.rank_end - a.rank_begin, a.flag_count, a.flag_cap, part, part_top);
+  if (grid_out) *grid_out = (int)grid;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_basis(const float* basis, unsigned long long stride_elems,
                                 unsigned long long n, unsigned long long id0, Combine cmb,
                                 int top_m, float* seed_thr, PartRec* part, TopEnt* part_top,

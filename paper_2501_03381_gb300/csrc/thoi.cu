@@ -80,6 +80,10 @@ struct thoi_ctx {
   double* b64 = nullptr;      // FP64 basis values (FP64 path pieces, re-factor list)
   size_t b64_cap = 0;         // doubles
   float* seed_thr = nullptr;  // starting top-M thresholds of the streaming reduction (2 floats)
+  // fused records: candidate counters and threshold keys per order slot, then
+  // the candidate list (ids, and three FP32 basis arrays of fz_cap entries)
+  unsigned char* fz = nullptr;
+  unsigned long long fz_cap = 0;
   // profiling: event pairs around launches, by class (0 nplet, 1 refactor, 2 merge, 3 reduce)
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;
@@ -263,6 +267,7 @@ extern "C" void thoi_default_options(thoi_options* o) {
   o->autotune = 1;
   o->flag_capacity = 0;
   o->profile = 0;
+  o->records_mode = THOI_RECORDS_AUTO;
 }
 
 extern "C" const char* thoi_status_string(thoi_status s) {
@@ -396,6 +401,7 @@ extern "C" void thoi_destroy(thoi_ctx* c) {
   free_ptr(c->basis);
   free_ptr(c->b64);
   free_ptr(c->seed_thr);
+  free_ptr(c->fz);
   free_ptr(c->grp);
   free_ptr(c->grp_meta);
   delete c;
@@ -411,6 +417,8 @@ static thoi_status ctx_common(thoi_ctx* c, int N, const thoi_options* opt) {
   if (!(c->opt.pivot_tau >= 0.0f) || !(c->opt.trace_tau > 0.0f)) return THOI_ERR_INVALID_ARG;
   if (c->opt.sigma32_source != THOI_SIGMA32_TENSORCORE &&
       c->opt.sigma32_source != THOI_SIGMA32_FROM_F64)
+    return THOI_ERR_INVALID_ARG;
+  if (c->opt.records_mode < THOI_RECORDS_AUTO || c->opt.records_mode > THOI_RECORDS_STORED)
     return THOI_ERR_INVALID_ARG;
   c->N = N;
   c->serial = next_serial();
@@ -575,6 +583,9 @@ constexpr int MAX_BLOCKS_PER_SM_OUT = 8;
 constexpr int REFACTOR_BLOCKS_PER_SM = 2;
 constexpr unsigned long long LAUNCH_SPLIT = 0xffffffffull;  // ranks per launch (u32 local ids)
 constexpr unsigned long long PIECE = 1ull << 28;  // FP32 records path: nplets per basis piece
+constexpr unsigned long long FUSE_MIN_N = 1ull << 20;  // automatic fused records from this size
+constexpr int FUSE_CAND_BLOCKS = 64;                   // candidate-reduction partials per slot
+constexpr size_t FZ_HEAD = 256 * 13;  // MAX_SLOTS counters, then MAX_SLOTS x 10 keys (3 KB)
 
 // Elements between the three basis arrays: the piece length rounded up to a
 // multiple of 64, so that every array is 256-byte aligned.
@@ -644,7 +655,7 @@ static NpletArgs base_args(thoi_ctx* c, const SlotRange& r) {
 }
 
 static thoi_status finish_status(thoi_ctx* c, cudaStream_t s, int n_slots, thoi_stats* stats,
-                                 uint64_t nplets, int launches) {
+                                 uint64_t nplets, int launches, int* hs_out = nullptr) {
   int hs = 0;
   unsigned long long fc[MAX_SLOTS];
   CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -671,6 +682,7 @@ static thoi_status finish_status(thoi_ctx* c, cudaStream_t s, int n_slots, thoi_
     stats->merge_ms = ms[2];
     stats->reduce_ms = ms[3];
   }
+  if (hs_out) *hs_out = hs;
   if (hs & ST_FLAG_OVERFLOW) return THOI_ERR_WORKSPACE;
   if (hs & ST_CANCELLED) return THOI_ERR_CANCELLED;
   if (hs & ST_NOT_PD) return THOI_ERR_NOT_PD;
@@ -705,12 +717,34 @@ static thoi_status ensure_parts(thoi_ctx* c, size_t n32, size_t n64, int top_m) 
   return THOI_OK;
 }
 
+// Fused records workspace for slots of up to max_n nplets: the candidate
+// list holds 1/24 of them (the sample bounds pass about 1.2% in expectation),
+// at least 2^16 entries; each array starts on a 256-byte boundary.
+static thoi_status ensure_fused_ws(thoi_ctx* c, unsigned long long max_n) {
+  unsigned long long cap = max_n / 24 + 1;
+  if (cap < (1ull << 16)) cap = 1ull << 16;
+  cap = (cap + 63) / 64 * 64;
+  if (c->fz && c->fz_cap >= cap) return THOI_OK;
+  free_ptr(c->fz);
+  c->fz = nullptr;
+  c->fz_cap = 0;
+  CK(cudaMalloc(&c->fz, FZ_HEAD + (size_t)cap * 8 + (size_t)cap * 3 * 4));
+  c->fz_cap = cap;
+  return THOI_OK;
+}
+static unsigned long long* fz_counts(thoi_ctx* c) { return (unsigned long long*)c->fz; }
+static unsigned* fz_keys(thoi_ctx* c) { return (unsigned*)(c->fz + 512); }
+static unsigned long long* fz_ids(thoi_ctx* c) { return (unsigned long long*)(c->fz + FZ_HEAD); }
+static float* fz_basis(thoi_ctx* c) { return (float*)(c->fz + FZ_HEAD + (size_t)c->fz_cap * 8); }
+
 // Queue the whole measure pass (no synchronisation).  Used directly by the
-// batched entry point, which captures it into a CUDA graph.
+// batched entry point, which captures it into a CUDA graph.  With `fuse`,
+// per-order records of the FP32 path reduce inside the nplet kernels where
+// the context's records_mode allows (see fused records in nplet_common.cuh).
 static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t n_orders,
                                     uint64_t id_begin, uint64_t id_end, int32_t kind, void* out_dev,
                                     thoi_order_record* recs_dev, TopEnt* tops_dev,
-                                    cudaStream_t s, int* launches_out) {
+                                    cudaStream_t s, int* launches_out, bool fuse = false) {
   std::vector<SlotRange> slots;
   thoi_status st = plan_slots(c, orders, n_orders, id_begin, &id_end, &slots);
   if (st != THOI_OK) return st;
@@ -719,8 +753,20 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
   const int top_m = red ? c->opt.top_m : 0;
   int launches = 0;
   c->ev_used = 0;
-  unsigned long long maxn = 0;
+  unsigned long long maxn = 0, maxn_fused = 0;
   for (auto& r : slots) maxn = (r.r1 - r.r0) > maxn ? (r.r1 - r.r0) : maxn;
+  auto fused_slot = [&](const SlotRange& r) {
+    const unsigned long long n = r.r1 - r.r0;
+    if (!fuse || !red || f64 || c->opt.records_mode == THOI_RECORDS_STORED) return false;
+    if (n == 0 || n > PIECE || r.k > 32) return false;
+    return c->opt.records_mode == THOI_RECORDS_FUSED || n >= FUSE_MIN_N;
+  };
+  for (auto& r : slots)
+    if (fused_slot(r) && r.r1 - r.r0 > maxn_fused) maxn_fused = r.r1 - r.r0;
+  if (maxn_fused > 0) {
+    st = ensure_fused_ws(c, maxn_fused);
+    if (st != THOI_OK) return st;
+  }
   if (!f64) {
     st = ensure_flag_ws(c, maxn);
     if (st != THOI_OK) return st;
@@ -734,7 +780,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
     for (auto& r : slots) {
       const unsigned long long n = r.r1 - r.r0;
       const size_t parts = n == 0 ? 0 : (size_t)((n + split - 1) / split);
-      n32 += parts * blk_cap;
+      n32 += parts * blk_cap + (fused_slot(r) ? FUSE_CAND_BLOCKS : 0);
     }
     if (!f64) {
       st = grow(&c->basis, &c->basis_cap, (size_t)3 * basis_stride(maxn));
@@ -753,6 +799,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
   }
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(c->flag_counts, 0, MAX_SLOTS * sizeof(unsigned long long), s));
+  if (maxn_fused > 0) CK(cudaMemsetAsync(c->fz, 0, FZ_HEAD, s));  // counters and keys
 
   MergeDescs D;
   memset(&D, 0, sizeof D);
@@ -766,7 +813,45 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
     md.p64_off = p64_off;
     md.refactored = f64 ? nullptr : c->flag_counts + si;
     const Shape sh = shape_for(c, r.k);
-    if (red && !f64) {
+    if (fused_slot(r)) {
+      // fused records: sample bounds, the nplet kernel reducing in place, the
+      // candidate list's reduction
+      NpletArgs a = base_args(c, r);
+      a.flag_count = c->flag_counts + si;
+      a.mode = 3;
+      a.top_m = top_m;
+      a.thr_keys = fz_keys(c) + (size_t)si * FUSE_NTHR;
+      a.cand_ids = fz_ids(c);
+      a.cand_b = fz_basis(c);
+      a.cand_count = fz_counts(c) + si;
+      a.cand_cap = c->fz_cap;
+      a.part = c->part32 + p32_off;
+      int grid = 0;
+      st = prof_begin(c, s, 3);
+      if (st != THOI_OK) return st;
+      CK(launch_fused_sample(a, c->num_sms, s));
+      st = prof_end(c, s);
+      if (st != THOI_OK) return st;
+      st = prof_begin(c, s, 0);
+      if (st != THOI_OK) return st;
+      CK(launch_nplet_f32(a, sh, c->num_sms, s, &grid, c->num_sms * MAX_BLOCKS_PER_SM_OUT));
+      st = prof_end(c, s);
+      if (st != THOI_OK) return st;
+      p32_off += grid;
+      md.g32 += grid;
+      st = prof_begin(c, s, 3);
+      if (st != THOI_OK) return st;
+      CK(launch_reduce_candidates(a, c->num_sms, FUSE_CAND_BLOCKS, c->part32 + p32_off,
+                                  top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr, s,
+                                  &grid));
+      st = prof_end(c, s);
+      if (st != THOI_OK) return st;
+      p32_off += grid;
+      md.g32 += grid;
+      md.thr_keys = a.thr_keys;
+      md.status = c->status;
+      launches += 3;
+    } else if (red && !f64) {
       // FP32 records: basis values per piece, then the streaming reduction
       // each of the three arrays starts on a 256-byte boundary (16-byte loads)
       const unsigned long long bstride = basis_stride(maxn);
@@ -955,10 +1040,21 @@ extern "C" thoi_status thoi_measures(thoi_ctx* c, const int32_t* orders, int32_t
     }
     thoi_order_record* recs = (thoi_order_record*)dst;
     TopEnt* tops = (TopEnt*)(dst + (size_t)n_orders * sizeof(thoi_order_record));
-    st = enqueue_measures(c, orders, n_orders, id_begin, end, kind, nullptr, recs, tops, s,
-                          &launches);
-    if (st != THOI_OK) return st;
-    if (!dev) CK(cudaMemcpyAsync(out, dst, need, cudaMemcpyDeviceToHost, s));
+    // fused records first; a record the merge could not certify (or a full
+    // candidate list) repeats the request with stored basis values
+    for (int pass = 0; pass < 2; pass++) {
+      st = enqueue_measures(c, orders, n_orders, id_begin, end, kind, nullptr, recs, tops, s,
+                            &launches, pass == 0);
+      if (st != THOI_OK) return st;
+      if (!dev) CK(cudaMemcpyAsync(out, dst, need, cudaMemcpyDeviceToHost, s));
+      int hs = 0;
+      st = finish_status(c, s, (int)slots.size(), stats, n, launches, &hs);
+      if (!(hs & (ST_INEXACT | ST_CAND_OVERFLOW)) || pass == 1) {
+        if (stats && pass == 1) stats->fused_retries = 1;
+        return st;
+      }
+    }
+    return st;
   }
   return finish_status(c, s, (int)slots.size(), stats, n, launches);
 }
@@ -2215,7 +2311,7 @@ static double time_shape(thoi_ctx* c, int k, uint64_t n, const Shape& sh, cudaSt
       int launches = 0;
       thoi_stats st;
       if (enqueue_measures(c, &ord, 1, 0, n, THOI_RED_PER_ORDER, nullptr, recs, tops, s,
-                           &launches) != THOI_OK)
+                           &launches, true) != THOI_OK)
         break;
       const thoi_status fs = finish_status(c, s, 1, &st, n, launches);
       if (fs != THOI_OK && fs != THOI_ERR_NOT_PD) break;

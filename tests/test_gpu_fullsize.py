@@ -76,3 +76,31 @@ def test_planted30_records_full_size():
             np.testing.assert_allclose(ref[3, pos:pos + n], v, rtol=0, atol=tol)
             pos += n
     assert pos == len(ids)
+
+
+def test_planted30_fused_records_match_stored_full_size():
+    # the bench's records (fused: reduced inside the nplet kernels, certified
+    # by the merge) against the same records formed from stored per-nplet
+    # values, every order of the N = 30 workload with the autotuned kernels
+    X, orders = workloads.planted30()
+    Xd = torch.as_tensor(X, device="cuda")
+    res = {}
+    for mode in ("auto", "stored"):
+        with P.Context(Xd, top_m=TOP_M, records_mode=mode) as c:
+            path = os.path.join(tempfile.mkdtemp(), "tune.json")
+            P.thoi_autotune(c.h, 3, 30, path)
+            res[mode] = c.measures(orders, reduction="per_order")
+    (ra, ha, la), sta = res["auto"]
+    (rb, hb, lb), _ = res["stored"]
+    assert sta.fused_retries == 0
+    for q in range(len(orders)):
+        for f in ("k", "count", "n_refactored", "n_not_pd", "top_count"):
+            assert int(ra[q][f]) == int(rb[q][f]), (q, f)
+        for f in ("min", "max", "argmin", "argmax"):
+            np.testing.assert_array_equal(ra[q][f], rb[q][f], err_msg=f"order {orders[q]} {f}")
+        np.testing.assert_allclose(ra[q]["mean"], rb[q]["mean"], rtol=0, atol=1e-6)
+        assert abs(int(ra[q]["count_neg_O"]) - int(rb[q]["count_neg_O"])) <= 2
+        n = int(ra[q]["top_count"])
+        for x, y in ((ha[q], hb[q]), (la[q], lb[q])):
+            np.testing.assert_array_equal(x["id"][:n], y["id"][:n])
+            np.testing.assert_array_equal(x["value"][:n], y["value"][:n])
