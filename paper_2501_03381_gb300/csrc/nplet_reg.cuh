@@ -104,6 +104,14 @@ struct RegBlocks {
   static constexpr int value = K <= 16 ? 3 : ((K == 17 || K > 20) ? 1 : 2);
 };
 
+// Per-nplet output (mode 0) goes through shared memory: the 32 lanes of a
+// warp hold 32 consecutive chunks, i.e. 32 * chunk consecutive ranks, so the
+// warp stages their values and writes each measure's run with consecutive
+// lanes on consecutive addresses (a direct store from each lane's own chunk
+// would touch 32 sectors per instruction).
+constexpr int REG_STAGE = 5 * 32 * 8;  // floats staged per warp (five measures, chunk <= 8)
+constexpr size_t REG_STAGE_BYTES = (size_t)(RED_NT / 32) * REG_STAGE * sizeof(float);
+
 template <int K, typename M>
 __global__ void __launch_bounds__(RED_NT, RegBlocks<K>::value) k_nplet_reg(const NpletArgs a,
                                                                           const int chunk) {
@@ -116,7 +124,10 @@ __global__ void __launch_bounds__(RED_NT, RegBlocks<K>::value) k_nplet_reg(const
   const float* sls = reinterpret_cast<const float*>(smem + L.ls);
   const bool basis = a.mode == 2;
   const bool fused = a.mode == 3;
+  const bool stage = a.mode == 0;
   const float* sthr = reinterpret_cast<const float*>(smem + L.thr);
+  const int lane = threadIdx.x & 31;
+  float* sbuf = reinterpret_cast<float*>(smem + L.total) + (threadIdx.x >> 5) * REG_STAGE;
   FusedAcc acc;
   acc.init();
   const M full = (N >= (int)(8 * sizeof(M))) ? ~(M)0 : (((M)1 << N) - 1);
@@ -126,36 +137,62 @@ __global__ void __launch_bounds__(RED_NT, RegBlocks<K>::value) k_nplet_reg(const
   const float tau_piv = a.tau_piv, tau_tr = a.tau_tr;
   const CombineV<float> cmbv(a.cmb);
 
-  for (unsigned long long ch = (unsigned long long)blockIdx.x * RED_NT + threadIdx.x; ch < nch;
-       ch += stride) {
+  // whole warps step together (lane l takes chunk chw + l), so that the
+  // staged output of a warp is one contiguous run of ranks
+  for (unsigned long long chw = (unsigned long long)blockIdx.x * RED_NT + (threadIdx.x & ~31u);
+       chw < nch; chw += stride) {
     // the cancel flag lives in host memory: read it once every 64 rounds
-    if (((ch / stride) & 63) == 0 && a.cancel && *(volatile const int*)a.cancel) {
-      atomicOr(a.status, ST_CANCELLED);
+    if (((chw / stride) & 63) == 0 && a.cancel && *(volatile const int*)a.cancel) {
+      if (lane == 0) atomicOr(a.status, ST_CANCELLED);
       break;
     }
-    const unsigned long long r0 = a.rank_begin + ch * chunk;
-    const unsigned long long left = a.rank_end - r0;
-    const int cnt = left < (unsigned long long)chunk ? (int)left : chunk;
-    M mask = unrank_s<M>(r0, K, N, sb, K + 1);
-    for (int j = 0; j < cnt; j++) {
-      float lr, sp, lsum, pmin, trace;
-      bool bad = false;
-      nplet_reg_one<K, M>(mask, N, sR, ldr, sls, lr, sp, lsum, pmin, trace, bad);
-      bad |= !(pmin >= tau_piv) | !(trace <= tau_tr);
-      const unsigned long long gid = a.id_base + r0 + j;
-      if (fused) {
-        fused_emit(a, acc, sthr, cmbv, gid, lr, sp, lsum, bad);
-      } else {
-        if (basis) {
-          store_basis(a, gid, lr, sp, lsum, bad);
+    const unsigned long long ch = chw + lane;
+    if (ch < nch) {
+      const unsigned long long r0 = a.rank_begin + ch * chunk;
+      const unsigned long long left = a.rank_end - r0;
+      const int cnt = left < (unsigned long long)chunk ? (int)left : chunk;
+      M mask = unrank_s<M>(r0, K, N, sb, K + 1);
+      for (int j = 0; j < cnt; j++) {
+        float lr, sp, lsum, pmin, trace;
+        bool bad = false;
+        nplet_reg_one<K, M>(mask, N, sR, ldr, sls, lr, sp, lsum, pmin, trace, bad);
+        bad |= !(pmin >= tau_piv) | !(trace <= tau_tr);
+        const unsigned long long gid = a.id_base + r0 + j;
+        if (fused) {
+          fused_emit(a, acc, sthr, cmbv, gid, lr, sp, lsum, bad);
         } else {
-          float v[5];
-          combine5<float>(lr, sp, lsum, cmbv, v);
-          store5<float>(a, gid, v);
+          if (basis) {
+            store_basis(a, gid, lr, sp, lsum, bad);
+          } else {
+            float v[5];
+            combine5<float>(lr, sp, lsum, cmbv, v);
+            const int e = lane * chunk + j;
+#pragma unroll
+            for (int m = 0; m < 5; m++) sbuf[m * 32 * 8 + e] = v[m];
+          }
+          flag_append(a, bad, gid);
         }
-        flag_append(a, bad, gid);
+        if (j + 1 < cnt) mask = lex_succ(mask, full);
       }
-      if (j + 1 < cnt) mask = lex_succ(mask, full);
+    }
+    if (stage) {
+      __syncwarp();
+      const unsigned long long wr0 = a.rank_begin + chw * chunk;
+      const unsigned long long wleft = a.rank_end - wr0;
+      const int wn = wleft < (unsigned long long)(32 * chunk) ? (int)wleft : 32 * chunk;
+      const unsigned long long o0 = a.id_base + wr0 - a.out_first;
+      const int m0 = a.out_sel > 0 ? a.out_sel - 1 : 0, m1 = a.out_sel > 0 ? a.out_sel : 5;
+      for (int m = m0; m < m1; m++) {
+        const unsigned long long row = a.out_sel > 0 ? 0ull : (unsigned long long)m * a.out_n;
+        if (a.out_f64) {
+          double* O = reinterpret_cast<double*>(a.out) + row + o0;
+          for (int e = lane; e < wn; e += 32) O[e] = (double)sbuf[m * 32 * 8 + e];
+        } else {
+          float* O = reinterpret_cast<float*>(a.out) + row + o0;
+          for (int e = lane; e < wn; e += 32) O[e] = sbuf[m * 32 * 8 + e];
+        }
+      }
+      __syncwarp();
     }
   }
   if (fused) fused_block_end(a, acc);
@@ -165,9 +202,10 @@ template <int K, typename M>
 static cudaError_t launch_reg_t(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                                 int* grid_out, int max_blocks) {
   const SmemLayout L = smem_layout(a.N, K, row_stride(a.N), sizeof(float), sizeof(unsigned), 0);
+  const size_t smem = L.total + (a.mode == 0 ? REG_STAGE_BYTES : 0);
   void (*fn)(const NpletArgs, const int) = k_nplet_reg<K, M>;
   int occ = 0;
-  cudaError_t e = occupancy_cached((const void*)fn, RED_NT, L.total, &occ);
+  cudaError_t e = occupancy_cached((const void*)fn, RED_NT, smem, &occ);
   if (e != cudaSuccess) return e;
   if (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ) occ = sh.blocks_per_sm;
   int chunk = sh.chunk > 0 ? sh.chunk : 8;
@@ -178,7 +216,7 @@ static cudaError_t launch_reg_t(const NpletArgs& a, const Shape& sh, int num_sms
                                      ((unsigned long long)RED_NT * chunk));
   if (need < grid) grid = need > 0 ? need : 1;
   if (grid > max_blocks) grid = max_blocks;
-  fn<<<(unsigned)grid, RED_NT, L.total, s>>>(a, chunk);
+  fn<<<(unsigned)grid, RED_NT, smem, s>>>(a, chunk);
   if (grid_out) *grid_out = (int)grid;
   return cudaGetLastError();
 }

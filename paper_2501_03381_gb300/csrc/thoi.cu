@@ -936,7 +936,13 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       if (f64 && !red && f64s_threads(c->N, r.k, nullptr) > 0)
         CK(launch_nplet_f64s(a, false, nullptr, 0, c->num_sms, s, &grid, cap));
       else if (f64) CK(launch_nplet_f64(a, c->num_sms, s, &grid, cap));
-      else CK(launch_nplet_f32(a, sh, c->num_sms, s, &grid, cap));
+      else if (!red && r.k <= 8) {
+        // per-nplet output of small orders is bound by its stores: the dense
+        // kernel writes them coalesced through shared memory
+        Shape sd = sh;
+        sd.prefix = 0;
+        CK(launch_nplet_f32(a, sd, c->num_sms, s, &grid, cap));
+      } else CK(launch_nplet_f32(a, sh, c->num_sms, s, &grid, cap));
       st = prof_end(c, s);
       if (st != THOI_OK) return st;
       launches++;
