@@ -164,6 +164,7 @@ typedef struct {
   int32_t fused_retries; /* 1 when fused records could not be certified and the
                             request was repeated with stored values */
   int32_t pad2;
+  uint64_t n_candidates; /* fused records: nplets listed beyond the sample bounds */
 } thoi_stats;
 
 /* Fill `opt` with the defaults listed above. */

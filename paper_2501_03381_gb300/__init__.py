@@ -59,7 +59,7 @@ class thoi_stats(ctypes.Structure):
                 ("pad", ctypes.c_int32), ("nplet_ms", ctypes.c_double),
                 ("refactor_ms", ctypes.c_double), ("merge_ms", ctypes.c_double),
                 ("reduce_ms", ctypes.c_double), ("fused_retries", ctypes.c_int32),
-                ("pad2", ctypes.c_int32)]
+                ("pad2", ctypes.c_int32), ("n_candidates", ctypes.c_uint64)]
 
 
 RECORD_DTYPE = np.dtype([("k", "<i4"), ("top_count", "<i4"), ("count", "<u8"),

@@ -1,9 +1,9 @@
-// Multi-dataset batch: dispatch of the batched FP32 nplet kernel by order,
-// and the batched reduction, FP64 re-factor and list-reduction kernels.  The
-// bodies are those of the single-dataset kernels (reduce_core, f64s_body,
-// f64g_body); here a block finds its dataset, order and range from
-// descriptors in device memory instead of from launch arguments, so that one
-// launch covers every dataset of the batch.
+// Multi-dataset batch: dispatch of the persistent batched FP32 nplet kernel
+// by band of orders, and the batched FP64 re-factor and list-reduction
+// kernels.  The bodies are those of the single-dataset kernels (f64s_body,
+// f64g_body, reduce_core); here a block finds its dataset, order and range
+// from descriptors in device memory instead of from launch arguments, so
+// that one launch covers every dataset of the batch.
 #include <type_traits>
 
 #include "nplet_f64.cuh"
@@ -11,75 +11,24 @@
 
 namespace thoi {
 
-template <int K>
-cudaError_t batch_occ_k(bool wide, int maxN, size_t* smem, int* occ);
-template <int K>
-cudaError_t batch_launch_k(bool wide, const BatchArgs& b, size_t smem, int grid, int chunk,
-                           cudaStream_t s);
+template <int KLO, int KHI>
+cudaError_t bfused_launch(bool wide, const BatchFArgs& b, int maxN, int blocks_per_sm,
+                          int num_sms, cudaStream_t s, int* grid_out);
 
-#define THOI_BATCH_CASES(CALL)                                                              \
-  switch (k) {                                                                              \
-    case 1: return CALL(1); case 2: return CALL(2); case 3: return CALL(3);                 \
-    case 4: return CALL(4); case 5: return CALL(5); case 6: return CALL(6);                 \
-    case 7: return CALL(7); case 8: return CALL(8); case 9: return CALL(9);                 \
-    case 10: return CALL(10); case 11: return CALL(11); case 12: return CALL(12);           \
-    case 13: return CALL(13); case 14: return CALL(14); case 15: return CALL(15);           \
-    case 16: return CALL(16); case 17: return CALL(17); case 18: return CALL(18);           \
-    case 19: return CALL(19); case 20: return CALL(20);                                     \
-    default: return cudaErrorInvalidValue;                                                  \
+cudaError_t launch_batch_fused(int band, bool wide, const BatchFArgs& b, int maxN,
+                               int blocks_per_sm, int num_sms, cudaStream_t s, int* grid_out) {
+  if (b.n_tiles <= 0) return cudaSuccess;
+  switch (band) {
+    case 0: return bfused_launch<1, 8>(wide, b, maxN, blocks_per_sm, num_sms, s, grid_out);
+    case 1: return bfused_launch<9, 14>(wide, b, maxN, blocks_per_sm, num_sms, s, grid_out);
+    case 2: return bfused_launch<15, 17>(wide, b, maxN, blocks_per_sm, num_sms, s, grid_out);
+    case 3: return bfused_launch<18, 20>(wide, b, maxN, blocks_per_sm, num_sms, s, grid_out);
+    default: return cudaErrorInvalidValue;
   }
-
-cudaError_t batch_nplet_occupancy(int k, bool wide, int maxN, size_t* smem, int* occ) {
-#define OCC(KK) batch_occ_k<KK>(wide, maxN, smem, occ)
-  THOI_BATCH_CASES(OCC)
-#undef OCC
-}
-
-cudaError_t launch_nplet_batch(int k, bool wide, const BatchArgs& b, size_t smem, int grid,
-                               int chunk, cudaStream_t s) {
-  if (grid < 1 || chunk < 1 || chunk > 8) return cudaErrorInvalidValue;
-#define LAUNCH(KK) batch_launch_k<KK>(wide, b, smem, grid, chunk, s)
-  THOI_BATCH_CASES(LAUNCH)
-#undef LAUNCH
-}
-#undef THOI_BATCH_CASES
-
-// ------------------------------------------------------------------ reduction tiles
-// One block per reduction tile: the streaming reduction of the tile's basis
-// triples into partial blockIdx.x.
-__global__ void __launch_bounds__(RED_NT, 6) k_reduce_batch(const float* __restrict__ basis,
-                                                          unsigned long long bstride,
-                                                          const BatchRTile* __restrict__ rt,
-                                                          const BatchSlot* __restrict__ slots,
-                                                          int top_m, PartRec* __restrict__ part,
-                                                          TopEnt* __restrict__ part_top) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ RedScratch sc;
-  __shared__ int s_tcnt[2];
-  const BatchRTile t = rt[blockIdx.x];
-  const Combine cmb = slots[t.slot].cmb;
-  const float* B = basis + t.boff;
-  reduce_core<float, false>(threadIdx.x, RED_NT, B, B + bstride, B + 2 * bstride, t.n, nullptr,
-                            nullptr, 0, t.id0, cmb, top_m, 0, nullptr, part + blockIdx.x,
-                            part_top + (size_t)blockIdx.x * 2 * top_m, smem, sc, s_tcnt);
 }
 
 static size_t reduce_smem(int top_m, size_t vsz, size_t isz) {
   return top_m > 0 ? (size_t)RTOP_CAP * 2 * (vsz + isz) : 0;
-}
-
-cudaError_t batch_reduce_occupancy(int top_m, size_t* smem, int* occ) {
-  *smem = reduce_smem(top_m, sizeof(float), sizeof(unsigned));
-  return occupancy_cached((const void*)k_reduce_batch, RED_NT, *smem, occ);
-}
-
-cudaError_t launch_reduce_batch(const float* basis, unsigned long long bstride,
-                                const BatchRTile* rt, int n_rt, const BatchSlot* slots, int top_m,
-                                PartRec* part, TopEnt* part_top, cudaStream_t s) {
-  if (n_rt <= 0) return cudaSuccess;
-  const size_t sm = reduce_smem(top_m, sizeof(float), sizeof(unsigned));
-  k_reduce_batch<<<n_rt, RED_NT, sm, s>>>(basis, bstride, rt, slots, top_m, part, part_top);
-  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ FP64 re-factor

@@ -1,0 +1,6 @@
+// Instance of the persistent batched FP32 nplet kernel for orders 15..17.
+#include "batch_fused.cuh"
+
+namespace thoi {
+template cudaError_t bfused_launch<15, 17>(bool, const BatchFArgs&, int, int, int, cudaStream_t, int*);
+}  // namespace thoi

@@ -88,12 +88,19 @@ struct NpletArgs {
   int top_m;
   // mode 3 (fused records): thresholds of this order slot (FUSE_NTHR keys),
   // and the candidate list the kernel appends to (ids; three FP32 arrays of
-  // log det R_S, sum_j log p_j, sum_i log Sigma_ii at cand_b[m * cand_cap + e])
+  // log det R_S, sum_j log p_j, sum_i log Sigma_ii at cand_b[m * cand_cap + e]).
+  // The list is cut into cand_nseg segments of cand_seg entries; block b
+  // appends to segment b % cand_nseg (counter cand_count[segment]), which
+  // spreads the appends' atomics over several addresses.
+  // mode 4 (sample bounds): the kernel evaluates sampled nplets and adds
+  // their extremes to thr_keys (see launch_fused_sample).
   const unsigned* thr_keys;
   unsigned long long* cand_ids;
   float* cand_b;
   unsigned long long* cand_count;
   unsigned long long cand_cap;
+  unsigned long long cand_seg;
+  int cand_nseg;
   // FP64 re-factor list (FP32 kernels append; the re-factor kernel reads)
   unsigned long long* flag_ids;
   unsigned long long* flag_count;
@@ -164,6 +171,8 @@ cudaError_t launch_reduce_basis64(const double* basis, unsigned long long stride
 // the slot's nplets (FP32, every sampled nplet evaluated directly; keys added
 // with atomicMax into thr_keys, which must be zero beforehand) ...
 cudaError_t launch_fused_sample(const NpletArgs& a, int num_sms, cudaStream_t s);
+int fused_sample_per_thread(unsigned long long n, int top_m);
+constexpr int FUSE_NSEG = 16;  // candidate-list segments (and candidate-reduction blocks)
 // ... and, after the nplet launch, the reduction of the candidate list into
 // per-block partials holding the extremes and top lists only; block 0 also
 // carries the count of FP32 nplets (rank range minus the flagged ones).
@@ -284,40 +293,39 @@ struct BatchSlot {
   unsigned long long flag_off, flag_cap;  // region of the flag list (and FP64 basis)
   Combine cmb;
 };
-// Nplet tile: ranks [r0, r0 + n) of a slot; basis values at boff of the piece.
-struct BatchTile {
-  unsigned long long r0, boff;
+// Tile of the persistent batched kernel: ranks [r0, r0 + n) of a slot
+// (n <= 2^16, order k), reduced into partial record pidx.
+struct BatchFTile {
+  unsigned long long r0;
   unsigned n;
   int slot;
+  int pidx;
+  int k;
 };
-// Reduction tile: n basis triples at boff of the piece, global ids id0 + e.
-struct BatchRTile {
-  unsigned long long boff, n, id0;
-  int slot, pad;
-};
-struct BatchArgs {
+struct BatchFArgs {
   const BatchDataset* ds;
   const BatchSlot* slots;
-  const BatchTile* tiles;
+  const BatchFTile* tiles;
   int n_tiles;
-  int pad;
+  int top_m;
   const unsigned long long* binom;  // NB x NB
-  float* basis;                     // three arrays of bstride floats
-  unsigned long long bstride;
   unsigned long long* flag_ids;
   unsigned long long* flag_counts;  // one counter per slot
+  PartRec* part;
+  TopEnt* part_top;
+  unsigned* tile_counter;           // zero before the launch
   int* status;
   const int* cancel;
+  int chunk_k[KBATCH_MAX + 1];      // nplets per thread per round, by order
 };
-// Dynamic shared memory and blocks per SM of the batched FP32 nplet kernel
-// for order k (maxN = the largest N of the batch; wide = 64-bit masks).
-cudaError_t batch_nplet_occupancy(int k, bool wide, int maxN, size_t* smem, int* occ);
-cudaError_t launch_nplet_batch(int k, bool wide, const BatchArgs& b, size_t smem, int grid,
-                               int chunk, cudaStream_t s);
-cudaError_t batch_reduce_occupancy(int top_m, size_t* smem, int* occ);
-cudaError_t launch_reduce_batch(const float* basis, unsigned long long bstride,
-                                const BatchRTile* rt, int n_rt, const BatchSlot* slots, int top_m,
-                                PartRec* part, TopEnt* part_top, cudaStream_t s);
+// Orders of each band of the persistent batched kernel (one kernel per band).
+constexpr int BATCH_BANDS = 4;
+constexpr int BATCH_BAND_LO[BATCH_BANDS] = {1, 9, 15, 18};
+constexpr int BATCH_BAND_HI[BATCH_BANDS] = {8, 14, 17, 20};
+// One launch of band `band` over the tiles in b (all of the band's orders);
+// blocks_per_sm 0 = the occupancy maximum.
+cudaError_t launch_batch_fused(int band, bool wide, const BatchFArgs& b, int maxN,
+                               int blocks_per_sm, int num_sms, cudaStream_t s, int* grid_out);
 // FP64 re-factor of the flagged nplets of slots [slot0, slot0 + n_slots),
 // grid (bx, n_slots); basis values at b64[m * lstride + flag_off + e].
 cudaError_t launch_refactor_batch(const BatchDataset* ds, const BatchSlot* slots, int slot0,

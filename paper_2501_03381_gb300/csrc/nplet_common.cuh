@@ -602,20 +602,76 @@ __device__ __forceinline__ void cand_append(const NpletArgs& a, bool cand, unsig
   if (!fl) return;
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(fl) - 1;
+  const int seg = (int)(blockIdx.x % (unsigned)a.cand_nseg);
   unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(a.cand_count, (unsigned long long)__popc(fl));
+  if (lane == leader) base = atomicAdd(a.cand_count + seg, (unsigned long long)__popc(fl));
   if (cand) {
     base = __shfl_sync(fl, base, leader);
     const unsigned long long pos = base + __popc(fl & ((1u << lane) - 1u));
-    if (pos < a.cand_cap) {
-      a.cand_ids[pos] = gid;
-      a.cand_b[pos] = lr;
-      a.cand_b[a.cand_cap + pos] = sp;
-      a.cand_b[2 * a.cand_cap + pos] = lsum;
+    if (pos < a.cand_seg) {
+      const unsigned long long e = (unsigned long long)seg * a.cand_seg + pos;
+      a.cand_ids[e] = gid;
+      a.cand_b[e] = lr;
+      a.cand_b[a.cand_cap + e] = sp;
+      a.cand_b[2 * a.cand_cap + e] = lsum;
     } else {
       atomicOr(a.status, ST_CAND_OVERFLOW);
     }
   }
+}
+
+// Mode 4: a block's extremes of sampled nplets into the slot's bound keys
+// (every thread passes its own minima and maxima; see launch_fused_sample).
+__device__ inline void sample_block_keys(const NpletArgs& a, float (&mn)[5], float (&mx)[5],
+                                         unsigned valid) {
+  __shared__ float s_mn[RED_NT / 32][5], s_mx[RED_NT / 32][5];
+  __shared__ unsigned s_valid[RED_NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+      mn[m] = fminf(mn[m], __shfl_xor_sync(0xffffffffu, mn[m], o));
+      mx[m] = fmaxf(mx[m], __shfl_xor_sync(0xffffffffu, mx[m], o));
+    }
+    valid += __shfl_xor_sync(0xffffffffu, valid, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+      s_mn[w][m] = mn[m];
+      s_mx[w][m] = mx[m];
+    }
+    s_valid[w] = valid;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned nv = 0;
+    for (int q = 0; q < RED_NT / 32; q++) {
+      nv += s_valid[q];
+      for (int m = 0; m < 5; m++) {
+        mn[m] = fminf(mn[m], s_mn[q][m]);
+        mx[m] = fmaxf(mx[m], s_mx[q][m]);
+      }
+    }
+    if (nv > 0) {
+      unsigned* keys = const_cast<unsigned*>(a.thr_keys);
+      const int top = a.cmb.top;
+      for (int m = 0; m < 5; m++) {
+        const unsigned klo = fkey32(mn[m]), khi = fkey32(mx[m]);
+        atomicMax(&keys[m], fused_slot_negated(m, top) ? ~klo : klo);
+        atomicMax(&keys[5 + m], fused_slot_negated(5 + m, top) ? ~khi : khi);
+      }
+    }
+  }
+}
+
+// Rank of sample i of S spread evenly over the range (n = q S + rem).
+__device__ __forceinline__ unsigned long long sample_rank(const NpletArgs& a, unsigned long long i,
+                                                          unsigned long long S) {
+  const unsigned long long n = a.rank_end - a.rank_begin;
+  const unsigned long long q = n / S, rem = n % S;
+  return a.rank_begin + i * q + (i * rem) / S;
 }
 
 // One nplet in mode 3: sums and count of O < 0 when the FP32 value is kept,

@@ -283,12 +283,33 @@ __global__ void __launch_bounds__(FS_NT) k_fused_sample(const NpletArgs a, unsig
   }
 }
 
+// Samples per thread of the sample bounds: about n / 256 samples in all
+// (at least 32K, at most 1M), over max(256, top_m) blocks of 128 threads.
+int fused_sample_per_thread(unsigned long long n, int top_m) {
+  const unsigned long long grid = top_m > 256 ? (unsigned long long)top_m : 256ull;
+  unsigned long long S = n / 256;
+  if (S < (1ull << 15)) S = 1ull << 15;
+  if (S > (1ull << 20)) S = 1ull << 20;
+  unsigned long long e = (S + grid * FS_NT - 1) / (grid * FS_NT);
+  return (int)(e < 1 ? 1 : (e > 32 ? 32 : e));
+}
+
 cudaError_t launch_fused_sample(const NpletArgs& a0, int num_sms, cudaStream_t s) {
-  (void)num_sms;
+  const unsigned long long n = a0.rank_end - a0.rank_begin;
+  if (n == 0) return cudaSuccess;
+  if (a0.k <= KREG_MAX) {
+    // the one-thread register kernel in its sample mode
+    NpletArgs a = a0;
+    a.mode = 4;
+    Shape sh;
+    sh.blocks_per_sm = 0;
+    sh.chunk = fused_sample_per_thread(n, a.top_m);
+    sh.lanes = 1;
+    sh.prefix = 0;
+    return launch_nplet_f32(a, sh, num_sms, s, nullptr, 1 << 30);
+  }
   NpletArgs a = a0;
   a.mode = 0;  // the sample kernel reads no bounds
-  const unsigned long long n = a.rank_end - a.rank_begin;
-  if (n == 0) return cudaSuccess;
   const int grid = a.top_m > 256 ? a.top_m : 256;
   const unsigned long long cap = (unsigned long long)grid * FS_NT * FS_PER;
   const unsigned long long S = n < cap ? n : cap;

@@ -137,6 +137,41 @@ __global__ void __launch_bounds__(RED_NT, RegBlocks<K>::value) k_nplet_reg(const
   const float tau_piv = a.tau_piv, tau_tr = a.tau_tr;
   const CombineV<float> cmbv(a.cmb);
 
+  if (a.mode == 4) {
+    // sample bounds of fused records: `chunk` samples per thread, sample i of
+    // S taken by block i % grid, every sample unranked on its own
+    const unsigned long long S0 = (unsigned long long)gridDim.x * RED_NT * (unsigned)chunk;
+    const unsigned long long S = n < S0 ? n : S0;
+    float mn[5], mx[5];
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+      mn[m] = pinf<float>();
+      mx[m] = -pinf<float>();
+    }
+    unsigned valid = 0;
+    for (int e = 0; e < chunk; e++) {
+      const unsigned long long i =
+          ((unsigned long long)threadIdx.x * chunk + e) * gridDim.x + blockIdx.x;
+      if (i >= S) continue;
+      const M mask = unrank_s<M>(sample_rank(a, i, S), K, N, sb, K + 1);
+      float lr, sp, lsum, pmin, trace;
+      bool bad = false;
+      nplet_reg_one<K, M>(mask, N, sR, ldr, sls, lr, sp, lsum, pmin, trace, bad);
+      bad |= !(pmin >= tau_piv) | !(trace <= tau_tr);
+      if (bad) continue;
+      float v[5];
+      combine5<float>(lr, sp, lsum, cmbv, v);
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        mn[m] = fminf(mn[m], v[m]);
+        mx[m] = fmaxf(mx[m], v[m]);
+      }
+      valid++;
+    }
+    sample_block_keys(a, mn, mx, valid);
+    return;
+  }
+
   // whole warps step together (lane l takes chunk chw + l), so that the
   // staged output of a warp is one contiguous run of ranks
   for (unsigned long long chw = (unsigned long long)blockIdx.x * RED_NT + (threadIdx.x & ~31u);
@@ -207,6 +242,15 @@ static cudaError_t launch_reg_t(const NpletArgs& a, const Shape& sh, int num_sms
   int occ = 0;
   cudaError_t e = occupancy_cached((const void*)fn, RED_NT, smem, &occ);
   if (e != cudaSuccess) return e;
+  if (a.mode == 4) {
+    // sample bounds: max(256, top_m) blocks (so that the smallest block
+    // maximum has at least top_m samples at or above it), sh.chunk samples
+    // per thread
+    const int sgrid = a.top_m > 256 ? a.top_m : 256;
+    fn<<<(unsigned)sgrid, RED_NT, smem, s>>>(a, sh.chunk > 0 ? sh.chunk : 1);
+    if (grid_out) *grid_out = sgrid;
+    return cudaGetLastError();
+  }
   if (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ) occ = sh.blocks_per_sm;
   int chunk = sh.chunk > 0 ? sh.chunk : 8;
   if (chunk > 8) chunk = 8;

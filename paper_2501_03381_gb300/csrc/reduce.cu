@@ -249,19 +249,19 @@ static cudaError_t launch_reduce_t(const V* basis, unsigned long long stride_ele
   return cudaGetLastError();
 }
 
-// Candidate list of a fused-records order slot: the FP32 list reduction,
-// seeded with the slot's top-list bounds (every nplet of the final top lists
-// lies beyond them once the merge certifies the record).  The partials carry
-// the extremes and the top lists only: the sums and the count of O < 0 came
-// from the nplet kernel, and block 0 carries the count of FP32 nplets (the
-// rank range less the nplets flagged for the FP64 re-factor).
-constexpr int CAND_MAX_BLOCKS = 64;
-
+// Candidate list of a fused-records order slot: block s reduces segment s
+// of the list (the FP32 list reduction), seeded with the slot's top-list
+// bounds (every nplet of the final top lists lies beyond them once the merge
+// certifies the record).  The partials carry the extremes and the top lists
+// only: the sums and the count of O < 0 came from the nplet kernel, and
+// block 0 carries the count of FP32 nplets (the rank range less the nplets
+// flagged for the FP64 re-factor).
 __global__ void __launch_bounds__(RED_NT, 6) k_reduce_candidates(
-    const float* __restrict__ cb, unsigned long long cap, const unsigned long long* __restrict__ ids,
-    const unsigned long long* cand_count, const unsigned* __restrict__ keys, Combine cmb, int top_m,
-    unsigned long long n_range, const unsigned long long* flag_count, unsigned long long flag_cap,
-    PartRec* __restrict__ part, TopEnt* __restrict__ part_top) {
+    const float* __restrict__ cb, unsigned long long cap, unsigned long long seg,
+    const unsigned long long* __restrict__ ids, const unsigned long long* cand_count,
+    const unsigned* __restrict__ keys, Combine cmb, int top_m, unsigned long long n_range,
+    const unsigned long long* flag_count, unsigned long long flag_cap, PartRec* __restrict__ part,
+    TopEnt* __restrict__ part_top) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ RedScratch sc;
   __shared__ int s_tcnt[2];
@@ -271,10 +271,11 @@ __global__ void __launch_bounds__(RED_NT, 6) k_reduce_candidates(
     s_seed[1] = fused_threshold(keys[cmb.top], cmb.top, cmb.top);
   }
   __syncthreads();
-  reduce_core<float, true>((unsigned long long)blockIdx.x * RED_NT + threadIdx.x,
-                           (unsigned long long)gridDim.x * RED_NT, cb, cb + cap, cb + 2 * cap, 0,
-                           ids, cand_count, cap, 0, cmb, top_m, 0, s_seed, part + blockIdx.x,
-                           part_top + (size_t)blockIdx.x * 2 * top_m, smem, sc, s_tcnt);
+  const unsigned long long o = (unsigned long long)blockIdx.x * seg;
+  reduce_core<float, true>(threadIdx.x, RED_NT, cb + o, cb + cap + o, cb + 2 * cap + o, 0,
+                           ids + o, cand_count + blockIdx.x, seg, 0, cmb, top_m, 0, s_seed,
+                           part + blockIdx.x, part_top + (size_t)blockIdx.x * 2 * top_m, smem,
+                           sc, s_tcnt);
   if (threadIdx.x == 0) {
     // same thread as the partial's writer in reduce_core
     PartRec* r = part + blockIdx.x;
@@ -289,19 +290,17 @@ __global__ void __launch_bounds__(RED_NT, 6) k_reduce_candidates(
 cudaError_t launch_reduce_candidates(const NpletArgs& a, int num_sms, int max_blocks,
                                      PartRec* part, TopEnt* part_top, cudaStream_t s,
                                      int* grid_out) {
+  (void)num_sms;
   const size_t sm =
       a.top_m > 0 ? (size_t)RTOP_CAP * 2 * (sizeof(float) + sizeof(unsigned long long)) : 0;
   int occ = 0;
   cudaError_t e = occupancy_cached((const void*)k_reduce_candidates, RED_NT, sm, &occ);
   if (e != cudaSuccess) return e;
-  long long grid = (long long)num_sms * occ;
-  if (grid > CAND_MAX_BLOCKS) grid = CAND_MAX_BLOCKS;
-  if (grid > max_blocks) grid = max_blocks;
-  if (grid < 1) grid = 1;
-  k_reduce_candidates<<<(unsigned)grid, RED_NT, sm, s>>>(
-      a.cand_b, a.cand_cap, a.cand_ids, a.cand_count, a.thr_keys, a.cmb, a.top_m,
+  if (a.cand_nseg < 1 || a.cand_nseg > max_blocks) return cudaErrorInvalidValue;
+  k_reduce_candidates<<<(unsigned)a.cand_nseg, RED_NT, sm, s>>>(
+      a.cand_b, a.cand_cap, a.cand_seg, a.cand_ids, a.cand_count, a.thr_keys, a.cmb, a.top_m,
       a.rank_end - a.rank_begin, a.flag_count, a.flag_cap, part, part_top);
-  if (grid_out) *grid_out = (int)grid;
+  if (grid_out) *grid_out = a.cand_nseg;
   return cudaGetLastError();
 }
 

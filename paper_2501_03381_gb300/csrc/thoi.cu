@@ -84,6 +84,7 @@ struct thoi_ctx {
   // the candidate list (ids, and three FP32 basis arrays of fz_cap entries)
   unsigned char* fz = nullptr;
   unsigned long long fz_cap = 0;
+  int fz_used = 0;  // the last measure pass used fused records
   // profiling: event pairs around launches, by class (0 nplet, 1 refactor, 2 merge, 3 reduce)
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;
@@ -584,8 +585,11 @@ constexpr int REFACTOR_BLOCKS_PER_SM = 2;
 constexpr unsigned long long LAUNCH_SPLIT = 0xffffffffull;  // ranks per launch (u32 local ids)
 constexpr unsigned long long PIECE = 1ull << 28;  // FP32 records path: nplets per basis piece
 constexpr unsigned long long FUSE_MIN_N = 1ull << 20;  // automatic fused records from this size
-constexpr int FUSE_CAND_BLOCKS = 64;                   // candidate-reduction partials per slot
-constexpr size_t FZ_HEAD = 256 * 13;  // MAX_SLOTS counters, then MAX_SLOTS x 10 keys (3 KB)
+constexpr int FUSE_CAND_BLOCKS = FUSE_NSEG;  // candidate-reduction partials per slot
+// head of the fused workspace: MAX_SLOTS x FUSE_NSEG segment counters (8 KB),
+// then MAX_SLOTS x 10 threshold keys (2.5 KB)
+constexpr size_t FZ_COUNTS = (size_t)MAX_SLOTS * FUSE_NSEG * 8;
+constexpr size_t FZ_HEAD = FZ_COUNTS + 2560 + 512;
 
 // Elements between the three basis arrays: the piece length rounded up to a
 // multiple of 64, so that every array is 256-byte aligned.
@@ -661,9 +665,15 @@ static thoi_status finish_status(thoi_ctx* c, cudaStream_t s, int n_slots, thoi_
   CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (n_slots > 0)
     CK(cudaMemcpyAsync(fc, c->flag_counts, n_slots * 8, cudaMemcpyDeviceToHost, s));
+  std::vector<unsigned long long> cc;
+  if (c->fz_used && c->fz) {
+    cc.resize((size_t)MAX_SLOTS * FUSE_NSEG);
+    CK(cudaMemcpyAsync(cc.data(), c->fz, cc.size() * 8, cudaMemcpyDeviceToHost, s));
+  }
   CK(cudaStreamSynchronize(s));
-  unsigned long long nref = 0;
+  unsigned long long nref = 0, ncand = 0;
   for (int i = 0; i < n_slots; i++) nref += fc[i] < c->flag_cap ? fc[i] : c->flag_cap;
+  for (auto x : cc) ncand += x;
   double ms[4] = {0, 0, 0, 0};
   for (int i = 0; i < c->ev_used; i++) {
     float t = 0.f;
@@ -681,6 +691,7 @@ static thoi_status finish_status(thoi_ctx* c, cudaStream_t s, int n_slots, thoi_
     stats->refactor_ms = ms[1];
     stats->merge_ms = ms[2];
     stats->reduce_ms = ms[3];
+    stats->n_candidates = ncand;
   }
   if (hs_out) *hs_out = hs;
   if (hs & ST_FLAG_OVERFLOW) return THOI_ERR_WORKSPACE;
@@ -717,13 +728,28 @@ static thoi_status ensure_parts(thoi_ctx* c, size_t n32, size_t n64, int top_m) 
   return THOI_OK;
 }
 
-// Fused records workspace for slots of up to max_n nplets: the candidate
-// list holds 1/24 of them (the sample bounds pass about 1.2% in expectation),
-// at least 2^16 entries; each array starts on a 256-byte boundary.
-static thoi_status ensure_fused_ws(thoi_ctx* c, unsigned long long max_n) {
-  unsigned long long cap = max_n / 24 + 1;
-  if (cap < (1ull << 16)) cap = 1ull << 16;
-  cap = (cap + 63) / 64 * 64;
+// Candidate-list entries for a fused slot of n nplets.  The sample bounds of
+// the top lists pass, per side, about 6 / (samples per block) of the nplets
+// (the smallest of 256 block maxima), and each extreme of the other measures
+// about n / S; three times the expected count, at least 2^16, at most n.
+static unsigned long long fused_cand_cap(unsigned long long n, int top_m) {
+  const unsigned long long grid = top_m > 256 ? (unsigned long long)top_m : 256ull;
+  unsigned long long S = grid * 128ull * (unsigned long long)fused_sample_per_thread(n, top_m);
+  if (S > n) S = n;
+  const double per_block = (double)S / (double)grid;
+  const double expect = 2.0 * 6.0 * (double)n / (per_block > 1.0 ? per_block : 1.0) +
+                        10.0 * (double)n / (double)(S > 0 ? S : 1);
+  unsigned long long cap = (unsigned long long)(3.0 * expect) + (1ull << 16);
+  return cap < n ? cap : n;
+}
+
+// Fused records workspace for candidate lists of up to cap entries, cut
+// into FUSE_NSEG segments; every array and segment starts on a 256-byte
+// boundary.
+static thoi_status ensure_fused_ws(thoi_ctx* c, unsigned long long cap_need) {
+  unsigned long long seg = (cap_need + FUSE_NSEG - 1) / FUSE_NSEG;
+  seg = (seg + 63) / 64 * 64;
+  const unsigned long long cap = seg * FUSE_NSEG;
   if (c->fz && c->fz_cap >= cap) return THOI_OK;
   free_ptr(c->fz);
   c->fz = nullptr;
@@ -733,7 +759,7 @@ static thoi_status ensure_fused_ws(thoi_ctx* c, unsigned long long max_n) {
   return THOI_OK;
 }
 static unsigned long long* fz_counts(thoi_ctx* c) { return (unsigned long long*)c->fz; }
-static unsigned* fz_keys(thoi_ctx* c) { return (unsigned*)(c->fz + 512); }
+static unsigned* fz_keys(thoi_ctx* c) { return (unsigned*)(c->fz + FZ_COUNTS); }
 static unsigned long long* fz_ids(thoi_ctx* c) { return (unsigned long long*)(c->fz + FZ_HEAD); }
 static float* fz_basis(thoi_ctx* c) { return (float*)(c->fz + FZ_HEAD + (size_t)c->fz_cap * 8); }
 
@@ -761,10 +787,16 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
     if (n == 0 || n > PIECE || r.k > 32) return false;
     return c->opt.records_mode == THOI_RECORDS_FUSED || n >= FUSE_MIN_N;
   };
-  for (auto& r : slots)
-    if (fused_slot(r) && r.r1 - r.r0 > maxn_fused) maxn_fused = r.r1 - r.r0;
+  unsigned long long cand_need = 0;
+  for (auto& r : slots) {
+    if (!fused_slot(r)) continue;
+    const unsigned long long n = r.r1 - r.r0;
+    if (n > maxn_fused) maxn_fused = n;
+    const unsigned long long cc = fused_cand_cap(n, c->opt.top_m);
+    if (cc > cand_need) cand_need = cc;
+  }
   if (maxn_fused > 0) {
-    st = ensure_fused_ws(c, maxn_fused);
+    st = ensure_fused_ws(c, cand_need);
     if (st != THOI_OK) return st;
   }
   if (!f64) {
@@ -800,6 +832,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(c->flag_counts, 0, MAX_SLOTS * sizeof(unsigned long long), s));
   if (maxn_fused > 0) CK(cudaMemsetAsync(c->fz, 0, FZ_HEAD, s));  // counters and keys
+  c->fz_used = maxn_fused > 0;
 
   MergeDescs D;
   memset(&D, 0, sizeof D);
@@ -823,8 +856,10 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       a.thr_keys = fz_keys(c) + (size_t)si * FUSE_NTHR;
       a.cand_ids = fz_ids(c);
       a.cand_b = fz_basis(c);
-      a.cand_count = fz_counts(c) + si;
+      a.cand_count = fz_counts(c) + (size_t)si * FUSE_NSEG;
       a.cand_cap = c->fz_cap;
+      a.cand_nseg = FUSE_NSEG;
+      a.cand_seg = c->fz_cap / FUSE_NSEG;
       a.part = c->part32 + p32_off;
       int grid = 0;
       st = prof_begin(c, s, 3);
@@ -1342,27 +1377,19 @@ extern "C" thoi_status thoi_group_measures(thoi_ctx* const* ctxs, int32_t D, con
 
 // ------------------------------------------------------------------ API: batch
 // Multi-dataset batch plan: descriptors, workspace and the CUDA graph of one
-// (contexts, kmin, kmax) combination.  Per order k, the slots (dataset d
-// with k <= N_d) are cut into nplet tiles of BATCH_TILE ranks; tiles are
-// grouped into pieces of at most BATCH_PIECE nplets (the basis buffer holds
-// one piece), and runs of BATCH_RTILE ranks of one slot inside one piece
-// form the reduction tiles.  Graph per order and piece: the batched nplet
-// launch, then the batched reduction; per order: the batched FP64 re-factor
-// of the flagged nplets and its list reduction; at the end one merge over
-// every (dataset, order) pair.  Plans are cached by context serial numbers,
-// so a repeated call replays the graph.
+// (contexts, kmin, kmax) combination.  Every (dataset d, order k <= N_d)
+// pair is a slot; every slot is cut into tiles of BATCH_TILE ranks.  The
+// tiles of all slots form one list, largest orders first, and one launch of
+// the persistent batched kernel per band of orders (one launch when kmax <=
+// 8) evaluates and reduces them all, each tile into its own partial record.
+// Then, per order, the batched FP64 re-factor of the flagged nplets; one list
+// reduction over every slot; one merge over every (dataset, order) pair.
+// Plans are cached by context serial numbers, so a repeated call replays the
+// graph.
 namespace {
 
 constexpr unsigned long long BATCH_TILE = 1ull << 16;
-constexpr unsigned long long BATCH_RTILE = 1ull << 18;
-constexpr unsigned long long BATCH_PIECE = 1ull << 27;
 constexpr int BATCH_CACHE = 4;
-
-struct BatchLaunch {
-  int k;
-  int tile0, n_tiles;
-  int rt0, n_rt;
-};
 
 struct BatchPlan {
   std::vector<unsigned long long> serials;
@@ -1378,6 +1405,7 @@ struct BatchPlan {
   std::vector<unsigned long long> flag_caps;
   int n_slots = 0;
   int launches = 0;
+  int nplet_launches = 0;
   unsigned long long nplets = 0;
 };
 
@@ -1423,6 +1451,66 @@ static thoi_status plan_alloc(BatchPlan* p, T** ptr, size_t n) {
   return THOI_OK;
 }
 
+static int batch_band_of(int k) {
+  for (int b = 0; b < BATCH_BANDS; b++)
+    if (k >= BATCH_BAND_LO[b] && k <= BATCH_BAND_HI[b]) return b;
+  return -1;
+}
+
+// Autotune cache key of the batched kernel's per-order chunk (nplets per
+// thread per round), tuned on a batch: GPU, SM count, order, mask width.
+static std::string batch_tune_key(const char* gpu, int sms, int k, int wide) {
+  return tune_key(gpu, sms, k, wide) + "|batch";
+}
+
+// Time the batched kernel on the tiles [t0, t1) of one order with each
+// chunk in {1, 2, 4, 8} (after a warm-up run) and cache the fastest.
+static thoi_status batch_tune_order(thoi_ctx* c0, int k, bool wide, BatchFArgs b,
+                                    const BatchFTile* d_tiles, int t0, int t1, int maxN,
+                                    unsigned* counter) {
+  cudaStream_t s = nullptr;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int best_chunk = 8;
+  float best = -1.f;
+  const int chunks[4] = {8, 4, 2, 1};
+  b.tiles = d_tiles + t0;
+  b.n_tiles = t1 - t0;
+  b.tile_counter = counter;
+  for (int ci = 0; ci < 4 && e == cudaSuccess; ci++) {
+    b.chunk_k[k] = chunks[ci];
+    for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+      e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess)
+        e = launch_batch_fused(batch_band_of(k), wide, b, maxN, 0, c0->num_sms, s, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e == cudaSuccess && rep == 1 && (best < 0.f || t < best)) {
+        best = t;
+        best_chunk = chunks[ci];
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  Shape sh;
+  sh.blocks_per_sm = 0;
+  sh.chunk = best_chunk;
+  sh.lanes = 1;
+  sh.prefix = 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[batch_tune_key(c0->gpu_name, c0->num_sms, k, wide)] = sh;
+  g_tune_gen++;
+  return THOI_OK;
+}
+
 static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
                                BatchPlan* P) {
   cudaStream_t s = nullptr;
@@ -1445,16 +1533,15 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
     hds[d].tau_tr = c->opt.trace_tau;
     hds[d].pad = 0;
   }
-  // slots by order; flag regions restart at 0 for every order (the re-factor
-  // of order k runs before the nplet launch of order k + 1)
+  // slots by order; every slot has its own region of the flag list (all
+  // orders run in one launch)
   std::vector<BatchSlot> hsl;
   std::vector<int> slot0(no, 0), nslot(no, 0);
   std::vector<int> slot_of(D * no, -1);  // (d, q) -> slot
-  unsigned long long lstride = 64;
+  unsigned long long foff = 0;
   for (int q = 0; q < no; q++) {
     const int k = kmin + q;
     slot0[q] = (int)hsl.size();
-    unsigned long long foff = 0;
     for (int d = 0; d < D; d++) {
       const thoi_ctx* c = ctxs[d];
       if (k > c->N) continue;
@@ -1471,7 +1558,7 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
         cap = c->opt.flag_capacity;
       } else {
         cap = sl.n / 16 + 1;
-        if (cap < (1ull << 16)) cap = 1ull << 16;
+        if (cap < (1ull << 12)) cap = 1ull << 12;
       }
       if (cap > sl.n) cap = sl.n;
       sl.flag_off = foff;
@@ -1483,75 +1570,54 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
       P->nplets += sl.n;
     }
     nslot[q] = (int)hsl.size() - slot0[q];
-    if (foff > lstride) lstride = foff;
   }
+  const unsigned long long lstride = foff > 64 ? foff : 64;
   const int n_slots = (int)hsl.size();
   P->n_slots = n_slots;
   for (auto& sl : hsl) P->flag_caps.push_back(sl.flag_cap);
-  // tiles, pieces, reduction tiles
-  std::vector<BatchTile> htiles;
-  std::vector<BatchRTile> hrt;
-  std::vector<BatchLaunch> launches;
-  std::vector<int> rt_first(n_slots, -1), rt_count(n_slots, 0);
-  unsigned long long bstride = 64;
-  for (int q = 0; q < no; q++) {
-    if (nslot[q] == 0) continue;
-    BatchLaunch L;
-    L.k = kmin + q;
-    L.tile0 = (int)htiles.size();
-    L.rt0 = (int)hrt.size();
-    unsigned long long boff = 0;
-    auto close_piece = [&]() {
-      L.n_tiles = (int)htiles.size() - L.tile0;
-      L.n_rt = (int)hrt.size() - L.rt0;
-      if (L.n_tiles > 0) launches.push_back(L);
-      if (boff > bstride) bstride = boff;
-      L.tile0 = (int)htiles.size();
-      L.rt0 = (int)hrt.size();
-      boff = 0;
-    };
-    for (int si = slot0[q]; si < slot0[q] + nslot[q]; si++) {
-      const BatchSlot& sl = hsl[si];
-      for (unsigned long long r0 = 0; r0 < sl.n; r0 += BATCH_TILE) {
-        const unsigned long long n = sl.n - r0 < BATCH_TILE ? sl.n - r0 : BATCH_TILE;
-        const unsigned long long nal = (n + 63) / 64 * 64;
-        if (boff + nal > BATCH_PIECE) close_piece();
-        BatchTile t;
-        t.r0 = r0;
-        t.boff = boff;
-        t.n = (unsigned)n;
-        t.slot = si;
-        // a reduction tile starts at a multiple of BATCH_RTILE ranks or at
-        // the first tile of a piece; it grows by whole nplet tiles
-        const bool starts = hrt.empty() || (int)hrt.size() == L.rt0 || hrt.back().slot != si ||
-                            r0 % BATCH_RTILE == 0;
-        if (starts) {
-          BatchRTile r;
-          r.boff = boff;
-          r.n = n;
-          r.id0 = sl.id_base + r0;
-          r.slot = si;
-          r.pad = 0;
-          if (rt_first[si] < 0) rt_first[si] = (int)hrt.size();
-          rt_count[si]++;
-          hrt.push_back(r);
-        } else {
-          hrt.back().n += n;
-        }
-        htiles.push_back(t);
-        boff += nal;
-      }
+  // tiles: partial indices slot-major (a slot's partials are contiguous),
+  // list order by order descending (then slot)
+  std::vector<BatchFTile> htiles;
+  std::vector<int> pfirst(n_slots, 0), pcount(n_slots, 0);
+  int np = 0;
+  for (int si = 0; si < n_slots; si++) {
+    pfirst[si] = np;
+    for (unsigned long long r0 = 0; r0 < hsl[si].n; r0 += BATCH_TILE) {
+      BatchFTile t;
+      t.r0 = r0;
+      t.n = (unsigned)(hsl[si].n - r0 < BATCH_TILE ? hsl[si].n - r0 : BATCH_TILE);
+      t.slot = si;
+      t.pidx = np++;
+      t.k = hsl[si].k;
+      htiles.push_back(t);
     }
-    close_piece();
+    pcount[si] = np - pfirst[si];
   }
-  // merge descriptors: every (dataset, order) pair, records in output order
+  std::stable_sort(htiles.begin(), htiles.end(),
+                   [](const BatchFTile& a, const BatchFTile& b) { return a.k > b.k; });
+  // band ranges of the sorted list
+  int band_t0[BATCH_BANDS], band_t1[BATCH_BANDS];
+  for (int b = 0; b < BATCH_BANDS; b++) band_t0[b] = band_t1[b] = 0;
+  for (int b = 0; b < BATCH_BANDS; b++) {
+    int t0 = -1, t1 = -1;
+    for (int t = 0; t < (int)htiles.size(); t++)
+      if (batch_band_of(htiles[t].k) == b) {
+        if (t0 < 0) t0 = t;
+        t1 = t + 1;
+      }
+    if (t0 >= 0) {
+      band_t0[b] = t0;
+      band_t1[b] = t1;
+    }
+  }
+  // merge descriptors: every (dataset, order) pair, records in output order;
+  // FP64 list partials: B2 blocks per slot
   const int B2 = [&]() {
-    int b = D > 0 ? (2 * num_sms) / D : 1;
+    int b = n_slots > 0 ? (2 * num_sms) / n_slots : 1;
     if (b < 1) b = 1;
     if (b > 8) b = 8;
     return b;
   }();
-  int bx_ref = 2 * num_sms;
   const size_t per = thoi_records_bytes(no, top_m);
   P->per = per;
   std::vector<MergeDesc> hmd(D * no);
@@ -1563,8 +1629,8 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
       m.k = kmin + q;
       const int si = slot_of[d * no + q];
       if (si >= 0) {
-        m.p32_off = rt_first[si];
-        m.g32 = rt_count[si];
+        m.p32_off = pfirst[si];
+        m.g32 = pcount[si];
         m.p64_off = si * B2;
         m.g64 = B2;
         m.cmb = hsl[si].cmb;
@@ -1576,35 +1642,32 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
   thoi_status st;
   BatchDataset* d_ds;
   BatchSlot* d_sl;
-  BatchTile* d_tiles;
-  BatchRTile* d_rt;
+  BatchFTile* d_tiles;
   MergeDesc* d_md;
   thoi_order_record** d_recp;
   TopEnt** d_topp;
-  float* basis;
   double* b64;
   unsigned long long* flag_ids;
   PartRec *part32, *part64;
   TopEnt *top32, *top64;
-  const size_t n_rt = hrt.size();
+  unsigned* counters;
   const size_t n64 = (size_t)n_slots * B2;
   if ((st = plan_alloc(P, &d_ds, D)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &d_sl, n_slots)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &d_tiles, htiles.size())) != THOI_OK) return st;
-  if ((st = plan_alloc(P, &d_rt, n_rt)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &d_md, hmd.size())) != THOI_OK) return st;
   if ((st = plan_alloc(P, &d_recp, hmd.size())) != THOI_OK) return st;
   if ((st = plan_alloc(P, &d_topp, hmd.size())) != THOI_OK) return st;
-  if ((st = plan_alloc(P, &basis, 3 * (size_t)bstride)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &b64, 3 * (size_t)lstride)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &flag_ids, (size_t)lstride)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &P->flag_counts, (size_t)n_slots)) != THOI_OK) return st;
-  if ((st = plan_alloc(P, &part32, n_rt)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &part32, (size_t)np)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &part64, n64)) != THOI_OK) return st;
-  if ((st = plan_alloc(P, &top32, n_rt * 2 * (size_t)top_m)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &top32, (size_t)np * 2 * (size_t)top_m)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &top64, n64 * 2 * (size_t)top_m)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &P->staging, per * (size_t)D)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &P->status, 1)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &counters, BATCH_BANDS + 1)) != THOI_OK) return st;
   for (int d = 0; d < D; d++) {
     for (int q = 0; q < no; q++) {
       const int si = slot_of[d * no + q];
@@ -1622,32 +1685,60 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
     }
   CK(cudaMemcpy(d_ds, hds.data(), hds.size() * sizeof(BatchDataset), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_sl, hsl.data(), hsl.size() * sizeof(BatchSlot), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(d_tiles, htiles.data(), htiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(d_rt, hrt.data(), hrt.size() * sizeof(BatchRTile), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_tiles, htiles.data(), htiles.size() * sizeof(BatchFTile),
+                cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_md, hmd.data(), hmd.size() * sizeof(MergeDesc), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_recp, hrecp.data(), hrecp.size() * sizeof(void*), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_topp, htopp.data(), htopp.size() * sizeof(void*), cudaMemcpyHostToDevice));
-  // launch shapes (occupancy queried before the capture)
-  std::vector<size_t> smem_k(no, 0);
-  std::vector<int> grid_k(no, 0), chunk_k(no, 8);
+  // kernel arguments; per-order chunks from the batch autotune cache, tuned
+  // here on this batch where missing (when the contexts autotune)
+  BatchFArgs ba;
+  memset(&ba, 0, sizeof ba);
+  ba.ds = d_ds;
+  ba.slots = d_sl;
+  ba.top_m = top_m;
+  ba.binom = c0->binom;
+  ba.flag_ids = flag_ids;
+  ba.flag_counts = P->flag_counts;
+  ba.part = part32;
+  ba.part_top = top32;
+  ba.status = P->status;
+  ba.cancel = c0->d_cancel;
+  for (int k = 0; k <= KBATCH_MAX; k++) ba.chunk_k[k] = 8;
   for (int q = 0; q < no; q++) {
-    if (nslot[q] == 0) continue;
     const int k = kmin + q;
-    int occ = 0;
-    CK(batch_nplet_occupancy(k, wide, maxN, &smem_k[q], &occ));
-    const Shape sh = shape_for(c0, k);
-    if (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ) occ = sh.blocks_per_sm;
-    grid_k[q] = num_sms * (occ > 0 ? occ : 1);
-    chunk_k[q] = sh.chunk > 0 && sh.chunk <= 8 ? sh.chunk : 8;
+    if (nslot[q] == 0) continue;
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(batch_tune_key(c0->gpu_name, num_sms, k, wide));
+      if (it != g_tune.end()) {
+        ba.chunk_k[k] = it->second.chunk;
+        have = true;
+      }
+    }
+    if (!have && c0->opt.autotune) {
+      int t0 = -1, t1 = -1;
+      for (int t = 0; t < (int)htiles.size(); t++)
+        if (htiles[t].k == k) {
+          if (t0 < 0) t0 = t;
+          t1 = t + 1;
+        }
+      if (t0 >= 0) {
+        st = batch_tune_order(c0, k, wide, ba, d_tiles, t0, t1, maxN, counters + BATCH_BANDS);
+        if (st != THOI_OK) return st;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        ba.chunk_k[k] = g_tune[batch_tune_key(c0->gpu_name, num_sms, k, wide)].chunk;
+      }
+    }
   }
   {
-    size_t sm = 0;
-    int occ = 0;
-    CK(batch_reduce_occupancy(top_m, &sm, &occ));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    P->tune_gen = g_tune_gen;
   }
   // capture on a private stream (the caller's may be the legacy default
   // stream, which cannot be captured); the graph is launched on the caller's
-  int nl = 0;
+  int nl = 0, nnl = 0;
   cudaStream_t cs = nullptr;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   s = cs;
@@ -1662,40 +1753,33 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
   };
   ok(cudaMemsetAsync(P->status, 0, sizeof(int), s));
   ok(cudaMemsetAsync(P->flag_counts, 0, (size_t)(n_slots > 0 ? n_slots : 1) * 8, s));
-  size_t li = 0;
+  ok(cudaMemsetAsync(counters, 0, (BATCH_BANDS + 1) * sizeof(unsigned), s));
+  // the nplets: one persistent launch per band, largest orders first
+  for (int b = BATCH_BANDS - 1; b >= 0 && e == cudaSuccess; b--) {
+    if (band_t1[b] <= band_t0[b]) continue;
+    BatchFArgs bb = ba;
+    bb.tiles = d_tiles + band_t0[b];
+    bb.n_tiles = band_t1[b] - band_t0[b];
+    bb.tile_counter = counters + b;
+    ok(launch_batch_fused(b, wide, bb, maxN, 0, num_sms, s, nullptr));
+    nl++;
+    nnl++;
+  }
+  // FP64 re-factor of the flagged nplets, per order (its launch shape depends
+  // on k), then one list reduction over every slot
   for (int q = 0; q < no && e == cudaSuccess; q++) {
     if (nslot[q] == 0) continue;
     const int k = kmin + q;
-    for (; li < launches.size() && launches[li].k == k && e == cudaSuccess; li++) {
-      const BatchLaunch& L = launches[li];
-      BatchArgs b;
-      memset(&b, 0, sizeof b);
-      b.ds = d_ds;
-      b.slots = d_sl;
-      b.tiles = d_tiles + L.tile0;
-      b.n_tiles = L.n_tiles;
-      b.binom = c0->binom;
-      b.basis = basis;
-      b.bstride = bstride;
-      b.flag_ids = flag_ids;
-      b.flag_counts = P->flag_counts;
-      b.status = P->status;
-      b.cancel = c0->d_cancel;
-      const int grid = grid_k[q] < L.n_tiles ? grid_k[q] : L.n_tiles;
-      ok(launch_nplet_batch(k, wide, b, smem_k[q], grid, chunk_k[q], s));
-      ok(launch_reduce_batch(basis, bstride, d_rt + L.rt0, L.n_rt, d_sl, top_m, part32 + L.rt0,
-                             top32 + (size_t)L.rt0 * 2 * top_m, s));
-      nl += 2;
-    }
-    int bx = bx_ref / nslot[q];
+    int bx = (2 * num_sms) / nslot[q];
     if (bx < 1) bx = 1;
     if (bx > 64) bx = 64;
     ok(launch_refactor_batch(d_ds, d_sl, slot0[q], nslot[q], maxN, k, wide, c0->binom, flag_ids,
                              P->flag_counts, b64, lstride, P->status, bx, s));
-    ok(launch_reduce_list_batch(b64, lstride, d_sl, slot0[q], nslot[q], flag_ids, P->flag_counts,
-                                top_m, part64, top64, B2, s));
-    nl += 2;
+    nl++;
   }
+  ok(launch_reduce_list_batch(b64, lstride, d_sl, 0, n_slots, flag_ids, P->flag_counts, top_m,
+                              part64, top64, B2, s));
+  nl++;
   ok(launch_merge_arr(d_md, D * no, gmax, part32, top32, part64, top64, top_m, d_recp, d_topp, s));
   nl++;
   cudaGraph_t g = nullptr;
@@ -1710,6 +1794,7 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
   P->graph = g;
   CK(cudaGraphInstantiate(&P->exec, g, 0));
   P->launches = nl;
+  P->nplet_launches = nnl;
   return THOI_OK;
 }
 
@@ -1743,7 +1828,6 @@ static thoi_status batch_graph(thoi_ctx* const* ctxs, int32_t D, int32_t kmin, i
     P->kmax = kmax;
     P->top_m = c0->opt.top_m;
     P->device = c0->device;
-    P->tune_gen = tg;
     const thoi_status st = batch_build(ctxs, D, kmin, kmax, P);
     if (st != THOI_OK) {
       plan_free(P);
