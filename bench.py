@@ -540,6 +540,7 @@ def run_extra(args, dev, stream, flush, peak, rank, fp64_peak):
         _, st = P.thoi_batch_measures(hs, 3, 8, top_m=TOP_M)
         graph_ms = st.nplet_ms
         launches = st.launches
+        nplet_launches = st.nplet_launches
     finally:
         for c in ctxs + [prof]:
             c.close()
@@ -548,9 +549,10 @@ def run_extra(args, dev, stream, flush, peak, rank, fp64_peak):
     ach = fl / (graph_ms / 1e3) / 1e12
     entry = {"workload": "64 datasets, N ~ U{10..40}, T ~ U{200..2000} (seeds 3000+d), orders "
                          f"3..min(N,8) ({n:,} nplets), per-order records with top-256 lists, "
-                         "one replayed CUDA graph",
+                         "one replayed CUDA graph around one persistent nplet launch",
              "value": n / (ms / 1e3), "unit": "nplets/s", "ms_per_call": ms,
              "graph_ms": graph_ms, "gpu_launches_per_call": launches,
+             "nplet_launches_per_call": nplet_launches,
              "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                           "frac": ach / peak, "flops_per_call": fl,
                           "kernel": "whole graph (nplet, reduction, re-factor, merge)"}}

@@ -151,7 +151,8 @@ typedef struct {
   uint64_t n_refactored; /* nplets re-computed in FP64 */
   uint64_t n_not_pd;     /* nplets not positive definite */
   int32_t launches;      /* kernel launches queued by the call */
-  int32_t pad;
+  int32_t nplet_launches;/* thoi_batch_measures: launches of the batched nplet kernel
+                            (one per band of orders: 1..8, 9..14, 15..17, 18..20) */
   /* device time in milliseconds, measured with CUDA events when opt.profile = 1
      (otherwise 0): the nplet kernels (FP32 or FP64 path), the FP64 re-factor
      kernels, the merge, and the streaming reduction */

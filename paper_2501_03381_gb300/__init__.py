@@ -56,7 +56,7 @@ class thoi_options(ctypes.Structure):
 class thoi_stats(ctypes.Structure):
     _fields_ = [("nplets", ctypes.c_uint64), ("n_refactored", ctypes.c_uint64),
                 ("n_not_pd", ctypes.c_uint64), ("launches", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("nplet_ms", ctypes.c_double),
+                ("nplet_launches", ctypes.c_int32), ("nplet_ms", ctypes.c_double),
                 ("refactor_ms", ctypes.c_double), ("merge_ms", ctypes.c_double),
                 ("reduce_ms", ctypes.c_double), ("fused_retries", ctypes.c_int32),
                 ("pad2", ctypes.c_int32), ("n_candidates", ctypes.c_uint64)]

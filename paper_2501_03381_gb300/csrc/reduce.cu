@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(RED_NT, 6) k_reduce_candidates(
   reduce_core<float, true>(threadIdx.x, RED_NT, cb + o, cb + cap + o, cb + 2 * cap + o, 0,
                            ids + o, cand_count + blockIdx.x, seg, 0, cmb, top_m, 0, s_seed,
                            part + blockIdx.x, part_top + (size_t)blockIdx.x * 2 * top_m, smem,
-                           sc, s_tcnt);
+                           sc, s_tcnt, 2654435761ull);
   if (threadIdx.x == 0) {
     // same thread as the partial's writer in reduce_core
     PartRec* r = part + blockIdx.x;

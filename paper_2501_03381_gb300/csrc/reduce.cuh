@@ -31,7 +31,8 @@ __device__ void reduce_core(unsigned long long first, unsigned long long step,
                                                          PartRec* __restrict__ part,
                                                          TopEnt* __restrict__ part_top,
                                                          unsigned char* smem, RedScratch& sc,
-                                                         int* s_tcnt) {
+                                                         int* s_tcnt,
+                                                         unsigned long long scramble = 0) {
   using I = typename std::conditional<LIST, unsigned long long, unsigned>::type;
   const bool with_top = top_m > 0;
   TopBuf<V, I> tb;
@@ -67,7 +68,22 @@ __device__ void reduce_core(unsigned long long first, unsigned long long step,
     if (q < nq) {
       const unsigned long long e0 = q * RB_PER_THREAD;
       V lr[RB_PER_THREAD], sp[RB_PER_THREAD], ls[RB_PER_THREAD];
-      if (sizeof(V) == 4 && e0 + RB_PER_THREAD <= n) {
+      unsigned long long pos[RB_PER_THREAD];
+#pragma unroll
+      for (int t = 0; t < RB_PER_THREAD; t++) pos[t] = e0 + t;
+      if (LIST && scramble) {
+        // a list read in the order e -> e * scramble mod n (a permutation when
+        // the multiplier is a prime not dividing n): values that trend along
+        // the list do not keep refilling the top buffers
+#pragma unroll
+        for (int t = 0; t < RB_PER_THREAD; t++) {
+          const bool ok = e0 + t < n;
+          pos[t] = ok ? ((e0 + t) * scramble) % n : 0ull;
+          lr[t] = ok ? blr[pos[t]] : pinf<V>() - pinf<V>();
+          sp[t] = ok ? bsp[pos[t]] : (V)0;
+          ls[t] = ok ? bls[pos[t]] : (V)0;
+        }
+      } else if (sizeof(V) == 4 && e0 + RB_PER_THREAD <= n) {
 #pragma unroll
         for (int g = 0; g < RB_VEC; g++) {
           const float4 fx = reinterpret_cast<const float4*>(blr)[q * RB_VEC + g];
@@ -96,7 +112,7 @@ __device__ void reduce_core(unsigned long long first, unsigned long long step,
         V v[5];
         combine5<V>(lr[t], sp[t], ls[t], cmbv, v);
         if (LIST) {
-          const I id = (I)ids[e0 + t];
+          const I id = (I)ids[pos[t]];
           tr.add(v, id, lr[t], sp[t], ls[t]);
           if (with_top) top_offer(tb, pick5(v, cmb.top), id, thr_hi, thr_lo);
         } else {
@@ -112,12 +128,10 @@ __device__ void reduce_core(unsigned long long first, unsigned long long step,
       __syncthreads();
       const bool c0 = tb.cnt[0] > trigger, c1 = tb.cnt[1] > trigger;
       if (c0) {
-        top_sort_cut(tb, 0, top_m);
-        thr_hi = top_threshold(tb, 0, top_m);
+        thr_hi = top_select_cut(tb, 0, top_m);
       }
       if (c1) {
-        top_sort_cut(tb, 1, top_m);
-        thr_lo = top_threshold(tb, 1, top_m);
+        thr_lo = top_select_cut(tb, 1, top_m);
       }
       // every thread has read the counts before anyone appends again
       __syncthreads();

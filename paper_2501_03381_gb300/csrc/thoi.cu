@@ -1558,7 +1558,7 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
         cap = c->opt.flag_capacity;
       } else {
         cap = sl.n / 16 + 1;
-        if (cap < (1ull << 12)) cap = 1ull << 12;
+        if (cap < (1ull << 16)) cap = 1ull << 16;
       }
       if (cap > sl.n) cap = sl.n;
       sl.flag_off = foff;
@@ -1866,6 +1866,7 @@ static thoi_status batch_graph(thoi_ctx* const* ctxs, int32_t D, int32_t kmin, i
     stats->nplets = P->nplets;
     stats->n_refactored = nref;
     stats->launches = P->launches;
+    stats->nplet_launches = P->nplet_launches;
     stats->nplet_ms = ms;
   }
   if (hs & ST_FLAG_OVERFLOW) return THOI_ERR_WORKSPACE;
