@@ -89,10 +89,12 @@ __device__ __forceinline__ void bfused_tile(const BatchFArgs& b, const BatchFTil
       __syncthreads();
       const bool c0 = tb.cnt[0] > BF_TRIGGER, c1 = tb.cnt[1] > BF_TRIGGER;
       if (c0) {
-        thr_hi = top_select_cut(tb, 0, top_m);
+        top_sort_cut(tb, 0, top_m);
+        thr_hi = top_threshold(tb, 0, top_m);
       }
       if (c1) {
-        thr_lo = top_select_cut(tb, 1, top_m);
+        top_sort_cut(tb, 1, top_m);
+        thr_lo = top_threshold(tb, 1, top_m);
       }
       __syncthreads();
     }

@@ -101,6 +101,7 @@ struct NpletArgs {
   unsigned long long cand_cap;
   unsigned long long cand_seg;
   int cand_nseg;
+  unsigned char* cand_ws;  // selection workspace of the candidate reduction (cand_ws_bytes())
   // FP64 re-factor list (FP32 kernels append; the re-factor kernel reads)
   unsigned long long* flag_ids;
   unsigned long long* flag_count;
@@ -172,6 +173,8 @@ cudaError_t launch_reduce_basis64(const double* basis, unsigned long long stride
 // with atomicMax into thr_keys, which must be zero beforehand) ...
 cudaError_t launch_fused_sample(const NpletArgs& a, int num_sms, cudaStream_t s);
 int fused_sample_per_thread(unsigned long long n, int top_m);
+size_t cand_ws_bytes();
+int cand_partials(int nseg);  // partial records the candidate reduction writes
 constexpr int FUSE_NSEG = 16;  // candidate-list segments (and candidate-reduction blocks)
 // ... and, after the nplet launch, the reduction of the candidate list into
 // per-block partials holding the extremes and top lists only; block 0 also

@@ -399,169 +399,6 @@ __device__ void top_sort_cut(TopBuf<V, I>& tb, int side, int M) {
   __syncthreads();
 }
 
-// Keys that order a side's entries best first (larger key = better): the
-// value's order-preserving key, complemented for the side of the smallest
-// values.
-__device__ __forceinline__ unsigned long long side_key(float v, int side) {
-  unsigned u = __float_as_uint(v);
-  if ((u << 1) == 0) u = 0;
-  u = (u >> 31) ? ~u : (u | 0x80000000u);
-  return side == 0 ? (unsigned long long)u : (unsigned long long)(~u);
-}
-__device__ __forceinline__ unsigned long long side_key(double v, int side) {
-  const unsigned long long k = okey(v);
-  return side == 0 ? k : ~k;
-}
-
-// Digit of a radix select: the largest d with at least `need` counts in
-// bins d..255 of hist, and the count left to take inside bin d.  Warp 0 does
-// it: lane l sums bins 255 - 8l .. 248 - 8l, a shuffle scan finds the lane
-// whose bins hold the need-th count, and that lane walks its eight bins.
-__device__ __forceinline__ void radix_digit(const unsigned* hist, unsigned need, int* digit,
-                                            unsigned* left) {
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
-  const int hi = 255 - 8 * lane;
-  unsigned mine = 0;
-#pragma unroll
-  for (int b = 0; b < 8; b++) mine += hist[hi - b];
-  unsigned incl = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  const unsigned excl = incl - mine;
-  const bool here = excl < need && incl >= need;
-  const unsigned who = __ballot_sync(0xffffffffu, here);
-  const int src = who ? __ffs(who) - 1 : 31;
-  if (lane == src) {
-    unsigned cum = excl;
-    int d = hi - 7;
-    for (int b = 0; b < 8; b++) {
-      if (cum + hist[hi - b] >= need) {
-        d = hi - b;
-        break;
-      }
-      cum += hist[hi - b];
-    }
-    *digit = d;
-    *left = need - cum;
-  }
-}
-
-// Keep the best M entries of a side's buffer (value first, then the smaller
-// id), unsorted, and return the M-th best value, the new admission bound.
-// The M-th best key is found by a radix select (8-bit digits, most
-// significant first, shared-memory histograms); entries that tie with it
-// are cut by a second radix select on their ids.  Far cheaper than a full
-// sort of the buffer, so it can run whenever the buffer fills; the lists
-// are sorted once at the end (top_sort_cut).  Called by every thread of the
-// block; needs more than M entries in the buffer.
-template <typename V, typename I>
-__device__ V top_select_cut(TopBuf<V, I>& tb, int side, int M) {
-  constexpr int PER = TOP_CAP / RED_NT;
-  constexpr int KB = (int)sizeof(V) * 8;
-  constexpr int IB = (int)sizeof(I) * 8;
-  constexpr unsigned long long IMASK = IB == 64 ? ~0ull : ((1ull << IB) - 1ull);
-  __shared__ unsigned s_hist[256];
-  __shared__ int s_digit;
-  __shared__ unsigned s_need, s_pos;
-  __shared__ V s_val;
-  __syncthreads();
-  const int c = tb.cnt[side];
-  unsigned long long key[PER];
-  V val[PER];
-  I idv[PER];
-#pragma unroll
-  for (int q = 0; q < PER; q++) {
-    const int i = threadIdx.x + q * RED_NT;
-    if (i < c) {
-      val[q] = tb.val[side][i];
-      idv[q] = tb.idx[side][i];
-      key[q] = side_key(val[q], side);
-    }
-  }
-  // the M-th best key: at most M - 1 entries above it, at least M at or above
-  unsigned long long prefix = 0, mask = 0;
-  unsigned need = (unsigned)M;
-  for (int shift = KB - 8; shift >= 0; shift -= 8) {
-    for (int q = threadIdx.x; q < 256; q += RED_NT) s_hist[q] = 0;
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PER; q++) {
-      const int i = threadIdx.x + q * RED_NT;
-      if (i < c && (key[q] & mask) == prefix) atomicAdd(&s_hist[(key[q] >> shift) & 255], 1u);
-    }
-    __syncthreads();
-    radix_digit(s_hist, need, &s_digit, &s_need);
-    __syncthreads();
-    need = s_need;
-    prefix |= (unsigned long long)s_digit << shift;
-    mask |= 255ull << shift;
-  }
-  // entries with the M-th best key: keep the `need` smallest ids (their
-  // largest kept id by a radix select on complemented ids)
-  unsigned long long idcut = ~0ull, ipre = 0, imask = 0;
-  {
-    unsigned ties = 0;
-    for (int q = threadIdx.x; q < 256; q += RED_NT) s_hist[q] = 0;
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PER; q++) {
-      const int i = threadIdx.x + q * RED_NT;
-      ties += (i < c && key[q] == prefix) ? 1u : 0u;
-    }
-    if (ties) atomicAdd(&s_hist[0], ties);
-    __syncthreads();
-    const unsigned t_all = s_hist[0];
-    __syncthreads();
-    if (t_all > need) {
-      unsigned nd = need;
-      for (int shift = IB - 8; shift >= 0; shift -= 8) {
-        for (int q = threadIdx.x; q < 256; q += RED_NT) s_hist[q] = 0;
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PER; q++) {
-          const int i = threadIdx.x + q * RED_NT;
-          const unsigned long long ik = ~(unsigned long long)idv[q] & IMASK;  // larger = smaller id
-          if (i < c && key[q] == prefix && (ik & imask) == ipre)
-            atomicAdd(&s_hist[(ik >> shift) & 255], 1u);
-        }
-        __syncthreads();
-        radix_digit(s_hist, nd, &s_digit, &s_need);
-        __syncthreads();
-        nd = s_need;
-        ipre |= (unsigned long long)s_digit << shift;
-        imask |= 255ull << shift;
-      }
-      idcut = ~ipre & IMASK;  // the largest id kept among the ties
-    }
-  }
-  if (threadIdx.x == 0) s_pos = 0;
-  __syncthreads();
-  // compaction (every entry was read into registers above)
-#pragma unroll
-  for (int q = 0; q < PER; q++) {
-    const int i = threadIdx.x + q * RED_NT;
-    if (i < c) {
-      const bool keep =
-          key[q] > prefix || (key[q] == prefix && (unsigned long long)idv[q] <= idcut);
-      if (key[q] == prefix) s_val = val[q];
-      if (keep) {
-        const unsigned p = atomicAdd(&s_pos, 1u);
-        tb.val[side][p] = val[q];
-        tb.idx[side][p] = idv[q];
-      }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) tb.cnt[side] = M;
-  const V thr = s_val;
-  __syncthreads();
-  return thr;
-}
-
 template <typename V, typename I>
 __device__ __forceinline__ V top_threshold(const TopBuf<V, I>& tb, int side, int M) {
   if (tb.cnt[side] >= M) return tb.val[side][M - 1];

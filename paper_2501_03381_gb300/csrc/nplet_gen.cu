@@ -160,10 +160,12 @@ __global__ void __launch_bounds__(RED_NT) k_nplet_gen(const NpletArgs a) {
       // unordered, and the last sorted M-th entry stays a valid bound
       const bool c0 = tb.cnt[0] > trigger, c1 = tb.cnt[1] > trigger;
       if (c0) {
-        thr_hi = top_select_cut(tb, 0, a.top_m);
+        top_sort_cut(tb, 0, a.top_m);
+        thr_hi = top_threshold(tb, 0, a.top_m);
       }
       if (c1) {
-        thr_lo = top_select_cut(tb, 1, a.top_m);
+        top_sort_cut(tb, 1, a.top_m);
+        thr_lo = top_threshold(tb, 1, a.top_m);
       }
       __syncthreads();
     }
@@ -529,68 +531,36 @@ __device__ void merge_slot(const MergeDesc& d, const PartRec* __restrict__ p32ba
   __shared__ int s_have[MERGE_NT];
   __shared__ int s_total;
   for (int side = 0; side < 2; side++) {
-    // (a) threshold: the key of the want-th best entry over every list
-    // (want = min(M, entries)), found bit by bit from the top: K grows while
-    // at least `want` entries have a key >= K, each count a binary search per
-    // list (the lists are sorted best first).  The entries at least as good
-    // as that entry -- the top `want` and any that tie with the last one in
-    // value -- are the survivors.
+    // (a) threshold: the best M-th entry among the blocks with a full list.
+    // Such a block alone holds M entries at least that good, so the global
+    // top M is among the entries of all lists that are at least that good.
     {
-      auto skey = [&](double v) { return side == 0 ? dkey(v) : ~dkey(v); };
-      // entries in all lists
-      unsigned long long tot = 0;
+      TopEnt best;
+      best.v = 0.0;
+      best.id = ~0ull;
+      int have = 0;
       for (int b = threadIdx.x; b < G; b += MERGE_NT) {
         const PartRec& P = b < g32 ? p32[b] : p64[b - g32];
         const int nl = side == 0 ? P.top_hi : P.top_lo;
-        tot += nl > 0 ? (unsigned long long)nl : 0ull;
+        if (nl < top_m) continue;
+        const TopEnt* Lst = (b < g32 ? t32 + (size_t)b * 2 * top_m
+                                     : t64 + (size_t)(b - g32) * 2 * top_m) + (size_t)side * top_m;
+        const TopEnt e = Lst[top_m - 1];
+        if (!have || ent_before(side, e, best)) { best = e; have = 1; }
       }
-      s_cnt[threadIdx.x][0] = tot;
+      s_best[threadIdx.x] = best;
+      s_have[threadIdx.x] = have;
       __syncthreads();
       for (int h = MERGE_NT / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) s_cnt[threadIdx.x][0] += s_cnt[threadIdx.x + h][0];
+        if (threadIdx.x < h) {
+          const int o = threadIdx.x + h;
+          if (s_have[o] && (!s_have[threadIdx.x] || ent_before(side, s_best[o], s_best[threadIdx.x]))) {
+            s_best[threadIdx.x] = s_best[o];
+            s_have[threadIdx.x] = 1;
+          }
+        }
         __syncthreads();
       }
-      const unsigned long long all = s_cnt[0][0];
-      __syncthreads();
-      const unsigned long long want = all < (unsigned long long)top_m ? all : top_m;
-      unsigned long long K = 0;
-      if (want > 0) {
-        for (int bit = 63; bit >= 0; bit--) {
-          const unsigned long long Kt = K | (1ull << bit);
-          unsigned long long c = 0;
-          for (int b = threadIdx.x; b < G; b += MERGE_NT) {
-            const PartRec& P = b < g32 ? p32[b] : p64[b - g32];
-            const int nl = side == 0 ? P.top_hi : P.top_lo;
-            const TopEnt* Lst = (b < g32 ? t32 + (size_t)b * 2 * top_m
-                                         : t64 + (size_t)(b - g32) * 2 * top_m) +
-                                (size_t)side * top_m;
-            int lo = 0, hi = nl > 0 ? nl : 0;
-            while (lo < hi) {
-              const int mid = (lo + hi) >> 1;
-              if (skey(Lst[mid].v) >= Kt) lo = mid + 1;
-              else hi = mid;
-            }
-            c += (unsigned long long)lo;
-          }
-          s_cnt[threadIdx.x][0] = c;
-          __syncthreads();
-          for (int h = MERGE_NT / 2; h > 0; h >>= 1) {
-            if (threadIdx.x < h) s_cnt[threadIdx.x][0] += s_cnt[threadIdx.x + h][0];
-            __syncthreads();
-          }
-          if (s_cnt[0][0] >= want) K = Kt;
-          __syncthreads();
-        }
-      }
-      if (threadIdx.x == 0) {
-        // the value whose key is K, and the largest id: every tie survives
-        const unsigned long long dk = side == 0 ? K : ~K;
-        const unsigned long long u = (dk >> 63) ? (dk & 0x7fffffffffffffffull) : ~dk;
-        s_best[0].v = __longlong_as_double((long long)u);
-        s_best[0].id = ~0ull;
-        s_have[0] = want > 0 ? 1 : 0;
-      }
-      __syncthreads();
     }
     const bool have = s_have[0] != 0;
     const TopEnt thr = s_best[0];

@@ -249,41 +249,223 @@ static cudaError_t launch_reduce_t(const V* basis, unsigned long long stride_ele
   return cudaGetLastError();
 }
 
-// Candidate list of a fused-records order slot: block s reduces segment s
-// of the list (the FP32 list reduction), seeded with the slot's top-list
-// bounds (every nplet of the final top lists lies beyond them once the merge
-// certifies the record).  The partials carry the extremes and the top lists
-// only: the sums and the count of O < 0 came from the nplet kernel, and
-// block 0 carries the count of FP32 nplets (the rank range less the nplets
-// flagged for the FP64 re-factor).
-__global__ void __launch_bounds__(RED_NT, 6) k_reduce_candidates(
-    const float* __restrict__ cb, unsigned long long cap, unsigned long long seg,
-    const unsigned long long* __restrict__ ids, const unsigned long long* cand_count,
-    const unsigned* __restrict__ keys, Combine cmb, int top_m, unsigned long long n_range,
-    const unsigned long long* flag_count, unsigned long long flag_cap, PartRec* __restrict__ part,
-    TopEnt* __restrict__ part_top) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// Candidate list of a fused-records order slot (see nplet_common.cuh): the
+// extremes of every measure by a streaming pass, and the top-M lists of the
+// ranked measure by a radix select over the list -- a histogram of the top
+// 11 bits of the order-preserving key, the bin holding the M-th best, a
+// histogram of the next 11 bits inside it, then every entry at or beyond the
+// 22-bit bin so found (the top M and few more) gathered and sorted.  No
+// per-block top buffers are cut and recut, whatever the order of the list.
+// Partials: CAND_SUB blocks per segment carry the extremes (block 0 of
+// segment 0 also the count of FP32 nplets: the rank range less the flagged
+// ones), then one partial carries the two top lists.
+constexpr int CAND_SUB = 4;        // blocks per candidate segment
+constexpr int CAND_SURV = 8192;    // gathered entries per side, at most
+constexpr int CAND_BINS = 2048;
+constexpr size_t CW_HIST1 = 0;
+constexpr size_t CW_HIST2 = CW_HIST1 + 2 * CAND_BINS * 4;
+constexpr size_t CW_SEL = CW_HIST2 + 2 * CAND_BINS * 4;   // bin1[2], above1[2], bin2[2], above2[2], n[2]
+constexpr size_t CW_HEAD = CW_SEL + 256;                    // zeroed per slot
+constexpr size_t CW_SV = CW_HEAD;                           // float [2][CAND_SURV]
+constexpr size_t CW_SI = CW_SV + 2 * CAND_SURV * 4;         // u64 [2][CAND_SURV]
+constexpr size_t CW_BYTES = CW_SI + 2 * CAND_SURV * 8;
+
+size_t cand_ws_bytes() { return CW_BYTES; }
+int cand_partials(int nseg) { return nseg * CAND_SUB + 1; }
+
+__device__ __forceinline__ unsigned cand_key(float v, int side) {
+  const unsigned k = fkey(v);
+  return side == 0 ? k : ~k;
+}
+
+// pass 0: extremes, and the histogram of the top 11 key bits (both sides);
+// pass 1: inside the selected top bins, the histogram of the next 11 bits;
+// pass 2: gather the entries at or beyond the selected 22-bit bins.
+__global__ void __launch_bounds__(RED_NT) k_cand_pass(const NpletArgs a, unsigned char* __restrict__ ws,
+                                                      int pass, PartRec* __restrict__ part) {
+  __shared__ unsigned h[2][CAND_BINS];
   __shared__ RedScratch sc;
-  __shared__ int s_tcnt[2];
-  __shared__ float s_seed[2];
-  if (threadIdx.x == 0) {
-    s_seed[0] = fused_threshold(keys[5 + cmb.top], 5 + cmb.top, cmb.top);
-    s_seed[1] = fused_threshold(keys[cmb.top], cmb.top, cmb.top);
+  const int seg = blockIdx.y;
+  const unsigned long long cnt = a.cand_count[seg];
+  const unsigned long long n = cnt < a.cand_seg ? cnt : a.cand_seg;
+  const unsigned long long base = (unsigned long long)seg * a.cand_seg;
+  const float* cb = a.cand_b;
+  const CombineV<float> cv(a.cmb);
+  const int top = a.cmb.top;
+  unsigned* gh1 = reinterpret_cast<unsigned*>(ws + CW_HIST1);
+  unsigned* gh2 = reinterpret_cast<unsigned*>(ws + CW_HIST2);
+  const int* sel = reinterpret_cast<const int*>(ws + CW_SEL);
+  unsigned* nsurv = reinterpret_cast<unsigned*>(ws + CW_SEL) + 8;
+  float* sv = reinterpret_cast<float*>(ws + CW_SV);
+  unsigned long long* si = reinterpret_cast<unsigned long long*>(ws + CW_SI);
+  if (pass < 2) {
+    for (int q = threadIdx.x; q < 2 * CAND_BINS; q += RED_NT) (&h[0][0])[q] = 0;
+    __syncthreads();
+  }
+  ThreadRed<float, unsigned long long> tr;
+  tr.init();
+  // the selected bins (pass 1) and 22-bit thresholds (pass 2); a bin of -1
+  // means fewer than M entries on that side: everything is kept
+  int b1[2] = {0, 0};
+  unsigned t22[2] = {0u, 0u};
+  if (pass >= 1) {
+    for (int sd = 0; sd < 2; sd++) {
+      b1[sd] = sel[sd];
+      const int b2 = sel[4 + sd];
+      t22[sd] = (b1[sd] < 0 || b2 < 0) ? 0u : (((unsigned)b1[sd] << 11) | (unsigned)b2);
+    }
+  }
+  for (unsigned long long e = (unsigned long long)blockIdx.x * RED_NT + threadIdx.x; e < n;
+       e += (unsigned long long)gridDim.x * RED_NT) {
+    const unsigned long long p = base + e;
+    const float lr = cb[p], sp = cb[a.cand_cap + p], ls = cb[2 * a.cand_cap + p];
+    float v[5];
+    combine5<float>(lr, sp, ls, cv, v);
+    const float o = pick5(v, top);
+    if (pass == 0) {
+      tr.add(v, a.cand_ids[p], lr, sp, ls);
+      atomicAdd(&h[0][cand_key(o, 0) >> 21], 1u);
+      atomicAdd(&h[1][cand_key(o, 1) >> 21], 1u);
+    } else if (pass == 1) {
+#pragma unroll
+      for (int sd = 0; sd < 2; sd++) {
+        const unsigned k = cand_key(o, sd);
+        if (b1[sd] >= 0 && (int)(k >> 21) == b1[sd]) atomicAdd(&h[sd][(k >> 10) & 2047u], 1u);
+      }
+    } else {
+#pragma unroll
+      for (int sd = 0; sd < 2; sd++) {
+        if ((cand_key(o, sd) >> 10) >= t22[sd]) {
+          const unsigned q = atomicAdd(&nsurv[sd], 1u);
+          if (q < (unsigned)CAND_SURV) {
+            sv[sd * CAND_SURV + q] = o;
+            si[sd * CAND_SURV + q] = a.cand_ids[p];
+          } else {
+            atomicOr(a.status, ST_INEXACT);  // repeated with stored values
+          }
+        }
+      }
+    }
+  }
+  if (pass < 2) {
+    __syncthreads();
+    unsigned* g = pass == 0 ? gh1 : gh2;
+    for (int q = threadIdx.x; q < 2 * CAND_BINS; q += RED_NT) {
+      const unsigned c = (&h[0][0])[q];
+      if (c) atomicAdd(&g[q], c);
+    }
+  }
+  if (pass == 0) {
+    const int pidx = seg * gridDim.x + blockIdx.x;
+    block_write_part<float, unsigned long long>(tr, 0u, 0ull, sc, part + pidx, 0, 0);
+    if (threadIdx.x == 0) {
+      // same thread as the partial's writer
+      PartRec* r = part + pidx;
+      const unsigned long long fc = *a.flag_count;
+      r->s_lr = r->s_sp = r->s_ls = 0.0;
+      r->neg = 0;
+      r->notpd = 0;
+      r->count = pidx == 0 ? (a.rank_end - a.rank_begin) - (fc < a.flag_cap ? fc : a.flag_cap)
+                           : 0ull;
+    }
+  }
+}
+
+// The bin holding the target-th best of each side (warp w: side w).
+__global__ void k_cand_find(const NpletArgs a, unsigned char* __restrict__ ws, int pass) {
+  const int sd = threadIdx.x >> 5;
+  if (sd > 1) return;
+  const unsigned* hist = reinterpret_cast<const unsigned*>(ws + (pass == 0 ? CW_HIST1 : CW_HIST2)) +
+                         sd * CAND_BINS;
+  int* sel = reinterpret_cast<int*>(ws + CW_SEL);
+  const unsigned M = (unsigned)a.top_m;
+  unsigned target = M;
+  if (pass == 1) {
+    if (sel[sd] < 0) {
+      if ((threadIdx.x & 31) == 0) sel[4 + sd] = -1;
+      return;
+    }
+    target = M - (unsigned)sel[2 + sd];
+  }
+  __shared__ int s_bin[2];
+  __shared__ unsigned s_above[2];
+  seed_find_bin(hist, target, &s_bin[sd], &s_above[sd]);
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    sel[(pass == 0 ? 0 : 4) + sd] = s_bin[sd];
+    sel[(pass == 0 ? 2 : 6) + sd] = (int)s_above[sd];
+  }
+}
+
+// The gathered entries of side blockIdx.x sorted best first (value, then the
+// smaller id); the first M become the slot's top list.
+__global__ void __launch_bounds__(256) k_cand_final(const NpletArgs a, unsigned char* __restrict__ ws,
+                                                    PartRec* __restrict__ part,
+                                                    TopEnt* __restrict__ part_top) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int sd = blockIdx.x;
+  const unsigned* nsurv = reinterpret_cast<const unsigned*>(ws + CW_SEL) + 8;
+  const float* sv = reinterpret_cast<const float*>(ws + CW_SV) + sd * CAND_SURV;
+  const unsigned long long* si =
+      reinterpret_cast<const unsigned long long*>(ws + CW_SI) + (size_t)sd * CAND_SURV;
+  float* val = reinterpret_cast<float*>(smem);
+  unsigned long long* idx = reinterpret_cast<unsigned long long*>(smem + CAND_SURV * 4);
+  const int M = a.top_m;
+  const int c = nsurv[sd] < (unsigned)CAND_SURV ? (int)nsurv[sd] : CAND_SURV;
+  int P2 = 2;
+  while (P2 < c) P2 <<= 1;
+  const float sent = sd == 0 ? -pinf<float>() : pinf<float>();
+  for (int q = threadIdx.x; q < P2; q += blockDim.x) {
+    val[q] = q < c ? sv[q] : sent;
+    idx[q] = q < c ? si[q] : ~0ull;
   }
   __syncthreads();
-  const unsigned long long o = (unsigned long long)blockIdx.x * seg;
-  reduce_core<float, true>(threadIdx.x, RED_NT, cb + o, cb + cap + o, cb + 2 * cap + o, 0,
-                           ids + o, cand_count + blockIdx.x, seg, 0, cmb, top_m, 0, s_seed,
-                           part + blockIdx.x, part_top + (size_t)blockIdx.x * 2 * top_m, smem,
-                           sc, s_tcnt, 2654435761ull);
+  for (int kk = 2; kk <= P2; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & kk) == 0;
+          const float vi = val[i], vj = val[ixj];
+          const unsigned long long ii = idx[i], ij = idx[ixj];
+          const bool sw = up ? top_before(sd, vj, ij, vi, ii) : top_before(sd, vi, ii, vj, ij);
+          if (sw) {
+            val[i] = vj; val[ixj] = vi;
+            idx[i] = ij; idx[ixj] = ii;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const int nout = c < M ? c : M;
+  TopEnt* dst = part_top + (size_t)sd * M;
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    TopEnt e;
+    if (q < nout) {
+      e.v = (double)val[q];
+      e.id = idx[q];
+    } else {
+      e.v = 0.0;
+      e.id = ~0ull;
+    }
+    dst[q] = e;
+  }
   if (threadIdx.x == 0) {
-    // same thread as the partial's writer in reduce_core
-    PartRec* r = part + blockIdx.x;
-    const unsigned long long fc = *flag_count;
-    r->s_lr = r->s_sp = r->s_ls = 0.0;
-    r->neg = 0;
-    r->notpd = 0;
-    r->count = blockIdx.x == 0 ? n_range - (fc < flag_cap ? fc : flag_cap) : 0ull;
+    // the two blocks write disjoint fields of the one partial
+    if (sd == 0) {
+      for (int m = 0; m < 5; m++) {
+        part->vmin[m] = pinf<double>();
+        part->vmax[m] = -pinf<double>();
+        part->imin[m] = part->imax[m] = ~0ull;
+      }
+      part->s_lr = part->s_sp = part->s_ls = 0.0;
+      part->count = part->neg = part->notpd = 0;
+      part->top_hi = nout;
+      if (gridDim.x == 1) part->top_lo = 0;
+    } else {
+      part->top_lo = nout;
+    }
   }
 }
 
@@ -291,17 +473,32 @@ cudaError_t launch_reduce_candidates(const NpletArgs& a, int num_sms, int max_bl
                                      PartRec* part, TopEnt* part_top, cudaStream_t s,
                                      int* grid_out) {
   (void)num_sms;
-  const size_t sm =
-      a.top_m > 0 ? (size_t)RTOP_CAP * 2 * (sizeof(float) + sizeof(unsigned long long)) : 0;
-  int occ = 0;
-  cudaError_t e = occupancy_cached((const void*)k_reduce_candidates, RED_NT, sm, &occ);
+  const int np = cand_partials(a.cand_nseg);
+  if (a.cand_nseg < 1 || np > max_blocks || !a.cand_ws) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(a.cand_ws, 0, CW_HEAD, s);
   if (e != cudaSuccess) return e;
-  if (a.cand_nseg < 1 || a.cand_nseg > max_blocks) return cudaErrorInvalidValue;
-  k_reduce_candidates<<<(unsigned)a.cand_nseg, RED_NT, sm, s>>>(
-      a.cand_b, a.cand_cap, a.cand_seg, a.cand_ids, a.cand_count, a.thr_keys, a.cmb, a.top_m,
-      a.rank_end - a.rank_begin, a.flag_count, a.flag_cap, part, part_top);
-  if (grid_out) *grid_out = a.cand_nseg;
-  return cudaGetLastError();
+  const dim3 grid(CAND_SUB, (unsigned)a.cand_nseg);
+  k_cand_pass<<<grid, RED_NT, 0, s>>>(a, a.cand_ws, 0, part);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  PartRec* ptop = part + np - 1;
+  TopEnt* ttop = part_top ? part_top + (size_t)(np - 1) * 2 * a.top_m : nullptr;
+  const size_t sm = (size_t)CAND_SURV * (4 + 8);
+  static_assert((size_t)CAND_SURV * 12 <= 227 * 1024, "survivor sort exceeds shared memory");
+  int occ = 0;
+  if ((e = occupancy_cached((const void*)k_cand_final, 256, sm, &occ)) != cudaSuccess) return e;
+  if (a.top_m > 0) {
+    k_cand_find<<<1, 64, 0, s>>>(a, a.cand_ws, 0);
+    k_cand_pass<<<grid, RED_NT, 0, s>>>(a, a.cand_ws, 1, part);
+    k_cand_find<<<1, 64, 0, s>>>(a, a.cand_ws, 1);
+    k_cand_pass<<<grid, RED_NT, 0, s>>>(a, a.cand_ws, 2, part);
+    k_cand_final<<<2, 256, sm, s>>>(a, a.cand_ws, ptop, ttop);
+  } else {
+    // an empty top partial (no lists)
+    k_cand_final<<<1, 256, sm, s>>>(a, a.cand_ws, ptop, ttop);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (grid_out) *grid_out = np;
+  return cudaSuccess;
 }
 
 cudaError_t launch_reduce_basis(const float* basis, unsigned long long stride_elems,

@@ -128,10 +128,12 @@ __device__ void reduce_core(unsigned long long first, unsigned long long step,
       __syncthreads();
       const bool c0 = tb.cnt[0] > trigger, c1 = tb.cnt[1] > trigger;
       if (c0) {
-        thr_hi = top_select_cut(tb, 0, top_m);
+        top_sort_cut(tb, 0, top_m);
+        thr_hi = top_threshold(tb, 0, top_m);
       }
       if (c1) {
-        thr_lo = top_select_cut(tb, 1, top_m);
+        top_sort_cut(tb, 1, top_m);
+        thr_lo = top_threshold(tb, 1, top_m);
       }
       // every thread has read the counts before anyone appends again
       __syncthreads();

@@ -141,6 +141,9 @@ cudaError_t occupancy_cached(const void* fn, int block, size_t smem, int* occ) {
 // Process-wide: (GPU name, SM count, order, mask width) -> launch shape.
 static std::mutex g_tune_mu;
 static std::map<std::string, Shape> g_tune;
+// the batched kernel's per-order chunks, tuned on a batch (kept apart from
+// the single-dataset shapes, which the JSON cache holds)
+static std::map<std::string, Shape> g_tune_batch;
 static unsigned long long g_tune_gen = 0;  // bumped whenever g_tune changes
 
 static std::string tune_key(const char* gpu, int sms, int k, int wide) {
@@ -585,7 +588,7 @@ constexpr int REFACTOR_BLOCKS_PER_SM = 2;
 constexpr unsigned long long LAUNCH_SPLIT = 0xffffffffull;  // ranks per launch (u32 local ids)
 constexpr unsigned long long PIECE = 1ull << 28;  // FP32 records path: nplets per basis piece
 constexpr unsigned long long FUSE_MIN_N = 1ull << 20;  // automatic fused records from this size
-constexpr int FUSE_CAND_BLOCKS = FUSE_NSEG;  // candidate-reduction partials per slot
+const int FUSE_CAND_BLOCKS = cand_partials(FUSE_NSEG);  // candidate-reduction partials per slot
 // head of the fused workspace: MAX_SLOTS x FUSE_NSEG segment counters (8 KB),
 // then MAX_SLOTS x 10 threshold keys (2.5 KB)
 constexpr size_t FZ_COUNTS = (size_t)MAX_SLOTS * FUSE_NSEG * 8;
@@ -754,7 +757,7 @@ static thoi_status ensure_fused_ws(thoi_ctx* c, unsigned long long cap_need) {
   free_ptr(c->fz);
   c->fz = nullptr;
   c->fz_cap = 0;
-  CK(cudaMalloc(&c->fz, FZ_HEAD + (size_t)cap * 8 + (size_t)cap * 3 * 4));
+  CK(cudaMalloc(&c->fz, FZ_HEAD + (size_t)cap * 8 + (size_t)cap * 3 * 4 + cand_ws_bytes()));
   c->fz_cap = cap;
   return THOI_OK;
 }
@@ -762,6 +765,7 @@ static unsigned long long* fz_counts(thoi_ctx* c) { return (unsigned long long*)
 static unsigned* fz_keys(thoi_ctx* c) { return (unsigned*)(c->fz + FZ_COUNTS); }
 static unsigned long long* fz_ids(thoi_ctx* c) { return (unsigned long long*)(c->fz + FZ_HEAD); }
 static float* fz_basis(thoi_ctx* c) { return (float*)(c->fz + FZ_HEAD + (size_t)c->fz_cap * 8); }
+static unsigned char* fz_ws(thoi_ctx* c) { return c->fz + FZ_HEAD + (size_t)c->fz_cap * 20; }
 
 // Queue the whole measure pass (no synchronisation).  Used directly by the
 // batched entry point, which captures it into a CUDA graph.  With `fuse`,
@@ -860,6 +864,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       a.cand_cap = c->fz_cap;
       a.cand_nseg = FUSE_NSEG;
       a.cand_seg = c->fz_cap / FUSE_NSEG;
+      a.cand_ws = fz_ws(c);
       a.part = c->part32 + p32_off;
       int grid = 0;
       st = prof_begin(c, s, 3);
@@ -1506,8 +1511,7 @@ static thoi_status batch_tune_order(thoi_ctx* c0, int k, bool wide, BatchFArgs b
   sh.lanes = 1;
   sh.prefix = 0;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[batch_tune_key(c0->gpu_name, c0->num_sms, k, wide)] = sh;
-  g_tune_gen++;
+  g_tune_batch[batch_tune_key(c0->gpu_name, c0->num_sms, k, wide)] = sh;
   return THOI_OK;
 }
 
@@ -1711,8 +1715,8 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
     bool have = false;
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
-      auto it = g_tune.find(batch_tune_key(c0->gpu_name, num_sms, k, wide));
-      if (it != g_tune.end()) {
+      auto it = g_tune_batch.find(batch_tune_key(c0->gpu_name, num_sms, k, wide));
+      if (it != g_tune_batch.end()) {
         ba.chunk_k[k] = it->second.chunk;
         have = true;
       }
@@ -1728,7 +1732,7 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
         st = batch_tune_order(c0, k, wide, ba, d_tiles, t0, t1, maxN, counters + BATCH_BANDS);
         if (st != THOI_OK) return st;
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        ba.chunk_k[k] = g_tune[batch_tune_key(c0->gpu_name, num_sms, k, wide)].chunk;
+        ba.chunk_k[k] = g_tune_batch[batch_tune_key(c0->gpu_name, num_sms, k, wide)].chunk;
       }
     }
   }

@@ -104,3 +104,32 @@ def test_planted30_fused_records_match_stored_full_size():
         for x, y in ((ha[q], hb[q]), (la[q], lb[q])):
             np.testing.assert_array_equal(x["id"][:n], y["id"][:n])
             np.testing.assert_array_equal(x["value"][:n], y["value"][:n])
+
+
+@pytest.mark.parametrize("source", ["tensorcore", "from_f64"])
+def test_planted30_sigma32_sources_within_tolerance(source):
+    # the FP32 path from either FP32 covariance (the split-BF16 tensor-core
+    # GEMM, or the rounding of the FP64 one), with the FP64 re-factor on:
+    # sampled nplets of four orders of the N = 30 workload, including nplets
+    # that hold the whole synergy block (the worst conditioned), within 1e-4
+    X, _ = workloads.planted30()
+    S = oracle.copula_cov(X)
+    rng = np.random.default_rng(17)
+    others = [v for v in range(30) if not 10 <= v <= 19]
+    worst = 0.0
+    with P.Context(torch.as_tensor(X, device="cuda"), sigma32_source=source,
+                   out_f64=True) as c:
+        for k in (10, 15, 20, 25):
+            n = math.comb(30, k)
+            ids = set(rng.integers(0, n, 1500).tolist())
+            for _ in range(300):
+                extra = sorted(rng.choice(others, size=k - 10, replace=False).tolist())
+                ids.add(oracle.subset_rank(30, sorted(extra + list(range(10, 20)))))
+            ids = np.array(sorted(ids), dtype=np.int64)
+            out, _ = c.measures([k])
+            got = out[:, torch.as_tensor(ids, device="cuda")].cpu().numpy()
+            del out
+            ref, fl = oracle.measures_ids(S, [k], ids.astype(np.uint64))
+            assert not fl.any()
+            worst = max(worst, float(np.abs(got - ref).max()))
+    assert worst <= TOL32, worst
