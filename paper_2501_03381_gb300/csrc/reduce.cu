@@ -202,6 +202,8 @@ __global__ void __launch_bounds__(SEED_NT) k_seed_thresholds(const float* __rest
   }
 }
 
+constexpr unsigned long long RED_MIN_PER_BLOCK = 1ull << 14;
+
 template <typename V, bool LIST>
 __global__ void __launch_bounds__(RED_NT, 6) k_reduce_basis(
     const V* __restrict__ blr, const V* __restrict__ bsp, const V* __restrict__ bls,
@@ -237,8 +239,9 @@ static cudaError_t launch_reduce_t(const V* basis, unsigned long long stride_ele
   if (e != cudaSuccess) return e;
   long long grid = (long long)num_sms * occ;
   if (!LIST) {
-    const long long need =
-        (long long)((n + RED_NT * RB_PER_THREAD - 1) / (RED_NT * RB_PER_THREAD));
+    // at least 16K elements per block: a short range in many blocks would
+    // leave the merge many top lists of few entries each to sift
+    const long long need = (long long)((n + RED_MIN_PER_BLOCK - 1) / RED_MIN_PER_BLOCK);
     if (need < grid) grid = need > 0 ? need : 1;
   }
   if (grid > max_blocks) grid = max_blocks;
@@ -259,7 +262,7 @@ static cudaError_t launch_reduce_t(const V* basis, unsigned long long stride_ele
 // Partials: CAND_SUB blocks per segment carry the extremes (block 0 of
 // segment 0 also the count of FP32 nplets: the rank range less the flagged
 // ones), then one partial carries the two top lists.
-constexpr int CAND_SUB = 4;        // blocks per candidate segment
+constexpr int CAND_SUB = 12;       // blocks per candidate segment
 constexpr int CAND_SURV = 8192;    // gathered entries per side, at most
 constexpr int CAND_BINS = 2048;
 constexpr size_t CW_HIST1 = 0;

@@ -63,6 +63,15 @@ struct thoi_ctx {
   // workspace
   unsigned long long* flag_ids = nullptr;
   size_t flag_cap = 0;
+  // FP32 path: consecutive orders alternate between two re-factor lists (and
+  // their FP64 basis arrays), so that the FP64 re-factor of order k runs on
+  // a second stream while the FP32 kernel of order k + 1 fills the other list
+  unsigned long long* flag_ids2 = nullptr;
+  size_t flag_cap2 = 0;
+  double* b64_2 = nullptr;
+  size_t b64_2_cap = 0;
+  cudaStream_t s2 = nullptr;
+  std::vector<cudaEvent_t> sev;  // per-slot "list filled" and "re-factor done" events
   unsigned long long* flag_counts = nullptr;  // [MAX_SLOTS]
   PartRec* part32 = nullptr;
   TopEnt* top32 = nullptr;
@@ -395,6 +404,10 @@ extern "C" void thoi_destroy(thoi_ctx* c) {
   if (c->h_cancel) cudaFreeHost(c->h_cancel);
   for (auto e : c->ev) cudaEventDestroy(e);
   free_ptr(c->flag_ids);
+  free_ptr(c->flag_ids2);
+  free_ptr(c->b64_2);
+  for (auto e : c->sev) cudaEventDestroy(e);
+  if (c->s2) cudaStreamDestroy(c->s2);
   free_ptr(c->flag_counts);
   free_ptr(c->part32);
   free_ptr(c->top32);
@@ -585,6 +598,7 @@ struct SlotRange {
 constexpr int MAX_BLOCKS_PER_SM_RED = 8;   // cap for reduction launches (partials per block)
 constexpr int MAX_BLOCKS_PER_SM_OUT = 8;
 constexpr int REFACTOR_BLOCKS_PER_SM = 2;
+constexpr int LIST_RED_BLOCKS = 16;  // blocks of the re-factor list's reduction
 constexpr unsigned long long LAUNCH_SPLIT = 0xffffffffull;  // ranks per launch (u32 local ids)
 constexpr unsigned long long PIECE = 1ull << 28;  // FP32 records path: nplets per basis piece
 constexpr unsigned long long FUSE_MIN_N = 1ull << 20;  // automatic fused records from this size
@@ -635,7 +649,20 @@ static thoi_status ensure_flag_ws(thoi_ctx* c, unsigned long long max_slot_nplet
     if (a > max_slot_nplets) a = max_slot_nplets > 0 ? max_slot_nplets : 1;
     need = (size_t)a;
   }
-  return grow(&c->flag_ids, &c->flag_cap, need);
+  thoi_status st = grow(&c->flag_ids, &c->flag_cap, need);
+  if (st != THOI_OK) return st;
+  return grow(&c->flag_ids2, &c->flag_cap2, c->flag_cap);
+}
+
+// The second stream and the events of the overlapped FP64 re-factor.
+static thoi_status ensure_overlap(thoi_ctx* c, int n_slots) {
+  if (!c->s2) CK(cudaStreamCreateWithFlags(&c->s2, cudaStreamNonBlocking));
+  while ((int)c->sev.size() < 2 * n_slots + 1) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->sev.push_back(e);
+  }
+  return THOI_OK;
 }
 
 static NpletArgs base_args(thoi_ctx* c, const SlotRange& r) {
@@ -828,6 +855,10 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
                               : (size_t)3 * (((size_t)c->flag_cap + 63) / 64 * 64);
       st = grow(&c->b64, &c->b64_cap, need);
       if (st != THOI_OK) return st;
+      if (!f64) {
+        st = grow(&c->b64_2, &c->b64_2_cap, need);
+        if (st != THOI_OK) return st;
+      }
     }
     const size_t n64 = f64 ? 0 : slots.size() * (size_t)ref_cap;
     st = ensure_parts(c, n32, n64, top_m);
@@ -836,6 +867,13 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(c->flag_counts, 0, MAX_SLOTS * sizeof(unsigned long long), s));
   if (maxn_fused > 0) CK(cudaMemsetAsync(c->fz, 0, FZ_HEAD, s));  // counters and keys
+  // the FP64 re-factor of each order on a second stream (FP32 path, several
+  // orders): its FP64 work overlaps the next order's FP32 kernel
+  const bool overlap = !f64 && slots.size() > 1;
+  if (overlap) {
+    st = ensure_overlap(c, (int)slots.size());
+    if (st != THOI_OK) return st;
+  }
   c->fz_used = maxn_fused > 0;
 
   MergeDescs D;
@@ -850,10 +888,15 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
     md.p64_off = p64_off;
     md.refactored = f64 ? nullptr : c->flag_counts + si;
     const Shape sh = shape_for(c, r.k);
+    // this order's re-factor list (the two lists alternate between orders)
+    unsigned long long* const fids = (si & 1) ? c->flag_ids2 : c->flag_ids;
+    double* const fb64 = (si & 1) ? c->b64_2 : c->b64;
+    if (overlap && si >= 2) CK(cudaStreamWaitEvent(s, c->sev[2 * (si - 2) + 1], 0));
     if (fused_slot(r)) {
       // fused records: sample bounds, the nplet kernel reducing in place, the
       // candidate list's reduction
       NpletArgs a = base_args(c, r);
+      a.flag_ids = fids;
       a.flag_count = c->flag_counts + si;
       a.mode = 3;
       a.top_m = top_m;
@@ -900,6 +943,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         sub.r0 = a0;
         sub.r1 = r.r1 - a0 > PIECE ? a0 + PIECE : r.r1;
         NpletArgs a = base_args(c, sub);
+        a.flag_ids = fids;
         a.flag_count = c->flag_counts + si;
         a.mode = 2;
         a.out = c->basis;
@@ -960,6 +1004,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       sub.r0 = a0;
       sub.r1 = r.r1 - a0 > LAUNCH_SPLIT ? a0 + LAUNCH_SPLIT : r.r1;
       NpletArgs a = base_args(c, sub);
+      a.flag_ids = fids;
       a.flag_count = c->flag_counts + si;
       a.mode = red ? 1 : 0;
       a.top_m = top_m;
@@ -993,7 +1038,14 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
     }
     if (!f64 && r.r1 > r.r0) {
       // FP64 re-factor of this order's flagged nplets (count read on the device)
+      cudaStream_t sr = s;
+      if (overlap) {
+        CK(cudaEventRecord(c->sev[2 * si], s));
+        CK(cudaStreamWaitEvent(c->s2, c->sev[2 * si], 0));
+        sr = c->s2;
+      }
       NpletArgs a = base_args(c, r);
+      a.flag_ids = fids;
       a.flag_count = c->flag_counts + si;
       a.mode = red ? 1 : 0;
       a.top_m = top_m;
@@ -1009,37 +1061,45 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         // FP64 kernel over the list, then (records) the list reduction
         const unsigned long long lstride = ((unsigned long long)c->flag_cap + 63) / 64 * 64;
         a.mode = red ? 2 : 0;
-        st = prof_begin(c, s, 1);
+        st = prof_begin(c, sr, 1);
         if (st != THOI_OK) return st;
-        CK(launch_nplet_f64s(a, true, c->b64, lstride, c->num_sms, s, &grid,
+        CK(launch_nplet_f64s(a, true, fb64, lstride, c->num_sms, sr, &grid,
                              c->num_sms * MAX_BLOCKS_PER_SM_OUT));
-        st = prof_end(c, s);
+        st = prof_end(c, sr);
         if (st != THOI_OK) return st;
         launches++;
         if (red) {
-          st = prof_begin(c, s, 3);
+          st = prof_begin(c, sr, 3);
           if (st != THOI_OK) return st;
-          CK(launch_reduce_list64(c->b64, lstride, c->flag_ids, c->flag_counts + si, c->flag_cap,
-                                  md.cmb, top_m, c->part64 + p64_off,
+          // few blocks: the list is short next to the order, and each block's
+          // top lists then cover enough entries for the merge to keep few
+          CK(launch_reduce_list64(fb64, lstride, fids, c->flag_counts + si, c->flag_cap, md.cmb,
+                                  top_m, c->part64 + p64_off,
                                   top_m > 0 ? c->top64 + (size_t)p64_off * 2 * top_m : nullptr,
-                                  c->num_sms, ref_cap, s, &grid));
-          st = prof_end(c, s);
+                                  c->num_sms, LIST_RED_BLOCKS, sr, &grid));
+          st = prof_end(c, sr);
           if (st != THOI_OK) return st;
           launches++;
         }
       } else {
-        st = prof_begin(c, s, 1);
+        st = prof_begin(c, sr, 1);
         if (st != THOI_OK) return st;
-        CK(launch_refactor(a, c->num_sms, s, &grid, ref_cap));
-        st = prof_end(c, s);
+        CK(launch_refactor(a, c->num_sms, sr, &grid, ref_cap));
+        st = prof_end(c, sr);
         if (st != THOI_OK) return st;
         launches++;
       }
+      if (overlap) CK(cudaEventRecord(c->sev[2 * si + 1], sr));
       if (red) {
         p64_off += grid;
         md.g64 = grid;
       }
     }
+  }
+  if (overlap) {
+    // join: everything of the second stream before the merge and the return
+    CK(cudaEventRecord(c->sev[2 * slots.size()], c->s2));
+    CK(cudaStreamWaitEvent(s, c->sev[2 * slots.size()], 0));
   }
   if (red) {
     st = prof_begin(c, s, 2);
