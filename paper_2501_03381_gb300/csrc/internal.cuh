@@ -187,6 +187,26 @@ cudaError_t launch_reduce_list64(const double* basis, unsigned long long stride_
                                  unsigned long long cap, Combine cmb, int top_m, PartRec* part,
                                  TopEnt* part_top, int num_sms, int max_blocks, cudaStream_t s,
                                  int* grid_out);
+// Radix-select reductions (the candidate reduction's kernels on other
+// sources): every field of the record from one streaming pass, the top-M
+// lists from two histogram passes and one sort of the survivors.  More than
+// SEL_SURV survivors (values tied within 2^-13 relative of the M-th) raise
+// ST_INEXACT in *status: the request is then repeated with the streaming
+// reductions.  ws: sel_ws_bytes() of device memory, one per stream in flight.
+// A dense range of FP32 basis values (ids id0 + position; NaN = reduced from
+// the re-factor list):
+size_t sel_ws_bytes();
+cudaError_t launch_select_basis(const float* basis, unsigned long long stride_elems,
+                                unsigned long long n, unsigned long long id0, Combine cmb,
+                                int top_m, unsigned char* ws, int* status, PartRec* part,
+                                TopEnt* part_top, int max_blocks, cudaStream_t s, int* grid_out);
+// A re-factor list of FP64 basis values (count on the device, at most cap
+// entries; NaN = not positive definite):
+cudaError_t launch_select_list64(const double* basis, unsigned long long stride_elems,
+                                 const unsigned long long* ids, const unsigned long long* count,
+                                 unsigned long long cap, Combine cmb, int top_m,
+                                 unsigned char* ws, int* status, PartRec* part, TopEnt* part_top,
+                                 int max_blocks, cudaStream_t s, int* grid_out);
 // FP64 kernels with shared-memory matrices: one thread per nplet (G = 1) or
 // G lanes per nplet, 128 threads per block.
 struct F64Cfg {

@@ -10,6 +10,8 @@
 // Instances: FP32 values with dense ids (the FP32 path; NaN = re-factored in
 // FP64, skipped), FP64 values with dense ids (the FP64 path; NaN = not
 // positive definite) and FP64 values with ids from the re-factor list.
+#include <cstring>
+
 #include "reduce.cuh"
 
 namespace thoi {
@@ -252,61 +254,98 @@ static cudaError_t launch_reduce_t(const V* basis, unsigned long long stride_ele
   return cudaGetLastError();
 }
 
-// Candidate list of a fused-records order slot (see nplet_common.cuh): the
-// extremes of every measure by a streaming pass, and the top-M lists of the
-// ranked measure by a radix select over the list -- a histogram of the top
-// 11 bits of the order-preserving key, the bin holding the M-th best, a
-// histogram of the next 11 bits inside it, then every entry at or beyond the
-// 22-bit bin so found (the top M and few more) gathered and sorted.  No
-// per-block top buffers are cut and recut, whatever the order of the list.
-// Partials: CAND_SUB blocks per segment carry the extremes (block 0 of
-// segment 0 also the count of FP32 nplets: the rank range less the flagged
-// ones), then one partial carries the two top lists.
+// Radix-select reductions.  A source is a list of basis-value triples in
+// one or more segments: the candidate list of a fused-records order slot
+// (see nplet_common.cuh; FP32, explicit ids, 16 segments with device
+// counts), a dense range of FP32 basis values (ids from the position), or
+// an FP64 re-factor list (explicit ids, device count).  One streaming pass
+// gives the extremes of every measure, the sums and counts, and a
+// histogram of the top 11 bits of the order-preserving key of the ranked
+// measure (rounded to FP32: the rounding is monotone, so the key order
+// never contradicts the value order); the bin holding the M-th best, a
+// histogram of the next 11 bits inside it, then every entry at or beyond
+// the 22-bit bin so found (the top M and the few tied with them to 2^-13
+// relative) is gathered and sorted by value, then id.  No per-block top
+// buffers are cut and recut, whatever the order of the list.
+// Partials: SEL_SUB blocks (or the launch's count) per segment carry the
+// record fields, then one partial carries the two top lists.
 constexpr int CAND_SUB = 12;       // blocks per candidate segment
-constexpr int CAND_SURV = 8192;    // gathered entries per side, at most
+constexpr int SEL_SURV = 8192;     // gathered entries per side, at most
 constexpr int CAND_BINS = 2048;
 constexpr size_t CW_HIST1 = 0;
 constexpr size_t CW_HIST2 = CW_HIST1 + 2 * CAND_BINS * 4;
 constexpr size_t CW_SEL = CW_HIST2 + 2 * CAND_BINS * 4;   // bin1[2], above1[2], bin2[2], above2[2], n[2]
 constexpr size_t CW_HEAD = CW_SEL + 256;                    // zeroed per slot
-constexpr size_t CW_SV = CW_HEAD;                           // float [2][CAND_SURV]
-constexpr size_t CW_SI = CW_SV + 2 * CAND_SURV * 4;         // u64 [2][CAND_SURV]
-constexpr size_t CW_BYTES = CW_SI + 2 * CAND_SURV * 8;
+constexpr size_t CW_SV = CW_HEAD;                           // value [2][SEL_SURV] (8 B slots)
+constexpr size_t CW_SI = CW_SV + 2 * SEL_SURV * 8;          // u64 [2][SEL_SURV]
+constexpr size_t CW_BYTES = CW_SI + 2 * SEL_SURV * 8;
+constexpr unsigned long long SEL_PER_BLOCK = 8192;  // dense ranges: entries per pass block
+constexpr int SEL_LIST_BLOCKS = 48;                 // re-factor lists: pass blocks
 
 size_t cand_ws_bytes() { return CW_BYTES; }
+size_t sel_ws_bytes() { return CW_BYTES; }
 int cand_partials(int nseg) { return nseg * CAND_SUB + 1; }
+
+// One source of a select reduction.
+struct SelSrc {
+  const void* basis;                 // V: lr at [p], sp at [stride + p], lsum at [2 stride + p]
+  unsigned long long stride;
+  const unsigned long long* ids;     // id of entry p; null: id0 + p
+  unsigned long long id0;
+  const unsigned long long* counts;  // entries of each segment (device); null: n each
+  unsigned long long n;              // entries, or the capacity of a segment
+  unsigned long long seg_len;        // entry e of segment s sits at s * seg_len + e
+  int nseg;
+  int nan_notpd;                     // a NaN log det counts as not positive definite
+  int fused;                         // candidate list: partial 0 carries the FP32 count
+  unsigned long long rank_count;     // fused: ranks of the slot
+  const unsigned long long* flag_count;
+  unsigned long long flag_cap;
+  Combine cmb;
+  int top_m;
+  int* status;
+  unsigned char* ws;
+};
 
 __device__ __forceinline__ unsigned cand_key(float v, int side) {
   const unsigned k = fkey(v);
   return side == 0 ? k : ~k;
 }
 
-// pass 0: extremes, and the histogram of the top 11 key bits (both sides);
-// pass 1: inside the selected top bins, the histogram of the next 11 bits;
-// pass 2: gather the entries at or beyond the selected 22-bit bins.
-__global__ void __launch_bounds__(RED_NT) k_cand_pass(const NpletArgs a, unsigned char* __restrict__ ws,
-                                                      int pass, PartRec* __restrict__ part) {
+__device__ __forceinline__ unsigned long long sel_entries(const SelSrc& src, int seg) {
+  if (!src.counts) return src.n;
+  const unsigned long long c = src.counts[seg];
+  return c < src.n ? c : src.n;
+}
+
+// pass 0: record fields, and the histogram of the top 11 key bits (both
+// sides); pass 1: inside the selected top bins, the histogram of the next
+// 11 bits; pass 2: gather the entries at or beyond the selected 22-bit bins.
+template <typename V>
+__global__ void __launch_bounds__(RED_NT) k_sel_pass(const SelSrc src, int pass,
+                                                     PartRec* __restrict__ part) {
   __shared__ unsigned h[2][CAND_BINS];
   __shared__ RedScratch sc;
   const int seg = blockIdx.y;
-  const unsigned long long cnt = a.cand_count[seg];
-  const unsigned long long n = cnt < a.cand_seg ? cnt : a.cand_seg;
-  const unsigned long long base = (unsigned long long)seg * a.cand_seg;
-  const float* cb = a.cand_b;
-  const CombineV<float> cv(a.cmb);
-  const int top = a.cmb.top;
+  const unsigned long long n = sel_entries(src, seg);
+  const unsigned long long base = (unsigned long long)seg * src.seg_len;
+  const V* cb = static_cast<const V*>(src.basis);
+  const CombineV<V> cv(src.cmb);
+  const int top = src.cmb.top;
+  unsigned char* ws = src.ws;
   unsigned* gh1 = reinterpret_cast<unsigned*>(ws + CW_HIST1);
   unsigned* gh2 = reinterpret_cast<unsigned*>(ws + CW_HIST2);
   const int* sel = reinterpret_cast<const int*>(ws + CW_SEL);
   unsigned* nsurv = reinterpret_cast<unsigned*>(ws + CW_SEL) + 8;
-  float* sv = reinterpret_cast<float*>(ws + CW_SV);
+  V* sv = reinterpret_cast<V*>(ws + CW_SV);
   unsigned long long* si = reinterpret_cast<unsigned long long*>(ws + CW_SI);
   if (pass < 2) {
     for (int q = threadIdx.x; q < 2 * CAND_BINS; q += RED_NT) (&h[0][0])[q] = 0;
     __syncthreads();
   }
-  ThreadRed<float, unsigned long long> tr;
+  ThreadRed<V, unsigned long long> tr;
   tr.init();
+  unsigned notpd = 0;
   // the selected bins (pass 1) and 22-bit thresholds (pass 2); a bin of -1
   // means fewer than M entries on that side: everything is kept
   int b1[2] = {0, 0};
@@ -321,30 +360,38 @@ __global__ void __launch_bounds__(RED_NT) k_cand_pass(const NpletArgs a, unsigne
   for (unsigned long long e = (unsigned long long)blockIdx.x * RED_NT + threadIdx.x; e < n;
        e += (unsigned long long)gridDim.x * RED_NT) {
     const unsigned long long p = base + e;
-    const float lr = cb[p], sp = cb[a.cand_cap + p], ls = cb[2 * a.cand_cap + p];
-    float v[5];
-    combine5<float>(lr, sp, ls, cv, v);
-    const float o = pick5(v, top);
+    const V lr = cb[p], sp = cb[src.stride + p], ls = cb[2 * src.stride + p];
+    if (is_nan(lr)) {
+      notpd += src.nan_notpd ? 1u : 0u;
+      continue;
+    }
+    V v[5];
+    combine5<V>(lr, sp, ls, cv, v);
+    const V o = pick5(v, top);
+    const float fo = (float)o;
+    const unsigned long long id = src.ids ? src.ids[p] : src.id0 + p;
     if (pass == 0) {
-      tr.add(v, a.cand_ids[p], lr, sp, ls);
-      atomicAdd(&h[0][cand_key(o, 0) >> 21], 1u);
-      atomicAdd(&h[1][cand_key(o, 1) >> 21], 1u);
+      tr.add(v, id, lr, sp, ls);
+      if (src.top_m > 0) {
+        atomicAdd(&h[0][cand_key(fo, 0) >> 21], 1u);
+        atomicAdd(&h[1][cand_key(fo, 1) >> 21], 1u);
+      }
     } else if (pass == 1) {
 #pragma unroll
       for (int sd = 0; sd < 2; sd++) {
-        const unsigned k = cand_key(o, sd);
+        const unsigned k = cand_key(fo, sd);
         if (b1[sd] >= 0 && (int)(k >> 21) == b1[sd]) atomicAdd(&h[sd][(k >> 10) & 2047u], 1u);
       }
     } else {
 #pragma unroll
       for (int sd = 0; sd < 2; sd++) {
-        if ((cand_key(o, sd) >> 10) >= t22[sd]) {
+        if ((cand_key(fo, sd) >> 10) >= t22[sd]) {
           const unsigned q = atomicAdd(&nsurv[sd], 1u);
-          if (q < (unsigned)CAND_SURV) {
-            sv[sd * CAND_SURV + q] = o;
-            si[sd * CAND_SURV + q] = a.cand_ids[p];
+          if (q < (unsigned)SEL_SURV) {
+            sv[sd * SEL_SURV + q] = o;
+            si[sd * SEL_SURV + q] = id;
           } else {
-            atomicOr(a.status, ST_INEXACT);  // repeated with stored values
+            atomicOr(src.status, ST_INEXACT);  // repeated with the streaming reductions
           }
         }
       }
@@ -360,28 +407,29 @@ __global__ void __launch_bounds__(RED_NT) k_cand_pass(const NpletArgs a, unsigne
   }
   if (pass == 0) {
     const int pidx = seg * gridDim.x + blockIdx.x;
-    block_write_part<float, unsigned long long>(tr, 0u, 0ull, sc, part + pidx, 0, 0);
-    if (threadIdx.x == 0) {
-      // same thread as the partial's writer
+    block_write_part<V, unsigned long long>(tr, notpd, 0ull, sc, part + pidx, 0, 0);
+    if (src.fused && threadIdx.x == 0) {
+      // same thread as the partial's writer: the sums and the count of O < 0
+      // come from the nplet kernel's partials, the count from the rank range
       PartRec* r = part + pidx;
-      const unsigned long long fc = *a.flag_count;
+      const unsigned long long fc = *src.flag_count;
       r->s_lr = r->s_sp = r->s_ls = 0.0;
       r->neg = 0;
       r->notpd = 0;
-      r->count = pidx == 0 ? (a.rank_end - a.rank_begin) - (fc < a.flag_cap ? fc : a.flag_cap)
-                           : 0ull;
+      r->count = pidx == 0 ? src.rank_count - (fc < src.flag_cap ? fc : src.flag_cap) : 0ull;
     }
   }
 }
 
 // The bin holding the target-th best of each side (warp w: side w).
-__global__ void k_cand_find(const NpletArgs a, unsigned char* __restrict__ ws, int pass) {
+__global__ void k_sel_find(const SelSrc src, int pass) {
   const int sd = threadIdx.x >> 5;
   if (sd > 1) return;
+  unsigned char* ws = src.ws;
   const unsigned* hist = reinterpret_cast<const unsigned*>(ws + (pass == 0 ? CW_HIST1 : CW_HIST2)) +
                          sd * CAND_BINS;
   int* sel = reinterpret_cast<int*>(ws + CW_SEL);
-  const unsigned M = (unsigned)a.top_m;
+  const unsigned M = (unsigned)src.top_m;
   unsigned target = M;
   if (pass == 1) {
     if (sel[sd] < 0) {
@@ -402,22 +450,23 @@ __global__ void k_cand_find(const NpletArgs a, unsigned char* __restrict__ ws, i
 
 // The gathered entries of side blockIdx.x sorted best first (value, then the
 // smaller id); the first M become the slot's top list.
-__global__ void __launch_bounds__(256) k_cand_final(const NpletArgs a, unsigned char* __restrict__ ws,
-                                                    PartRec* __restrict__ part,
-                                                    TopEnt* __restrict__ part_top) {
+template <typename V>
+__global__ void __launch_bounds__(256) k_sel_final(const SelSrc src, PartRec* __restrict__ part,
+                                                   TopEnt* __restrict__ part_top) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = blockIdx.x;
+  unsigned char* ws = src.ws;
   const unsigned* nsurv = reinterpret_cast<const unsigned*>(ws + CW_SEL) + 8;
-  const float* sv = reinterpret_cast<const float*>(ws + CW_SV) + sd * CAND_SURV;
+  const V* sv = reinterpret_cast<const V*>(ws + CW_SV) + sd * SEL_SURV;
   const unsigned long long* si =
-      reinterpret_cast<const unsigned long long*>(ws + CW_SI) + (size_t)sd * CAND_SURV;
-  float* val = reinterpret_cast<float*>(smem);
-  unsigned long long* idx = reinterpret_cast<unsigned long long*>(smem + CAND_SURV * 4);
-  const int M = a.top_m;
-  const int c = nsurv[sd] < (unsigned)CAND_SURV ? (int)nsurv[sd] : CAND_SURV;
+      reinterpret_cast<const unsigned long long*>(ws + CW_SI) + (size_t)sd * SEL_SURV;
+  unsigned long long* idx = reinterpret_cast<unsigned long long*>(smem);
+  V* val = reinterpret_cast<V*>(smem + SEL_SURV * 8);
+  const int M = src.top_m;
+  const int c = nsurv[sd] < (unsigned)SEL_SURV ? (int)nsurv[sd] : SEL_SURV;
   int P2 = 2;
   while (P2 < c) P2 <<= 1;
-  const float sent = sd == 0 ? -pinf<float>() : pinf<float>();
+  const V sent = sd == 0 ? -pinf<V>() : pinf<V>();
   for (int q = threadIdx.x; q < P2; q += blockDim.x) {
     val[q] = q < c ? sv[q] : sent;
     idx[q] = q < c ? si[q] : ~0ull;
@@ -429,7 +478,7 @@ __global__ void __launch_bounds__(256) k_cand_final(const NpletArgs a, unsigned 
         const int ixj = i ^ j;
         if (ixj > i) {
           const bool up = (i & kk) == 0;
-          const float vi = val[i], vj = val[ixj];
+          const V vi = val[i], vj = val[ixj];
           const unsigned long long ii = idx[i], ij = idx[ixj];
           const bool sw = up ? top_before(sd, vj, ij, vi, ii) : top_before(sd, vi, ii, vj, ij);
           if (sw) {
@@ -472,36 +521,106 @@ __global__ void __launch_bounds__(256) k_cand_final(const NpletArgs a, unsigned 
   }
 }
 
-cudaError_t launch_reduce_candidates(const NpletArgs& a, int num_sms, int max_blocks,
-                                     PartRec* part, TopEnt* part_top, cudaStream_t s,
-                                     int* grid_out) {
-  (void)num_sms;
-  const int np = cand_partials(a.cand_nseg);
-  if (a.cand_nseg < 1 || np > max_blocks || !a.cand_ws) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(a.cand_ws, 0, CW_HEAD, s);
+// gx pass blocks per segment; partials: gx * nseg, then the top partial.
+template <typename V>
+static cudaError_t launch_select(const SelSrc& src, int gx, PartRec* part, TopEnt* part_top,
+                                 cudaStream_t s, int* grid_out) {
+  if (src.nseg < 1 || gx < 1 || !src.ws || !src.status) return cudaErrorInvalidValue;
+  const int np = gx * src.nseg + 1;
+  cudaError_t e = cudaMemsetAsync(src.ws, 0, CW_HEAD, s);
   if (e != cudaSuccess) return e;
-  const dim3 grid(CAND_SUB, (unsigned)a.cand_nseg);
-  k_cand_pass<<<grid, RED_NT, 0, s>>>(a, a.cand_ws, 0, part);
+  const dim3 grid((unsigned)gx, (unsigned)src.nseg);
+  k_sel_pass<V><<<grid, RED_NT, 0, s>>>(src, 0, part);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   PartRec* ptop = part + np - 1;
-  TopEnt* ttop = part_top ? part_top + (size_t)(np - 1) * 2 * a.top_m : nullptr;
-  const size_t sm = (size_t)CAND_SURV * (4 + 8);
-  static_assert((size_t)CAND_SURV * 12 <= 227 * 1024, "survivor sort exceeds shared memory");
+  TopEnt* ttop = part_top ? part_top + (size_t)(np - 1) * 2 * src.top_m : nullptr;
+  const size_t sm = (size_t)SEL_SURV * (8 + sizeof(V));
+  static_assert((size_t)SEL_SURV * 16 <= 227 * 1024, "survivor sort exceeds shared memory");
   int occ = 0;
-  if ((e = occupancy_cached((const void*)k_cand_final, 256, sm, &occ)) != cudaSuccess) return e;
-  if (a.top_m > 0) {
-    k_cand_find<<<1, 64, 0, s>>>(a, a.cand_ws, 0);
-    k_cand_pass<<<grid, RED_NT, 0, s>>>(a, a.cand_ws, 1, part);
-    k_cand_find<<<1, 64, 0, s>>>(a, a.cand_ws, 1);
-    k_cand_pass<<<grid, RED_NT, 0, s>>>(a, a.cand_ws, 2, part);
-    k_cand_final<<<2, 256, sm, s>>>(a, a.cand_ws, ptop, ttop);
+  if ((e = occupancy_cached((const void*)k_sel_final<V>, 256, sm, &occ)) != cudaSuccess) return e;
+  if (src.top_m > 0) {
+    k_sel_find<<<1, 64, 0, s>>>(src, 0);
+    k_sel_pass<V><<<grid, RED_NT, 0, s>>>(src, 1, part);
+    k_sel_find<<<1, 64, 0, s>>>(src, 1);
+    k_sel_pass<V><<<grid, RED_NT, 0, s>>>(src, 2, part);
+    k_sel_final<V><<<2, 256, sm, s>>>(src, ptop, ttop);
   } else {
     // an empty top partial (no lists)
-    k_cand_final<<<1, 256, sm, s>>>(a, a.cand_ws, ptop, ttop);
+    k_sel_final<V><<<1, 256, sm, s>>>(src, ptop, ttop);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (grid_out) *grid_out = np;
   return cudaSuccess;
+}
+
+cudaError_t launch_reduce_candidates(const NpletArgs& a, int num_sms, int max_blocks,
+                                     PartRec* part, TopEnt* part_top, cudaStream_t s,
+                                     int* grid_out) {
+  (void)num_sms;
+  if (a.cand_nseg < 1 || cand_partials(a.cand_nseg) > max_blocks) return cudaErrorInvalidValue;
+  SelSrc src;
+  memset(&src, 0, sizeof src);
+  src.basis = a.cand_b;
+  src.stride = a.cand_cap;
+  src.ids = a.cand_ids;
+  src.counts = a.cand_count;
+  src.n = a.cand_seg;
+  src.seg_len = a.cand_seg;
+  src.nseg = a.cand_nseg;
+  src.fused = 1;
+  src.rank_count = a.rank_end - a.rank_begin;
+  src.flag_count = a.flag_count;
+  src.flag_cap = a.flag_cap;
+  src.cmb = a.cmb;
+  src.top_m = a.top_m;
+  src.status = a.status;
+  src.ws = a.cand_ws;
+  return launch_select<float>(src, CAND_SUB, part, part_top, s, grid_out);
+}
+
+cudaError_t launch_select_basis(const float* basis, unsigned long long stride_elems,
+                                unsigned long long n, unsigned long long id0, Combine cmb,
+                                int top_m, unsigned char* ws, int* status, PartRec* part,
+                                TopEnt* part_top, int max_blocks, cudaStream_t s, int* grid_out) {
+  SelSrc src;
+  memset(&src, 0, sizeof src);
+  src.basis = basis;
+  src.stride = stride_elems;
+  src.id0 = id0;
+  src.n = n;
+  src.nseg = 1;
+  src.cmb = cmb;
+  src.top_m = top_m;
+  src.status = status;
+  src.ws = ws;
+  long long gx = (long long)((n + SEL_PER_BLOCK - 1) / SEL_PER_BLOCK);
+  if (gx < 1) gx = 1;
+  if (gx > max_blocks - 1) gx = max_blocks - 1;
+  if (gx < 1) return cudaErrorInvalidValue;
+  return launch_select<float>(src, (int)gx, part, part_top, s, grid_out);
+}
+
+cudaError_t launch_select_list64(const double* basis, unsigned long long stride_elems,
+                                 const unsigned long long* ids, const unsigned long long* count,
+                                 unsigned long long cap, Combine cmb, int top_m,
+                                 unsigned char* ws, int* status, PartRec* part, TopEnt* part_top,
+                                 int max_blocks, cudaStream_t s, int* grid_out) {
+  SelSrc src;
+  memset(&src, 0, sizeof src);
+  src.basis = basis;
+  src.stride = stride_elems;
+  src.ids = ids;
+  src.counts = count;
+  src.n = cap;
+  src.nseg = 1;
+  src.nan_notpd = 1;
+  src.cmb = cmb;
+  src.top_m = top_m;
+  src.status = status;
+  src.ws = ws;
+  const int gx = SEL_LIST_BLOCKS < max_blocks - 1 ? SEL_LIST_BLOCKS : max_blocks - 1;
+  if (gx < 1) return cudaErrorInvalidValue;
+  return launch_select<double>(src, gx, part, part_top, s, grid_out);
 }
 
 cudaError_t launch_reduce_basis(const float* basis, unsigned long long stride_elems,

@@ -94,6 +94,8 @@ struct thoi_ctx {
   unsigned char* fz = nullptr;
   unsigned long long fz_cap = 0;
   int fz_used = 0;  // the last measure pass used fused records
+  // radix-select workspaces: [0] the main stream, [1] the re-factor stream
+  unsigned char* sel_ws = nullptr;
   // profiling: event pairs around launches, by class (0 nplet, 1 refactor, 2 merge, 3 reduce)
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;
@@ -418,6 +420,7 @@ extern "C" void thoi_destroy(thoi_ctx* c) {
   free_ptr(c->basis);
   free_ptr(c->b64);
   free_ptr(c->seed_thr);
+  free_ptr(c->sel_ws);
   free_ptr(c->fz);
   free_ptr(c->grp);
   free_ptr(c->grp_meta);
@@ -788,6 +791,11 @@ static thoi_status ensure_fused_ws(thoi_ctx* c, unsigned long long cap_need) {
   c->fz_cap = cap;
   return THOI_OK;
 }
+static thoi_status ensure_sel_ws(thoi_ctx* c) {
+  if (c->sel_ws) return THOI_OK;
+  CK(cudaMalloc(&c->sel_ws, 2 * sel_ws_bytes()));
+  return THOI_OK;
+}
 static unsigned long long* fz_counts(thoi_ctx* c) { return (unsigned long long*)c->fz; }
 static unsigned* fz_keys(thoi_ctx* c) { return (unsigned*)(c->fz + FZ_COUNTS); }
 static unsigned long long* fz_ids(thoi_ctx* c) { return (unsigned long long*)(c->fz + FZ_HEAD); }
@@ -828,6 +836,13 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
   }
   if (maxn_fused > 0) {
     st = ensure_fused_ws(c, cand_need);
+    if (st != THOI_OK) return st;
+  }
+  // radix-select reductions (short stored ranges, re-factor lists) on the
+  // first pass of a records request; a repeat uses the streaming reductions
+  const bool sel = fuse && red && c->opt.records_mode != THOI_RECORDS_STORED;
+  if (sel) {
+    st = ensure_sel_ws(c);
     if (st != THOI_OK) return st;
   }
   if (!f64) {
@@ -958,10 +973,16 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         if (st != THOI_OK) return st;
         st = prof_begin(c, s, 3);
         if (st != THOI_OK) return st;
-        CK(launch_reduce_basis(c->basis, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb, top_m,
-                               c->seed_thr, c->part32 + p32_off,
-                               top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
-                               c->num_sms, blk_cap, s, &grid));
+        if (sel && sub.r1 - sub.r0 <= FUSE_MIN_N)
+          CK(launch_select_basis(c->basis, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb,
+                                 top_m, c->sel_ws, c->status, c->part32 + p32_off,
+                                 top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
+                                 blk_cap, s, &grid));
+        else
+          CK(launch_reduce_basis(c->basis, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb,
+                                 top_m, c->seed_thr, c->part32 + p32_off,
+                                 top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
+                                 c->num_sms, blk_cap, s, &grid));
         st = prof_end(c, s);
         if (st != THOI_OK) return st;
         launches += 2;
@@ -1071,12 +1092,21 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         if (red) {
           st = prof_begin(c, sr, 3);
           if (st != THOI_OK) return st;
-          // few blocks: the list is short next to the order, and each block's
-          // top lists then cover enough entries for the merge to keep few
-          CK(launch_reduce_list64(fb64, lstride, fids, c->flag_counts + si, c->flag_cap, md.cmb,
-                                  top_m, c->part64 + p64_off,
-                                  top_m > 0 ? c->top64 + (size_t)p64_off * 2 * top_m : nullptr,
-                                  c->num_sms, LIST_RED_BLOCKS, sr, &grid));
+          if (sel) {
+            CK(launch_select_list64(fb64, lstride, fids, c->flag_counts + si, c->flag_cap,
+                                    md.cmb, top_m, c->sel_ws + sel_ws_bytes(), c->status,
+                                    c->part64 + p64_off,
+                                    top_m > 0 ? c->top64 + (size_t)p64_off * 2 * top_m : nullptr,
+                                    ref_cap, sr, &grid));
+          } else {
+            // few blocks: the list is short next to the order, and each
+            // block's top lists then cover enough entries for the merge to
+            // keep few
+            CK(launch_reduce_list64(fb64, lstride, fids, c->flag_counts + si, c->flag_cap,
+                                    md.cmb, top_m, c->part64 + p64_off,
+                                    top_m > 0 ? c->top64 + (size_t)p64_off * 2 * top_m : nullptr,
+                                    c->num_sms, LIST_RED_BLOCKS, sr, &grid));
+          }
           st = prof_end(c, sr);
           if (st != THOI_OK) return st;
           launches++;

@@ -126,3 +126,34 @@ def test_fused_refactored_nplets_and_wide_masks():
     stored, st2 = _records(X, orders, "stored")
     assert st.n_refactored == st2.n_refactored > 0
     _same_records(fused, stored)
+
+
+@pytest.mark.parametrize("top_m", [0, 1, 256])
+def test_select_reductions_match_streaming(top_m):
+    # automatic mode on orders below the fused threshold: the stored FP32
+    # values and the FP64 re-factor lists reduced by radix select, against the
+    # streaming reductions of the stored mode (identical extremes and lists)
+    rng = np.random.default_rng(5)
+    S = workloads.random_corr(rng, 20)
+    X = rng.standard_normal((700, 20)) @ np.linalg.cholesky(S).T
+    X[:, 11] = X[:, 2] - X[:, 5] + 2e-3 * rng.standard_normal(700)
+    orders = [3, 4, 7, 10, 13, 19, 20]
+    auto, st = _records(X, orders, "auto", top_m=top_m)
+    stored, st2 = _records(X, orders, "stored", top_m=top_m)
+    assert st.fused_retries == 0
+    assert st.n_refactored == st2.n_refactored > 0
+    _same_records(auto, stored, mean_atol=1e-6, neg_slack=0)
+
+
+def test_select_falls_back_on_ties_in_auto_mode():
+    # Sigma = I: every O is exactly 0, so more than the select's survivors tie
+    # at the M-th value; the request is repeated with the streaming reductions
+    orders = [9, 10, 11]
+    with P.Context(Sigma=np.eye(20)) as c:
+        (recs, hi, lo), st = c.measures(orders, reduction="per_order")
+    assert st.fused_retries == 1
+    for q, k in enumerate(orders):
+        base = sum(math.comb(20, kk) for kk in orders[:q])
+        assert int(recs[q]["count"]) == math.comb(20, k)
+        np.testing.assert_array_equal(hi[q]["id"][:256], base + np.arange(256))
+        np.testing.assert_array_equal(lo[q]["id"][:256], base + np.arange(256))
