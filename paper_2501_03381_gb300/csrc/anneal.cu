@@ -80,7 +80,7 @@ __device__ double sa_measure(unsigned long long mask, const double* sR, int ldr,
   bool bad = false;
   for (int p = 0; p < k; p++) {
     const double d = SA(p, p);
-    bad |= !(d > 0.0);
+    bad |= !pivot_ok(d);
     P1 *= d;
     renorm(P1, E1, bad);
     const double rd = 1.0 / d;

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(RED_NT) k_grad(const NpletArgs a, const int me
       for (int p = 0; p < k; p++) {
         const V d = A[IXG(p, p)];
         pmin = d < pmin ? d : pmin;
-        bad |= !(d > (V)0);
+        bad |= !pivot_ok(d);
         const V inv = (V)1 / sqrt(d);
         A[IXG(p, p)] = inv;
         for (int i = p + 1; i < k; i++) A[IXG(i, p)] *= inv;

@@ -75,6 +75,21 @@ __device__ __forceinline__ void renorm(double& P, int& E, bool& bad) {
 template <typename V>
 __device__ __forceinline__ bool is_nan(V x) { return x != x; }
 
+// Positive-definiteness of a pivot of the unit-diagonal correlation
+// submatrix.  In FP64 a pivot at or below 2^-45 is within the rounding of
+// the zero pivot of an exactly singular submatrix (two equal variables, say),
+// so it counts as not positive definite whatever its sign; every FP64 kernel
+// decides the same way.  FP32 pivots only need to be positive here: small
+// ones are flagged for the FP64 re-factor by the pivot threshold.
+constexpr double PD_FLOOR64 = 2.8421709430404007e-14;  // 2^-45
+constexpr double PD_RCP_CEIL64 = 35184372088832.0;     // 2^45 (bound on 1/D)
+__device__ __forceinline__ bool pivot_ok(double d) { return d > PD_FLOOR64; }
+__device__ __forceinline__ bool pivot_ok(float d) { return d > 0.f; }
+// the same test on a reciprocal pivot 1/D (also rejects 1/0 and NaN)
+__device__ __forceinline__ bool rcp_pivot_ok(double rd) {
+  return (rd > 0.0) & (rd < PD_RCP_CEIL64);
+}
+
 // Reciprocal by the hardware approximation (about 1 ulp), one instruction.
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;

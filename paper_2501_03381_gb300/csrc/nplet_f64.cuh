@@ -54,7 +54,7 @@ __device__ void f64s_body(const NpletArgs& a, double* __restrict__ b64, unsigned
     bool bad = false;
     for (int p = 0; p < k; p++) {
       const double d = AE(p, p);
-      bad |= !(d > 0.0);
+      bad |= !pivot_ok(d);
       P1 *= d;
       if ((p & 7) == 7 || p == k - 1) renorm(P1, E1, bad);
       const double rd = 1.0 / d;
@@ -119,7 +119,7 @@ __device__ __forceinline__ void f64g_factor(double* __restrict__ A, const int k,
     __syncwarp(gmask);
     const double rd = AG(p, p);
     if (g == 0) {
-      bad |= !(rd > 0.0) | !(rd < pinf<double>());  // D_p <= 0, zero, or not finite
+      bad |= !rcp_pivot_ok(rd);  // D_p <= 2^-45, zero, or not finite
       P1 *= rd;
       if ((p & 7) == 7 || p == k - 1) renorm(P1, E1, bad);
     }

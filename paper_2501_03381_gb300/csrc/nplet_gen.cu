@@ -21,7 +21,7 @@ __device__ void chol_loo_gen(V* A, int k, V& lr, V& sp, V& pmin, V& trace, bool&
   for (int p = 0; p < k; p++) {
     const V d = A[IXG(p, p)];
     pmin = d < pmin ? d : pmin;
-    bad |= !(d > (V)0);
+    bad |= !pivot_ok(d);
     P1 *= d;
     if ((p & 7) == 7 || p == k - 1) renorm(P1, E1, bad);
     const V inv = (V)1 / sqrt(d);
