@@ -42,13 +42,19 @@ def flops_model(k: int) -> float:
     return 2.0 / 3.0 * k ** 3 + 2.0 * k ** 2
 
 
-# DRAM bytes per nplet of the FP32 nplet kernels, from ncu captures on this
-# workload (dram__bytes_read.sum + dram__bytes_write.sum per launch / nplets):
-# the dense, one-level and two-level prefix kernels at order 16 (145,422,675
-# nplets); traffic grows with the nplets written.  None: not captured for the
-# current kernel (the paired two-level variant has no capture yet).
-TRAFFIC_BYTES_PER_NPLET = {"dense": 13.32, "prefix": 69.54, "prefix2": 51.25,
-                           "prefix2_pair": None}
+# DRAM bytes per nplet of the FP32 nplet kernels with records reduced inside
+# them, from ncu captures on this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch / its nplets), each family at order 16
+# (145,422,675 nplets).  None: no capture of the current kernel.
+TRAFFIC_BYTES_PER_NPLET = {"dense": 0.00326, "group": 0.00375, "prefix": None,
+                           "prefix2": None, "prefix2_pair": None, "prefix3_pair": None}
+
+
+def kernel_family(shape) -> str:
+    lanes, _, prefix = (int(v) for v in shape)
+    if prefix:
+        return ("prefix", "prefix2", "prefix2_pair", "prefix3_pair")[prefix - 1]
+    return "group" if lanes > 1 else "dense"
 
 
 def grad_flops_model(k: int) -> float:
@@ -85,11 +91,24 @@ def prefix2_order_flops(N: int, k: int) -> float:
             math.comb(N, k) * per_nplet)
 
 
+def prefix3_order_flops(N: int, k: int) -> float:
+    # three-level prefix-shared kernel: every (k-3)-prefix built once, one
+    # stored bordered step per (k-2)-prefix and per (k-1)-prefix, one final
+    # step per nplet
+    HP = k - 3
+    per_h = sum(prefix_level_flops(i) for i in range(HP))
+    return (math.comb(N - 3, HP) * per_h + math.comb(N - 2, k - 2) * prefix_level_flops(HP) +
+            math.comb(N - 1, k - 1) * prefix_level_flops(k - 2) +
+            math.comb(N, k) * (prefix_level_flops(k - 1) + 2.0 * (k - 1)))
+
+
 def order_flops(N: int, k: int, prefix: int) -> float:
     # prefix 3 is the two-level kernel with the last variables two at a time:
     # the same algorithmic work as prefix 2
     if prefix in (2, 3):
         return prefix2_order_flops(N, k)
+    if prefix == 4:
+        return prefix3_order_flops(N, k)
     return prefix_order_flops(N, k) if prefix else math.comb(N, k) * flops_model(k)
 
 
@@ -423,8 +442,7 @@ def run_ours(args, rank, world, local_rank):
     f_dense = total_flops()
     traffic = 0.0
     for k in ORDERS:
-        b = TRAFFIC_BYTES_PER_NPLET[("dense", "prefix", "prefix2", "prefix2_pair")[
-            int(shapes.get(k, [1, 8, 0])[2])]]
+        b = TRAFFIC_BYTES_PER_NPLET[kernel_family(shapes.get(k, [1, 8, 0]))]
         traffic = None if (traffic is None or b is None) else traffic + b * math.comb(N_VARS, k)
     kern_s = sum(nplet_ms) / len(nplet_ms) / 1e3
     achieved = f_total / kern_s / 1e12
@@ -444,15 +462,19 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak,
                      "traffic": traffic,
                      "traffic_basis": "per-step DRAM bytes of the FP32 nplet kernels, scaled by "
-                                      "nplets from ncu captures of the order-16 kernels "
-                                      f"(B per nplet: {TRAFFIC_BYTES_PER_NPLET})",
-                     "kernel": "FP32 nplet kernels (k_nplet_reg, k_nplet_pfx, k_nplet_grp), CUDA events",
+                                      "nplets from ncu captures of each kernel family at "
+                                      f"order 16 (B per nplet: {TRAFFIC_BYTES_PER_NPLET})",
+                     "kernel": "FP32 nplet kernels with the records reduced inside (k_nplet_reg, "
+                               "k_nplet_grp, k_nplet_pfx, k_nplet_pfx2), CUDA events",
                      "flops_per_step": f_total, "kernel_ms_per_step": kern_s * 1e3,
                      "flops_model": "dense orders 2/3k^3+2k^2 per nplet; prefix-shared orders "
                                     "(tuned_shapes third entry 1) one bordered build per "
                                     "(k-1)-prefix plus one bordered step per nplet; entry 2: "
                                     "one build per (k-2)-prefix, one stored step per "
-                                    "(k-1)-prefix, one final step per nplet",
+                                    "(k-1)-prefix, one final step per nplet (entry 3 the "
+                                    "same); entry 4: one build per (k-3)-prefix, one "
+                                    "stored step per (k-2)- and per (k-1)-prefix, one "
+                                    "final step per nplet",
                      "dense_equivalent_tflops": f_dense / kern_s / 1e12,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                      "peak_measured_ffma_tflops": fma32,

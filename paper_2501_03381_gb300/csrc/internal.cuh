@@ -108,6 +108,9 @@ struct NpletArgs {
   unsigned long long flag_cap;
   int* status;
   const int* cancel;    // device flag polled per round (may be null)
+  // prefix-shared kernels: a zeroed device counter from which the warps take
+  // their prefixes, 32 at a time (null: a static split over the grid)
+  unsigned long long* work_counter;
 };
 
 // ------------------------------------------------------------------ launchers
@@ -121,7 +124,8 @@ struct Shape {
   int lanes;          // lanes per nplet: 1 (one-thread kernel), 2 or 4 (lane-group kernel)
   int prefix;         // prefix-shared kernels (whole orders, KPFX_MIN <= k <= KPFX_MAX):
                       // 1 shares a (k-1)-prefix, 2 a (k-2)-prefix, 3 a (k-2)-prefix with
-                      // the last variables two at a time; 0 dense
+                      // the last variables two at a time, 4 a (k-3)-prefix (from
+                      // order 5) with the last variables two at a time; 0 dense
 };
 constexpr int KPFX_MIN = 3;   // orders with a prefix-shared kernel
 constexpr int KPFX_MAX = 20;

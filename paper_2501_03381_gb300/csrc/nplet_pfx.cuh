@@ -50,17 +50,32 @@ __global__ void __launch_bounds__(RED_NT, PfxBlocks<K>::value) k_nplet_pfx(const
   const unsigned long long T = binom_s(sb, bs, N - 1, P);  // prefixes (largest index <= N-2)
   const unsigned long long NK = binom_s(sb, bs, N, K);
   const unsigned long long nch = (T + chunk - 1) / chunk;
-  const unsigned long long stride = (unsigned long long)gridDim.x * RED_NT;
   const float tau_piv = a.tau_piv, tau_tr = a.tau_tr;
   const CombineV<float> cmbv(a.cmb);
   constexpr int MB = 8 * sizeof(M);
 
-  for (unsigned long long ch = (unsigned long long)blockIdx.x * RED_NT + threadIdx.x; ch < nch;
-       ch += stride) {
-    if (((ch / stride) & 63) == 0 && a.cancel && *(volatile const int*)a.cancel) {
-      atomicOr(a.status, ST_CANCELLED);
+  // Chunks of prefixes, 32 per warp at a time (consecutive chunks, so the
+  // lanes share their prefixes' largest index): from the slot's work counter
+  // when there is one, else a static split over the grid.
+  const int lane = threadIdx.x & 31;
+  for (unsigned it = 0;; it++) {
+    unsigned long long wb = 0;
+    int stop = 0;
+    if (lane == 0) {
+      wb = a.work_counter ? atomicAdd(a.work_counter, 32ull)
+                          : (((unsigned long long)it * gridDim.x + blockIdx.x) * (RED_NT / 32) +
+                             (threadIdx.x >> 5)) * 32ull;
+      stop = (it & 63) == 63 && a.cancel && *(volatile const int*)a.cancel;
+    }
+    wb = __shfl_sync(0xffffffffu, wb, 0);
+    stop = __shfl_sync(0xffffffffu, stop, 0);
+    if (stop) {
+      if (lane == 0) atomicOr(a.status, ST_CANCELLED);
       break;
     }
+    if (wb >= nch) break;
+    const unsigned long long ch = wb + (unsigned long long)lane;
+    if (ch >= nch) continue;
     const unsigned long long g0 = ch * chunk;
     const int cnt = T - g0 < (unsigned long long)chunk ? (int)(T - g0) : chunk;
     // group (largest prefix index m) of prefix g0 and its rank j inside the group

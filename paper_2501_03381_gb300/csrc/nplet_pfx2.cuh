@@ -14,25 +14,35 @@
 // chains (forward solve, pivot, backward solve, products) interleave; with a
 // thread's few warps per scheduler that is the latency the single step
 // leaves exposed.
+//
+// DEPTH 3: a thread factors a (k-3)-prefix H once and, for every next index
+// a1 > max(H), restores H's state and adds a1 as one stored bordered step,
+// which yields the (k-2)-prefix of the loops above.  The rows of H's factor
+// stay in place (a bordered step writes only its own row); H's inverse
+// diagonal, which every step updates, is kept in shared memory.  A
+// (k-2)-prefix then costs one step instead of a whole factorisation.
 #pragma once
 #include "nplet_common.cuh"
 
 namespace thoi {
 
-// Minimum resident blocks per SM: three (168 registers) up to order 14,
-// measured 2-10% faster there despite a few spilled registers at 13 and 14;
-// above, the compiler's own allocation (up to 255 registers, two blocks).
-template <int K>
+// Minimum resident blocks per SM: three (168 registers) up to order 14 at
+// depth 2, measured 2-10% faster there despite a few spilled registers at 13
+// and 14; above, and at depth 3 (one more saved state), the compiler's own
+// allocation (up to 255 registers, two blocks).
+template <int K, int DEPTH>
 struct Pfx2Blocks {
-  static constexpr int value = K <= 14 ? 3 : 1;
+  static constexpr int value = (K <= 14 && DEPTH == 2) ? 3 : 1;
 };
 
-template <int K, typename M, bool PAIR>
-__global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(const NpletArgs a,
-                                                                            const int chunk) {
+template <int K, typename M, bool PAIR, int DEPTH>
+__global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K, DEPTH>::value)
+    k_nplet_pfx2(const NpletArgs a, const int chunk) {
+  static_assert(DEPTH == 2 || (DEPTH == 3 && K >= 5), "depth 2, or depth 3 from order 5");
   constexpr int P = K - 1;   // variables before the last one
   constexpr int GP = K - 2;  // grand-prefix size
-  constexpr int GQ = K - 3;  // grand-prefix indices below its largest index g
+  constexpr int B0 = K - DEPTH;  // variables of the thread's own prefix (the grand prefix at depth 2)
+  constexpr int BQ = B0 - 1;     // its indices below its largest index g
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N, ldr = row_stride(N);
   const SmemLayout L = smem_layout(N, K, ldr, sizeof(float), sizeof(unsigned), 0);
@@ -46,16 +56,18 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
   const float* sthr = reinterpret_cast<const float*>(smem + L.thr);
   FusedAcc acc;
   acc.init();
-  const unsigned long long T = binom_s(sb, bs, N - 2, GP);  // grand prefixes (largest <= N-3)
+  // the threads' prefixes (largest index <= N-1-DEPTH)
+  const unsigned long long T = binom_s(sb, bs, N - DEPTH, B0);
   const unsigned long long NK = binom_s(sb, bs, N, K);
   const unsigned long long nch = (T + chunk - 1) / chunk;
-  const unsigned long long stride = (unsigned long long)gridDim.x * RED_NT;
   const float tau_piv = a.tau_piv, tau_tr = a.tau_tr;
   const CombineV<float> cmbv(a.cmb);
   constexpr int MB = 8 * sizeof(M);
 
   float Lh[P][P];
   float dd[P], qd[P], qb[GP];
+  // depth 3: the inverse diagonal of H, entry r of this thread at qh[r * RED_NT]
+  float* const qh = reinterpret_cast<float*>(smem + (L.total + 15) / 16 * 16) + threadIdx.x;
   int c[P];
   float P1 = 1.f, pmin = pinf<float>(), lsp = 0.f;
   int E1 = 0;
@@ -99,42 +111,84 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
     qd[i] = dn;
   };
 
-  for (unsigned long long ch = (unsigned long long)blockIdx.x * RED_NT + threadIdx.x; ch < nch;
-       ch += stride) {
-    if (((ch / stride) & 63) == 0 && a.cancel && *(volatile const int*)a.cancel) {
-      atomicOr(a.status, ST_CANCELLED);
+  // Chunks of prefixes, 32 per warp at a time (consecutive chunks, so the
+  // lanes share their prefixes' largest index): from the slot's work counter
+  // when there is one (the work per prefix varies with its largest index,
+  // and the heaviest groups come first), else a static split over the grid.
+  const int lane = threadIdx.x & 31;
+  for (unsigned it = 0;; it++) {
+    unsigned long long wb = 0;
+    int stop = 0;
+    if (lane == 0) {
+      wb = a.work_counter ? atomicAdd(a.work_counter, 32ull)
+                          : (((unsigned long long)it * gridDim.x + blockIdx.x) * (RED_NT / 32) +
+                             (threadIdx.x >> 5)) * 32ull;
+      stop = (it & 63) == 63 && a.cancel && *(volatile const int*)a.cancel;
+    }
+    wb = __shfl_sync(0xffffffffu, wb, 0);
+    stop = __shfl_sync(0xffffffffu, stop, 0);
+    if (stop) {
+      if (lane == 0) atomicOr(a.status, ST_CANCELLED);
       break;
     }
+    if (wb >= nch) break;
+    const unsigned long long ch = wb + (unsigned long long)lane;
+    if (ch >= nch) continue;
     const unsigned long long g0 = ch * chunk;
     const int cnt = T - g0 < (unsigned long long)chunk ? (int)(T - g0) : chunk;
-    int g = GQ;
-    unsigned long long off = 0, gsz = binom_s(sb, bs, g, GQ);
+    int g = BQ;
+    unsigned long long off = 0, gsz = binom_s(sb, bs, g, BQ);
     while (g0 >= off + gsz) {
       off += gsz;
       g++;
-      gsz = binom_s(sb, bs, g, GQ);
+      gsz = binom_s(sb, bs, g, BQ);
     }
     unsigned long long j = g0 - off;
-    M pm = unrank_s<M>(j, GQ, g, sb, bs);
+    M pm = unrank_s<M>(j, BQ, g, sb, bs);
     for (int jn = 0; jn < cnt; jn++) {
       {
         M t = pm;
 #pragma unroll
-        for (int q = 0; q < GQ; q++) {
+        for (int q = 0; q < BQ; q++) {
           const int hb = hibit(t);
           t ^= (M)1 << hb;
           c[q] = g - 1 - hb;
         }
-        c[GQ] = g;
+        c[BQ] = g;
       }
-      // ---- grand prefix
+      // ---- the thread's prefix
       P1 = 1.f;
       E1 = 0;
       pmin = pinf<float>();
       lsp = 0.f;
       badp = false;
 #pragma unroll
-      for (int i = 0; i < GP; i++) level(i, c[i]);
+      for (int i = 0; i < B0; i++) level(i, c[i]);
+      [[maybe_unused]] const float P1h = P1, pminh = pmin, lsph = lsp;
+      [[maybe_unused]] const int E1h = E1;
+      [[maybe_unused]] const bool badh = badp;
+      if constexpr (DEPTH == 3) {
+#pragma unroll
+        for (int r = 0; r < B0; r++) qh[r * RED_NT] = qd[r];
+      }
+      // ---- depth 3: every next index a1 as one stored step onto H
+      const int a1_lo = DEPTH == 3 ? g + 1 : g;
+      const int a1_hi = DEPTH == 3 ? N - 3 : g;
+      for (int a1 = a1_lo; a1 <= a1_hi; a1++) {
+      if constexpr (DEPTH == 3) {
+        if (a1 > a1_lo) {
+#pragma unroll
+          for (int r = 0; r < B0; r++) qd[r] = qh[r * RED_NT];
+          P1 = P1h;
+          E1 = E1h;
+          pmin = pminh;
+          lsp = lsph;
+          badp = badh;
+        }
+        c[B0] = a1;
+        level(B0, a1);
+      }
+      // ---- grand prefix (largest index a1)
 #pragma unroll
       for (int r = 0; r < GP; r++) qb[r] = qd[r];
       const float P1g = P1, pming = pmin, lspg = lsp;
@@ -144,7 +198,7 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
 #pragma unroll
       for (int i = 0; i < GP; i++) rbase -= binom_s(sb, bs, N - 1 - c[i], K - i);
       // ---- middle variables
-      for (int am = g + 1; am < N - 1; am++) {
+      for (int am = a1 + 1; am < N - 1; am++) {
 #pragma unroll
         for (int r = 0; r < GP; r++) qd[r] = qb[r];
         P1 = P1g;
@@ -240,6 +294,7 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
           }
         }
       }
+      }  // a1
       if (jn + 1 < cnt) {
         if (j + 1 < gsz) {
           const M fullg = (g >= MB) ? ~(M)0 : (((M)1 << g) - 1);
@@ -247,9 +302,9 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
           j++;
         } else {
           g++;
-          gsz = binom_s(sb, bs, g, GQ);
+          gsz = binom_s(sb, bs, g, BQ);
           j = 0;
-          pm = unrank_s<M>(0, GQ, g, sb, bs);
+          pm = unrank_s<M>(0, BQ, g, sb, bs);
         }
       }
     }
@@ -257,41 +312,57 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K>::value) k_nplet_pfx2(con
   if (fused) fused_block_end(a, acc);
 }
 
-template <int K, typename M, bool PAIR>
+// Shared memory of a launch: the tables, then (depth 3) the inverse diagonal
+// of every thread's H.
+template <int K, int DEPTH>
+static size_t pfx2_smem(int N) {
+  const SmemLayout L = smem_layout(N, K, row_stride(N), sizeof(float), sizeof(unsigned), 0);
+  return (L.total + 15) / 16 * 16 + (DEPTH == 3 ? (size_t)(K - 3) * RED_NT * sizeof(float) : 0);
+}
+
+template <int K, typename M, bool PAIR, int DEPTH>
 static cudaError_t launch_pfx2_t(const NpletArgs& a, const Shape& sh, int num_sms,
                                  cudaStream_t s, int* grid_out, int max_blocks) {
-  const SmemLayout L = smem_layout(a.N, K, row_stride(a.N), sizeof(float), sizeof(unsigned), 0);
-  void (*fn)(const NpletArgs, const int) = k_nplet_pfx2<K, M, PAIR>;
+  const size_t smem = pfx2_smem<K, DEPTH>(a.N);
+  void (*fn)(const NpletArgs, const int) = k_nplet_pfx2<K, M, PAIR, DEPTH>;
   int occ = 0;
-  cudaError_t e = occupancy_cached((const void*)fn, RED_NT, L.total, &occ);
+  cudaError_t e = occupancy_cached((const void*)fn, RED_NT, smem, &occ);
   if (e != cudaSuccess) return e;
   if (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ) occ = sh.blocks_per_sm;
   int chunk = sh.chunk > 0 ? sh.chunk : 1;
   if (chunk > 8) chunk = 8;
-  // grand prefixes of the order: C(N-2, K-2)
+  // the threads' prefixes: C(N - DEPTH, K - DEPTH)
   unsigned __int128 t = 1;
-  for (int i = 1; i <= K - 2; i++) t = t * (unsigned)(a.N - K + i) / (unsigned)i;
+  for (int i = 1; i <= K - DEPTH; i++) t = t * (unsigned)(a.N - K + i) / (unsigned)i;
   const unsigned long long T = (unsigned long long)t;
   long long grid = (long long)num_sms * occ;
   const long long need =
       (long long)((T + (unsigned long long)RED_NT * chunk - 1) / ((unsigned long long)RED_NT * chunk));
   if (need < grid) grid = need > 0 ? need : 1;
   if (grid > max_blocks) grid = max_blocks;
-  fn<<<(unsigned)grid, RED_NT, L.total, s>>>(a, chunk);
+  fn<<<(unsigned)grid, RED_NT, smem, s>>>(a, chunk);
   if (grid_out) *grid_out = (int)grid;
   return cudaGetLastError();
 }
 
-// sh.prefix == 3: the last variables two at a time
+// sh.prefix 2: two-level; 3: two-level with the last variables two at a
+// time; 4: three-level (from order 5) with the last variables two at a time
 template <int K>
 cudaError_t launch_pfx2_k(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                           int* grid_out, int max_blocks) {
-  if (sh.prefix == 3) {
-    if (a.N <= 32) return launch_pfx2_t<K, unsigned, true>(a, sh, num_sms, s, grid_out, max_blocks);
-    return launch_pfx2_t<K, unsigned long long, true>(a, sh, num_sms, s, grid_out, max_blocks);
+  const bool wide = a.N > 32;
+  if constexpr (K >= 5) {
+    if (sh.prefix == 4) {
+      if (!wide) return launch_pfx2_t<K, unsigned, true, 3>(a, sh, num_sms, s, grid_out, max_blocks);
+      return launch_pfx2_t<K, unsigned long long, true, 3>(a, sh, num_sms, s, grid_out, max_blocks);
+    }
   }
-  if (a.N <= 32) return launch_pfx2_t<K, unsigned, false>(a, sh, num_sms, s, grid_out, max_blocks);
-  return launch_pfx2_t<K, unsigned long long, false>(a, sh, num_sms, s, grid_out, max_blocks);
+  if (sh.prefix >= 3) {
+    if (!wide) return launch_pfx2_t<K, unsigned, true, 2>(a, sh, num_sms, s, grid_out, max_blocks);
+    return launch_pfx2_t<K, unsigned long long, true, 2>(a, sh, num_sms, s, grid_out, max_blocks);
+  }
+  if (!wide) return launch_pfx2_t<K, unsigned, false, 2>(a, sh, num_sms, s, grid_out, max_blocks);
+  return launch_pfx2_t<K, unsigned long long, false, 2>(a, sh, num_sms, s, grid_out, max_blocks);
 }
 
 }  // namespace thoi

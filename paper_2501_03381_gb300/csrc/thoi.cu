@@ -73,6 +73,7 @@ struct thoi_ctx {
   cudaStream_t s2 = nullptr;
   std::vector<cudaEvent_t> sev;  // per-slot "list filled" and "re-factor done" events
   unsigned long long* flag_counts = nullptr;  // [MAX_SLOTS]
+  unsigned long long* work_ctr = nullptr;     // [MAX_SLOTS] prefix-kernel work counters
   PartRec* part32 = nullptr;
   TopEnt* top32 = nullptr;
   size_t part32_cap = 0;      // blocks
@@ -411,6 +412,7 @@ extern "C" void thoi_destroy(thoi_ctx* c) {
   for (auto e : c->sev) cudaEventDestroy(e);
   if (c->s2) cudaStreamDestroy(c->s2);
   free_ptr(c->flag_counts);
+  free_ptr(c->work_ctr);
   free_ptr(c->part32);
   free_ptr(c->top32);
   free_ptr(c->part64);
@@ -455,6 +457,7 @@ static thoi_status ctx_common(thoi_ctx* c, int N, const thoi_options* opt) {
   CK(cudaMalloc(&c->binom, (size_t)NB * NB * 8));
   CK(cudaMalloc(&c->status, sizeof(int)));
   CK(cudaMalloc(&c->flag_counts, MAX_SLOTS * sizeof(unsigned long long)));
+  CK(cudaMalloc(&c->work_ctr, MAX_SLOTS * sizeof(unsigned long long)));
   CK(cudaMalloc(&c->seed_thr, 2 * sizeof(float)));
   CK(cudaHostAlloc(&c->h_cancel, sizeof(int), cudaHostAllocMapped));
   *c->h_cancel = 0;
@@ -668,9 +671,12 @@ static thoi_status ensure_overlap(thoi_ctx* c, int n_slots) {
   return THOI_OK;
 }
 
-static NpletArgs base_args(thoi_ctx* c, const SlotRange& r) {
+// si >= 0: the request's order slot (the prefix-shared kernels take their
+// work from that slot's counter, zeroed with the request)
+static NpletArgs base_args(thoi_ctx* c, const SlotRange& r, int si = -1) {
   NpletArgs a;
   memset(&a, 0, sizeof a);
+  if (si >= 0) a.work_counter = c->work_ctr + si;
   a.N = c->N;
   a.k = r.k;
   a.R32 = c->R32;
@@ -881,6 +887,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
   }
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(c->flag_counts, 0, MAX_SLOTS * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(c->work_ctr, 0, MAX_SLOTS * sizeof(unsigned long long), s));
   if (maxn_fused > 0) CK(cudaMemsetAsync(c->fz, 0, FZ_HEAD, s));  // counters and keys
   // the FP64 re-factor of each order on a second stream (FP32 path, several
   // orders): its FP64 work overlaps the next order's FP32 kernel
@@ -910,7 +917,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
     if (fused_slot(r)) {
       // fused records: sample bounds, the nplet kernel reducing in place, the
       // candidate list's reduction
-      NpletArgs a = base_args(c, r);
+      NpletArgs a = base_args(c, r, (int)si);
       a.flag_ids = fids;
       a.flag_count = c->flag_counts + si;
       a.mode = 3;
@@ -957,7 +964,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         SlotRange sub = r;
         sub.r0 = a0;
         sub.r1 = r.r1 - a0 > PIECE ? a0 + PIECE : r.r1;
-        NpletArgs a = base_args(c, sub);
+        NpletArgs a = base_args(c, sub, (int)si);
         a.flag_ids = fids;
         a.flag_count = c->flag_counts + si;
         a.mode = 2;
@@ -997,7 +1004,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         SlotRange sub = r;
         sub.r0 = a0;
         sub.r1 = r.r1 - a0 > PIECE ? a0 + PIECE : r.r1;
-        NpletArgs a = base_args(c, sub);
+        NpletArgs a = base_args(c, sub, (int)si);
         a.mode = 2;
         int grid = 0;
         st = prof_begin(c, s, 0);
@@ -1024,7 +1031,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       SlotRange sub = r;
       sub.r0 = a0;
       sub.r1 = r.r1 - a0 > LAUNCH_SPLIT ? a0 + LAUNCH_SPLIT : r.r1;
-      NpletArgs a = base_args(c, sub);
+      NpletArgs a = base_args(c, sub, (int)si);
       a.flag_ids = fids;
       a.flag_count = c->flag_counts + si;
       a.mode = red ? 1 : 0;
@@ -1065,7 +1072,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         CK(cudaStreamWaitEvent(c->s2, c->sev[2 * si], 0));
         sr = c->s2;
       }
-      NpletArgs a = base_args(c, r);
+      NpletArgs a = base_args(c, r, (int)si);
       a.flag_ids = fids;
       a.flag_count = c->flag_counts + si;
       a.mode = red ? 1 : 0;
@@ -2450,7 +2457,7 @@ static void tune_load(const char* path, const char* gpu, int sms) {
     sh.lanes = lanes;
     sh.chunk = chunk;
     sh.blocks_per_sm = bps;
-    sh.prefix = (prefix >= 0 && prefix <= 3) ? prefix : 0;
+    sh.prefix = (prefix >= 0 && prefix <= 4) ? prefix : 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(gpu, sms, k, wide)] = sh;
     g_tune_gen++;
@@ -2552,13 +2559,15 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
     if (pfx_candidate) {
       // (k-1)-prefix kernel with 1, 2, 4 prefixes per thread per round, then
       // the (k-2)-prefix kernel with 1, 2, then that kernel with the last
-      // variables two at a time, with 1, 2
-      for (int v = 0; v < 7; v++) {
+      // variables two at a time, with 1, 2, then (from order 5) the
+      // three-level kernel with the last variables two at a time, with 1, 2
+      for (int v = 0; v < 9; v++) {
+        if (v >= 7 && k < 5) break;
         Shape sh;
         sh.lanes = 1;
         sh.chunk = v < 3 ? 1 << v : 1 << ((v - 3) & 1);
         sh.blocks_per_sm = 0;
-        sh.prefix = v < 3 ? 1 : (v < 5 ? 2 : 3);
+        sh.prefix = v < 3 ? 1 : (v < 5 ? 2 : (v < 7 ? 3 : 4));
         const double ms = time_shape(c, k, total, sh, s);
         if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
           best_ms = ms;

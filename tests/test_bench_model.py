@@ -3,7 +3,9 @@ the kernel time for the roofline.  The prefix-shared counts are checked
 against a walk of the kernels' loop structure on small N (every (k-1)-prefix
 with a last variable after it built once; every (k-2)-prefix with a middle
 and a last variable after it built once, one stored step per middle index,
-one final step per nplet)."""
+one final step per nplet; every (k-3)-prefix with three more variables after
+it built once, one stored step per next index and per middle index, one final
+step per nplet)."""
 import itertools
 import math
 
@@ -39,6 +41,23 @@ def _walk_two_level(N, k):
     return f
 
 
+def _walk_three_level(N, k):
+    f = 0.0
+    HP = k - 3
+    for h in itertools.combinations(range(N), HP):
+        m = h[-1] if HP else -1
+        firsts = [a for a in range(m + 1, N - 2)]
+        if not firsts:
+            continue
+        f += sum(bench.prefix_level_flops(i) for i in range(HP))
+        for a1 in firsts:
+            f += bench.prefix_level_flops(HP)
+            for a2 in range(a1 + 1, N - 1):
+                f += bench.prefix_level_flops(k - 2)
+                f += (N - 1 - a2) * (bench.prefix_level_flops(k - 1) + 2.0 * (k - 1))
+    return f
+
+
 @pytest.mark.parametrize("N", [7, 9])
 def test_prefix_counts_match_loop_walk(N):
     for k in range(3, N + 1):
@@ -46,6 +65,9 @@ def test_prefix_counts_match_loop_walk(N):
         assert bench.prefix2_order_flops(N, k) == pytest.approx(_walk_two_level(N, k), rel=1e-12)
         # the paired variant does the same algorithmic work as the two-level kernel
         assert bench.order_flops(N, k, 3) == bench.order_flops(N, k, 2)
+        if k >= 5:
+            assert bench.order_flops(N, k, 4) == pytest.approx(_walk_three_level(N, k),
+                                                               rel=1e-12)
         assert bench.order_flops(N, k, 0) == math.comb(N, k) * bench.flops_model(k)
 
 

@@ -503,12 +503,15 @@ def test_virtual_ranks_partition_and_merge():
 
 
 # ------------------------------------------------------------------ prefix-shared kernel
-@pytest.mark.parametrize("variant,chunk", [(1, 1), (1, 3), (2, 1), (2, 3), (3, 1), (3, 2)])
+@pytest.mark.parametrize("variant,chunk", [(1, 1), (1, 3), (2, 1), (2, 3), (3, 1), (3, 2),
+                                           (4, 1), (4, 3)])
 def test_prefix_kernel_every_order_matches_oracle(variant, chunk, tmp_path):
     # the prefix-shared kernels (bordered steps over a shared (k-1)-prefix,
     # variant 1, or (k-2)-prefix, variant 2, the latter with the last variables
-    # two at a time, variant 3) on every order of the fMRI-shaped workload
-    # (odd and even numbers of last variables), every nplet against the oracle
+    # two at a time, variant 3, and over a shared (k-3)-prefix with one stored
+    # step per next index, variant 4) on every order of the fMRI-shaped
+    # workload (odd and even numbers of last variables), every nplet against
+    # the oracle
     X, orders = workloads.fmri_like()
     S = oracle.copula_cov(X)
     with _ctx(X, out_f64=True) as c:
@@ -566,3 +569,27 @@ def test_module_level_measures_and_measure_sum():
 def _order_slices(orders, N=10):
     offs = np.cumsum([0] + [math.comb(N, k) for k in orders])
     return [slice(int(offs[i]), int(offs[i + 1])) for i in range(len(orders))]
+
+
+def test_three_level_prefix_kernel_wide_masks(tmp_path):
+    # the three-level kernel on 64-bit masks (N = 34), every nplet of order 5
+    # against the oracle, and the records of orders 5 and 6 against those of
+    # the dense kernel
+    S = workloads.random_corr(np.random.default_rng(21), 34)
+    with _ctx(Sigma=S, out_f64=True, top_m=16) as c:
+        _force_shape(c.h, 5, 1, 1, 2, str(tmp_path / "t5.json"), prefix=4)
+        ref, _ = _refs(S, [5])
+        got, _ = c.measures([5])
+        np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=TOL32)
+        _force_shape(c.h, 6, 1, 1, 1, str(tmp_path / "t6.json"), prefix=4)
+        (r3, h3, l3), _ = c.measures([5, 6], reduction="per_order")
+        for k in (5, 6):
+            _force_shape(c.h, k, 1, 1, 8, str(tmp_path / f"d{k}.json"), prefix=0)
+        (r0, h0, l0), _ = c.measures([5, 6], reduction="per_order")
+    for q in range(2):
+        np.testing.assert_allclose(r3[q]["min"], r0[q]["min"], rtol=0, atol=TOL32)
+        np.testing.assert_allclose(r3[q]["max"], r0[q]["max"], rtol=0, atol=TOL32)
+        np.testing.assert_allclose(r3[q]["mean"], r0[q]["mean"], rtol=0, atol=1e-6)
+        assert int(r3[q]["count"]) == int(r0[q]["count"])
+        np.testing.assert_allclose(h3[q]["value"][:16], h0[q]["value"][:16], rtol=0, atol=TOL32)
+        np.testing.assert_allclose(l3[q]["value"][:16], l0[q]["value"][:16], rtol=0, atol=TOL32)
