@@ -46,8 +46,8 @@ def flops_model(k: int) -> float:
 # them, from ncu captures on this workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch / its nplets), each family at order 16
 # (145,422,675 nplets).  None: no capture of the current kernel.
-TRAFFIC_BYTES_PER_NPLET = {"dense": 0.00326, "group": 0.00375, "prefix": None,
-                           "prefix2": None, "prefix2_pair": None, "prefix3_pair": None}
+TRAFFIC_BYTES_PER_NPLET = {"dense": 0.00326, "group": 0.00375, "prefix": 0.00055,
+                           "prefix2": 0.00061, "prefix2_pair": 0.00167, "prefix3_pair": 0.00076}
 
 
 def kernel_family(shape) -> str:
