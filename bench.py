@@ -47,13 +47,14 @@ def flops_model(k: int) -> float:
 # dram__bytes_write.sum of one launch / its nplets), each family at order 16
 # (145,422,675 nplets).  None: no capture of the current kernel.
 TRAFFIC_BYTES_PER_NPLET = {"dense": 0.00326, "group": 0.00375, "prefix": 0.00055,
-                           "prefix2": 0.00061, "prefix2_pair": 0.00167, "prefix3_pair": 0.00076}
+                           "prefix2": 0.00061, "prefix2_pair": 0.00167, "prefix3_pair": 0.00076,
+                           "prefix4_pair": None}
 
 
 def kernel_family(shape) -> str:
     lanes, _, prefix = (int(v) for v in shape)
     if prefix:
-        return ("prefix", "prefix2", "prefix2_pair", "prefix3_pair")[prefix - 1]
+        return ("prefix", "prefix2", "prefix2_pair", "prefix3_pair", "prefix4_pair")[prefix - 1]
     return "group" if lanes > 1 else "dense"
 
 
@@ -91,6 +92,18 @@ def prefix2_order_flops(N: int, k: int) -> float:
             math.comb(N, k) * per_nplet)
 
 
+def prefix4_order_flops(N: int, k: int) -> float:
+    # four-level prefix-shared kernel: every (k-4)-prefix built once, one
+    # stored bordered step per (k-3)-, (k-2)- and (k-1)-prefix, one final
+    # step per nplet
+    IP = k - 4
+    per_i = sum(prefix_level_flops(i) for i in range(IP))
+    return (math.comb(N - 4, IP) * per_i + math.comb(N - 3, k - 3) * prefix_level_flops(IP) +
+            math.comb(N - 2, k - 2) * prefix_level_flops(k - 3) +
+            math.comb(N - 1, k - 1) * prefix_level_flops(k - 2) +
+            math.comb(N, k) * (prefix_level_flops(k - 1) + 2.0 * (k - 1)))
+
+
 def prefix3_order_flops(N: int, k: int) -> float:
     # three-level prefix-shared kernel: every (k-3)-prefix built once, one
     # stored bordered step per (k-2)-prefix and per (k-1)-prefix, one final
@@ -109,6 +122,8 @@ def order_flops(N: int, k: int, prefix: int) -> float:
         return prefix2_order_flops(N, k)
     if prefix == 4:
         return prefix3_order_flops(N, k)
+    if prefix == 5:
+        return prefix4_order_flops(N, k)
     return prefix_order_flops(N, k) if prefix else math.comb(N, k) * flops_model(k)
 
 
@@ -474,7 +489,9 @@ def run_ours(args, rank, world, local_rank):
                                     "(k-1)-prefix, one final step per nplet (entry 3 the "
                                     "same); entry 4: one build per (k-3)-prefix, one "
                                     "stored step per (k-2)- and per (k-1)-prefix, one "
-                                    "final step per nplet",
+                                    "final step per nplet; entry 5: one build per "
+                                    "(k-4)-prefix, one stored step per (k-3)-, (k-2)- and "
+                                    "(k-1)-prefix, one final step per nplet",
                      "dense_equivalent_tflops": f_dense / kern_s / 1e12,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                      "peak_measured_ffma_tflops": fma32,

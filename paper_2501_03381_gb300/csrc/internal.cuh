@@ -125,7 +125,8 @@ struct Shape {
   int prefix;         // prefix-shared kernels (whole orders, KPFX_MIN <= k <= KPFX_MAX):
                       // 1 shares a (k-1)-prefix, 2 a (k-2)-prefix, 3 a (k-2)-prefix with
                       // the last variables two at a time, 4 a (k-3)-prefix (from
-                      // order 5) with the last variables two at a time; 0 dense
+                      // order 5) and 5 a (k-4)-prefix (from order 6), both with the
+                      // last variables two at a time; 0 dense
 };
 constexpr int KPFX_MIN = 3;   // orders with a prefix-shared kernel
 constexpr int KPFX_MAX = 20;

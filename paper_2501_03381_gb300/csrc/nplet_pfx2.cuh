@@ -21,6 +21,8 @@
 // stay in place (a bordered step writes only its own row); H's inverse
 // diagonal, which every step updates, is kept in shared memory.  A
 // (k-2)-prefix then costs one step instead of a whole factorisation.
+// DEPTH 4 adds one more such level: the thread factors a (k-4)-prefix I, and
+// every next index a0 makes H = I + a0 by one stored step.
 #pragma once
 #include "nplet_common.cuh"
 
@@ -38,7 +40,8 @@ struct Pfx2Blocks {
 template <int K, typename M, bool PAIR, int DEPTH>
 __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K, DEPTH>::value)
     k_nplet_pfx2(const NpletArgs a, const int chunk) {
-  static_assert(DEPTH == 2 || (DEPTH == 3 && K >= 5), "depth 2, or depth 3 from order 5");
+  static_assert(DEPTH == 2 || (DEPTH == 3 && K >= 5) || (DEPTH == 4 && K >= 6),
+                "depth 2, depth 3 from order 5, depth 4 from order 6");
   constexpr int P = K - 1;   // variables before the last one
   constexpr int GP = K - 2;  // grand-prefix size
   constexpr int B0 = K - DEPTH;  // variables of the thread's own prefix (the grand prefix at depth 2)
@@ -66,8 +69,11 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K, DEPTH>::value)
 
   float Lh[P][P];
   float dd[P], qd[P], qb[GP];
-  // depth 3: the inverse diagonal of H, entry r of this thread at qh[r * RED_NT]
+  // depth 3 and 4: the inverse diagonal of H, entry r of this thread at
+  // qh[r * RED_NT]; depth 4: that of I after it (qi)
   float* const qh = reinterpret_cast<float*>(smem + (L.total + 15) / 16 * 16) + threadIdx.x;
+  float* const qi = qh + (size_t)(K - 3) * RED_NT;
+  constexpr int HB = K - 3;  // row of the step onto H (the index a1)
   int c[P];
   float P1 = 1.f, pmin = pinf<float>(), lsp = 0.f;
   int E1 = 0;
@@ -164,29 +170,55 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K, DEPTH>::value)
       badp = false;
 #pragma unroll
       for (int i = 0; i < B0; i++) level(i, c[i]);
+      // ---- depth 4: every next index a0 as one stored step onto the thread's
+      // prefix I, giving H (at depth 3, H is the thread's prefix)
+      [[maybe_unused]] const float P1i = P1, pmini = pmin, lspi = lsp;
+      [[maybe_unused]] const int E1i = E1;
+      [[maybe_unused]] const bool badi = badp;
+      if constexpr (DEPTH == 4) {
+#pragma unroll
+        for (int r = 0; r < B0; r++) qi[r * RED_NT] = qd[r];
+      }
+      const int a0_lo = DEPTH == 4 ? g + 1 : g;
+      const int a0_hi = DEPTH == 4 ? N - 4 : g;
+      for (int a0 = a0_lo; a0 <= a0_hi; a0++) {
+      if constexpr (DEPTH == 4) {
+        if (a0 > a0_lo) {
+#pragma unroll
+          for (int r = 0; r < B0; r++) qd[r] = qi[r * RED_NT];
+          P1 = P1i;
+          E1 = E1i;
+          pmin = pmini;
+          lsp = lspi;
+          badp = badi;
+        }
+        c[B0] = a0;
+        level(B0, a0);
+      }
+      // ---- depth 3 and 4: every next index a1 as one stored step onto H
       [[maybe_unused]] const float P1h = P1, pminh = pmin, lsph = lsp;
       [[maybe_unused]] const int E1h = E1;
       [[maybe_unused]] const bool badh = badp;
-      if constexpr (DEPTH == 3) {
+      if constexpr (DEPTH >= 3) {
 #pragma unroll
-        for (int r = 0; r < B0; r++) qh[r * RED_NT] = qd[r];
+        for (int r = 0; r < HB; r++) qh[r * RED_NT] = qd[r];
       }
-      // ---- depth 3: every next index a1 as one stored step onto H
-      const int a1_lo = DEPTH == 3 ? g + 1 : g;
-      const int a1_hi = DEPTH == 3 ? N - 3 : g;
+      const int gh = DEPTH == 4 ? a0 : g;  // largest index of H (of the grand prefix at depth 2)
+      const int a1_lo = DEPTH >= 3 ? gh + 1 : gh;
+      const int a1_hi = DEPTH >= 3 ? N - 3 : gh;
       for (int a1 = a1_lo; a1 <= a1_hi; a1++) {
-      if constexpr (DEPTH == 3) {
+      if constexpr (DEPTH >= 3) {
         if (a1 > a1_lo) {
 #pragma unroll
-          for (int r = 0; r < B0; r++) qd[r] = qh[r * RED_NT];
+          for (int r = 0; r < HB; r++) qd[r] = qh[r * RED_NT];
           P1 = P1h;
           E1 = E1h;
           pmin = pminh;
           lsp = lsph;
           badp = badh;
         }
-        c[B0] = a1;
-        level(B0, a1);
+        c[HB] = a1;
+        level(HB, a1);
       }
       // ---- grand prefix (largest index a1)
 #pragma unroll
@@ -295,6 +327,7 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K, DEPTH>::value)
         }
       }
       }  // a1
+      }  // a0
       if (jn + 1 < cnt) {
         if (j + 1 < gsz) {
           const M fullg = (g >= MB) ? ~(M)0 : (((M)1 << g) - 1);
@@ -317,7 +350,8 @@ __global__ void __launch_bounds__(RED_NT, Pfx2Blocks<K, DEPTH>::value)
 template <int K, int DEPTH>
 static size_t pfx2_smem(int N) {
   const SmemLayout L = smem_layout(N, K, row_stride(N), sizeof(float), sizeof(unsigned), 0);
-  return (L.total + 15) / 16 * 16 + (DEPTH == 3 ? (size_t)(K - 3) * RED_NT * sizeof(float) : 0);
+  const size_t q = DEPTH == 3 ? (size_t)(K - 3) : (DEPTH == 4 ? (size_t)(2 * K - 7) : 0);
+  return (L.total + 15) / 16 * 16 + q * RED_NT * sizeof(float);
 }
 
 template <int K, typename M, bool PAIR, int DEPTH>
@@ -346,13 +380,20 @@ static cudaError_t launch_pfx2_t(const NpletArgs& a, const Shape& sh, int num_sm
 }
 
 // sh.prefix 2: two-level; 3: two-level with the last variables two at a
-// time; 4: three-level (from order 5) with the last variables two at a time
+// time; 4: three-level (from order 5) and 5: four-level (from order 6), with
+// the last variables two at a time
 template <int K>
 cudaError_t launch_pfx2_k(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                           int* grid_out, int max_blocks) {
   const bool wide = a.N > 32;
+  if constexpr (K >= 6) {
+    if (sh.prefix == 5) {
+      if (!wide) return launch_pfx2_t<K, unsigned, true, 4>(a, sh, num_sms, s, grid_out, max_blocks);
+      return launch_pfx2_t<K, unsigned long long, true, 4>(a, sh, num_sms, s, grid_out, max_blocks);
+    }
+  }
   if constexpr (K >= 5) {
-    if (sh.prefix == 4) {
+    if (sh.prefix >= 4) {
       if (!wide) return launch_pfx2_t<K, unsigned, true, 3>(a, sh, num_sms, s, grid_out, max_blocks);
       return launch_pfx2_t<K, unsigned long long, true, 3>(a, sh, num_sms, s, grid_out, max_blocks);
     }

@@ -2457,7 +2457,7 @@ static void tune_load(const char* path, const char* gpu, int sms) {
     sh.lanes = lanes;
     sh.chunk = chunk;
     sh.blocks_per_sm = bps;
-    sh.prefix = (prefix >= 0 && prefix <= 4) ? prefix : 0;
+    sh.prefix = (prefix >= 0 && prefix <= 5) ? prefix : 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(gpu, sms, k, wide)] = sh;
     g_tune_gen++;
@@ -2560,14 +2560,15 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
       // (k-1)-prefix kernel with 1, 2, 4 prefixes per thread per round, then
       // the (k-2)-prefix kernel with 1, 2, then that kernel with the last
       // variables two at a time, with 1, 2, then (from order 5) the
-      // three-level kernel with the last variables two at a time, with 1, 2
-      for (int v = 0; v < 9; v++) {
-        if (v >= 7 && k < 5) break;
+      // three-level and (from order 6) the four-level kernel with the last
+      // variables two at a time, with 1, 2
+      for (int v = 0; v < 11; v++) {
+        if ((v >= 7 && k < 5) || (v >= 9 && k < 6)) break;
         Shape sh;
         sh.lanes = 1;
         sh.chunk = v < 3 ? 1 << v : 1 << ((v - 3) & 1);
         sh.blocks_per_sm = 0;
-        sh.prefix = v < 3 ? 1 : (v < 5 ? 2 : (v < 7 ? 3 : 4));
+        sh.prefix = v < 3 ? 1 : (v < 5 ? 2 : (v < 7 ? 3 : (v < 9 ? 4 : 5)));
         const double ms = time_shape(c, k, total, sh, s);
         if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
           best_ms = ms;

@@ -58,6 +58,25 @@ def _walk_three_level(N, k):
     return f
 
 
+def _walk_four_level(N, k):
+    f = 0.0
+    IP = k - 4
+    for pre in itertools.combinations(range(N), IP):
+        m = pre[-1] if IP else -1
+        zeros = [a for a in range(m + 1, N - 3)]
+        if not zeros:
+            continue
+        f += sum(bench.prefix_level_flops(i) for i in range(IP))
+        for a0 in zeros:
+            f += bench.prefix_level_flops(IP)
+            for a1 in range(a0 + 1, N - 2):
+                f += bench.prefix_level_flops(k - 3)
+                for a2 in range(a1 + 1, N - 1):
+                    f += bench.prefix_level_flops(k - 2)
+                    f += (N - 1 - a2) * (bench.prefix_level_flops(k - 1) + 2.0 * (k - 1))
+    return f
+
+
 @pytest.mark.parametrize("N", [7, 9])
 def test_prefix_counts_match_loop_walk(N):
     for k in range(3, N + 1):
@@ -67,6 +86,9 @@ def test_prefix_counts_match_loop_walk(N):
         assert bench.order_flops(N, k, 3) == bench.order_flops(N, k, 2)
         if k >= 5:
             assert bench.order_flops(N, k, 4) == pytest.approx(_walk_three_level(N, k),
+                                                               rel=1e-12)
+        if k >= 6:
+            assert bench.order_flops(N, k, 5) == pytest.approx(_walk_four_level(N, k),
                                                                rel=1e-12)
         assert bench.order_flops(N, k, 0) == math.comb(N, k) * bench.flops_model(k)
 

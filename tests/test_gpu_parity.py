@@ -504,14 +504,14 @@ def test_virtual_ranks_partition_and_merge():
 
 # ------------------------------------------------------------------ prefix-shared kernel
 @pytest.mark.parametrize("variant,chunk", [(1, 1), (1, 3), (2, 1), (2, 3), (3, 1), (3, 2),
-                                           (4, 1), (4, 3)])
+                                           (4, 1), (4, 3), (5, 1), (5, 2)])
 def test_prefix_kernel_every_order_matches_oracle(variant, chunk, tmp_path):
     # the prefix-shared kernels (bordered steps over a shared (k-1)-prefix,
     # variant 1, or (k-2)-prefix, variant 2, the latter with the last variables
     # two at a time, variant 3, and over a shared (k-3)-prefix with one stored
-    # step per next index, variant 4) on every order of the fMRI-shaped
-    # workload (odd and even numbers of last variables), every nplet against
-    # the oracle
+    # step per next index, variant 4, and over a (k-4)-prefix with two such
+    # steps, variant 5) on every order of the fMRI-shaped workload (odd and
+    # even numbers of last variables), every nplet against the oracle
     X, orders = workloads.fmri_like()
     S = oracle.copula_cov(X)
     with _ctx(X, out_f64=True) as c:
