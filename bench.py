@@ -48,7 +48,7 @@ def flops_model(k: int) -> float:
 # (145,422,675 nplets).  None: no capture of the current kernel.
 TRAFFIC_BYTES_PER_NPLET = {"dense": 0.00326, "group": 0.00375, "prefix": 0.00055,
                            "prefix2": 0.00061, "prefix2_pair": 0.00167, "prefix3_pair": 0.00076,
-                           "prefix4_pair": None}
+                           "prefix4_pair": 0.00070}
 
 
 def kernel_family(shape) -> str:
