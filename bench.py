@@ -382,7 +382,7 @@ def run_ours(args, rank, world, local_rank):
             ms.append(e0.elapsed_time(e1))
             nplet_ms.append(st.nplet_ms)
             ref_ms.append(st.refactor_ms)
-            launches += st.launches + 8  # + the copula-stage kernels of thoi_create
+            launches += st.launches + 6  # + the six copula-stage kernels of thoi_create
             nref = st.n_refactored
         if dist:
             dist.barrier()

@@ -269,7 +269,7 @@ static cudaError_t launch_reduce_t(const V* basis, unsigned long long stride_ele
 // buffers are cut and recut, whatever the order of the list.
 // Partials: SEL_SUB blocks (or the launch's count) per segment carry the
 // record fields, then one partial carries the two top lists.
-constexpr int CAND_SUB = 12;       // blocks per candidate segment
+constexpr int CAND_SUB = 48;       // blocks per candidate segment
 constexpr int SEL_SURV = 8192;     // gathered entries per side, at most
 constexpr int CAND_BINS = 2048;
 constexpr size_t CW_HIST1 = 0;
@@ -335,7 +335,6 @@ __global__ void __launch_bounds__(RED_NT) k_sel_pass(const SelSrc src, int pass,
   unsigned char* ws = src.ws;
   unsigned* gh1 = reinterpret_cast<unsigned*>(ws + CW_HIST1);
   unsigned* gh2 = reinterpret_cast<unsigned*>(ws + CW_HIST2);
-  const int* sel = reinterpret_cast<const int*>(ws + CW_SEL);
   unsigned* nsurv = reinterpret_cast<unsigned*>(ws + CW_SEL) + 8;
   V* sv = reinterpret_cast<V*>(ws + CW_SV);
   unsigned long long* si = reinterpret_cast<unsigned long long*>(ws + CW_SI);
@@ -346,43 +345,70 @@ __global__ void __launch_bounds__(RED_NT) k_sel_pass(const SelSrc src, int pass,
   ThreadRed<V, unsigned long long> tr;
   tr.init();
   unsigned notpd = 0;
-  // the selected bins (pass 1) and 22-bit thresholds (pass 2); a bin of -1
+  // the selected bins (pass 1) and 22-bit thresholds (pass 2), found by
+  // every block from the finished histograms (warp w: side w); a bin of -1
   // means fewer than M entries on that side: everything is kept
+  __shared__ int s_bin[4];
+  __shared__ unsigned s_above[4];
   int b1[2] = {0, 0};
   unsigned t22[2] = {0u, 0u};
   if (pass >= 1) {
+    if (threadIdx.x < 64) {
+      const int sd = threadIdx.x >> 5;
+      seed_find_bin(gh1 + sd * CAND_BINS, (unsigned)src.top_m, &s_bin[sd], &s_above[sd]);
+      __syncwarp();
+      if (pass == 2) {
+        if (s_bin[sd] < 0) {
+          if ((threadIdx.x & 31) == 0) s_bin[2 + sd] = -1;
+        } else {
+          seed_find_bin(gh2 + sd * CAND_BINS, (unsigned)src.top_m - s_above[sd], &s_bin[2 + sd],
+                        &s_above[2 + sd]);
+        }
+      }
+    }
+    __syncthreads();
     for (int sd = 0; sd < 2; sd++) {
-      b1[sd] = sel[sd];
-      const int b2 = sel[4 + sd];
+      b1[sd] = s_bin[sd];
+      const int b2 = pass == 2 ? s_bin[2 + sd] : 0;
       t22[sd] = (b1[sd] < 0 || b2 < 0) ? 0u : (((unsigned)b1[sd] << 11) | (unsigned)b2);
     }
   }
-  for (unsigned long long e = (unsigned long long)blockIdx.x * RED_NT + threadIdx.x; e < n;
-       e += (unsigned long long)gridDim.x * RED_NT) {
+  // every thread of a block runs the same rounds (the histogram increments
+  // are aggregated over the lanes of a warp that hit the same bin: the
+  // candidates crowd into the few bins near the bounds)
+  for (unsigned long long e0 = (unsigned long long)blockIdx.x * RED_NT; e0 < n;
+       e0 += (unsigned long long)gridDim.x * RED_NT) {
+    const unsigned long long e = e0 + threadIdx.x;
     const unsigned long long p = base + e;
-    const V lr = cb[p], sp = cb[src.stride + p], ls = cb[2 * src.stride + p];
-    if (is_nan(lr)) {
-      notpd += src.nan_notpd ? 1u : 0u;
-      continue;
+    bool ok = e < n;
+    V lr = (V)0, sp = (V)0, ls = (V)0;
+    if (ok) {
+      lr = cb[p];
+      sp = cb[src.stride + p];
+      ls = cb[2 * src.stride + p];
+      if (is_nan(lr)) {
+        notpd += src.nan_notpd ? 1u : 0u;
+        ok = false;
+      }
     }
     V v[5];
     combine5<V>(lr, sp, ls, cv, v);
     const V o = pick5(v, top);
     const float fo = (float)o;
-    const unsigned long long id = src.ids ? src.ids[p] : src.id0 + p;
+    const unsigned long long id = !ok ? 0ull : (src.ids ? src.ids[p] : src.id0 + p);
     if (pass == 0) {
-      tr.add(v, id, lr, sp, ls);
+      if (ok) tr.add(v, id, lr, sp, ls);
       if (src.top_m > 0) {
-        atomicAdd(&h[0][cand_key(fo, 0) >> 21], 1u);
-        atomicAdd(&h[1][cand_key(fo, 1) >> 21], 1u);
+        hist_add(h[0], cand_key(fo, 0) >> 21, ok);
+        hist_add(h[1], cand_key(fo, 1) >> 21, ok);
       }
     } else if (pass == 1) {
 #pragma unroll
       for (int sd = 0; sd < 2; sd++) {
         const unsigned k = cand_key(fo, sd);
-        if (b1[sd] >= 0 && (int)(k >> 21) == b1[sd]) atomicAdd(&h[sd][(k >> 10) & 2047u], 1u);
+        hist_add(h[sd], (k >> 10) & 2047u, ok && b1[sd] >= 0 && (int)(k >> 21) == b1[sd]);
       }
-    } else {
+    } else if (ok) {
 #pragma unroll
       for (int sd = 0; sd < 2; sd++) {
         if ((cand_key(fo, sd) >> 10) >= t22[sd]) {
@@ -418,33 +444,6 @@ __global__ void __launch_bounds__(RED_NT) k_sel_pass(const SelSrc src, int pass,
       r->notpd = 0;
       r->count = pidx == 0 ? src.rank_count - (fc < src.flag_cap ? fc : src.flag_cap) : 0ull;
     }
-  }
-}
-
-// The bin holding the target-th best of each side (warp w: side w).
-__global__ void k_sel_find(const SelSrc src, int pass) {
-  const int sd = threadIdx.x >> 5;
-  if (sd > 1) return;
-  unsigned char* ws = src.ws;
-  const unsigned* hist = reinterpret_cast<const unsigned*>(ws + (pass == 0 ? CW_HIST1 : CW_HIST2)) +
-                         sd * CAND_BINS;
-  int* sel = reinterpret_cast<int*>(ws + CW_SEL);
-  const unsigned M = (unsigned)src.top_m;
-  unsigned target = M;
-  if (pass == 1) {
-    if (sel[sd] < 0) {
-      if ((threadIdx.x & 31) == 0) sel[4 + sd] = -1;
-      return;
-    }
-    target = M - (unsigned)sel[2 + sd];
-  }
-  __shared__ int s_bin[2];
-  __shared__ unsigned s_above[2];
-  seed_find_bin(hist, target, &s_bin[sd], &s_above[sd]);
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0) {
-    sel[(pass == 0 ? 0 : 4) + sd] = s_bin[sd];
-    sel[(pass == 0 ? 2 : 6) + sd] = (int)s_above[sd];
   }
 }
 
@@ -539,9 +538,7 @@ static cudaError_t launch_select(const SelSrc& src, int gx, PartRec* part, TopEn
   int occ = 0;
   if ((e = occupancy_cached((const void*)k_sel_final<V>, 256, sm, &occ)) != cudaSuccess) return e;
   if (src.top_m > 0) {
-    k_sel_find<<<1, 64, 0, s>>>(src, 0);
     k_sel_pass<V><<<grid, RED_NT, 0, s>>>(src, 1, part);
-    k_sel_find<<<1, 64, 0, s>>>(src, 1);
     k_sel_pass<V><<<grid, RED_NT, 0, s>>>(src, 2, part);
     k_sel_final<V><<<2, 256, sm, s>>>(src, ptop, ttop);
   } else {

@@ -802,6 +802,9 @@ static thoi_status ensure_sel_ws(thoi_ctx* c) {
   CK(cudaMalloc(&c->sel_ws, 2 * sel_ws_bytes()));
   return THOI_OK;
 }
+// Kernels of one radix-select reduction: three passes and the final sort
+// (with top lists), else the first pass and an empty top partial.
+static int sel_kernels(int top_m) { return top_m > 0 ? 4 : 2; }
 static unsigned long long* fz_counts(thoi_ctx* c) { return (unsigned long long*)c->fz; }
 static unsigned* fz_keys(thoi_ctx* c) { return (unsigned*)(c->fz + FZ_COUNTS); }
 static unsigned long long* fz_ids(thoi_ctx* c) { return (unsigned long long*)(c->fz + FZ_HEAD); }
@@ -955,7 +958,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       md.g32 += grid;
       md.thr_keys = a.thr_keys;
       md.status = c->status;
-      launches += 3;
+      launches += 2 + sel_kernels(top_m);  // sample, nplet kernel, candidate reduction
     } else if (red && !f64) {
       // FP32 records: basis values per piece, then the streaming reduction
       // each of the three arrays starts on a 256-byte boundary (16-byte loads)
@@ -980,19 +983,23 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         if (st != THOI_OK) return st;
         st = prof_begin(c, s, 3);
         if (st != THOI_OK) return st;
-        if (sel && sub.r1 - sub.r0 <= FUSE_MIN_N)
-          CK(launch_select_basis(c->basis, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb,
-                                 top_m, c->sel_ws, c->status, c->part32 + p32_off,
+        const unsigned long long nsub = sub.r1 - sub.r0;
+        if (sel && nsub <= FUSE_MIN_N) {
+          CK(launch_select_basis(c->basis, bstride, nsub, r.off + sub.r0, md.cmb, top_m,
+                                 c->sel_ws, c->status, c->part32 + p32_off,
                                  top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
                                  blk_cap, s, &grid));
-        else
-          CK(launch_reduce_basis(c->basis, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb,
-                                 top_m, c->seed_thr, c->part32 + p32_off,
+          launches += 1 + sel_kernels(top_m);
+        } else {
+          CK(launch_reduce_basis(c->basis, bstride, nsub, r.off + sub.r0, md.cmb, top_m,
+                                 c->seed_thr, c->part32 + p32_off,
                                  top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
                                  c->num_sms, blk_cap, s, &grid));
+          // the nplet kernel, the reduction and (long ranges) its seed kernel
+          launches += 2 + (top_m > 0 && nsub > (1ull << 20) && md.cmb.top != THOI_H ? 1 : 0);
+        }
         st = prof_end(c, s);
         if (st != THOI_OK) return st;
-        launches += 2;
         p32_off += grid;
         md.g32 += grid;
       }
@@ -1105,6 +1112,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
                                     c->part64 + p64_off,
                                     top_m > 0 ? c->top64 + (size_t)p64_off * 2 * top_m : nullptr,
                                     ref_cap, sr, &grid));
+            launches += sel_kernels(top_m) - 1;  // (one counted below)
           } else {
             // few blocks: the list is short next to the order, and each
             // block's top lists then cover enough entries for the merge to
