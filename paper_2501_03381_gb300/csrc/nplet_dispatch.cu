@@ -48,8 +48,8 @@ static unsigned long long binom_u(int n, int k) {
 cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, cudaStream_t s,
                              int* grid_out, int max_blocks) {
   // the prefix-shared kernel covers whole orders only
-  if (sh.prefix && a.k >= KPFX_MIN && a.k <= KPFX_MAX && a.rank_begin == 0 &&
-      a.rank_end == binom_u(a.N, a.k)) {
+  if (sh.prefix && a.k >= KPFX_MIN && a.k <= (sh.prefix >= 2 ? KPFX2_MAX : KPFX_MAX) &&
+      a.rank_begin == 0 && a.rank_end == binom_u(a.N, a.k)) {
     switch (a.k) {
 #define CASE_P(KK)                                                                  \
   case KK:                                                                          \
@@ -59,6 +59,8 @@ cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, c
       CASE_P(11) CASE_P(12) CASE_P(13) CASE_P(14) CASE_P(15) CASE_P(16) CASE_P(17) CASE_P(18)
       CASE_P(19) CASE_P(20)
 #undef CASE_P
+      case 21: return launch_pfx2_k<21>(a, sh, num_sms, s, grid_out, max_blocks);
+      case 22: return launch_pfx2_k<22>(a, sh, num_sms, s, grid_out, max_blocks);
       default: break;
     }
   }

@@ -2540,7 +2540,7 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
     // where the prefix-shared kernel competes, every candidate is timed on
     // the whole order (that kernel covers whole orders only); elsewhere on the
     // first 2^22 nplets, scaled to the order
-    const bool pfx_candidate = k >= KPFX_MIN && k <= KPFX_MAX && total <= (1ull << 28);
+    const bool pfx_candidate = k >= KPFX_MIN && k <= KPFX2_MAX && total <= (1ull << 28);
     const uint64_t n = pfx_candidate ? total : (total < (1ull << 22) ? total : (1ull << 22));
     Shape best = default_shape(k);
     double best_ms = -1.0;
@@ -2572,6 +2572,7 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
       // variables two at a time, with 1, 2
       for (int v = 0; v < 11; v++) {
         if ((v >= 7 && k < 5) || (v >= 9 && k < 6)) break;
+        if (v < 3 && k > KPFX_MAX) continue;  // the one-level kernel stops at KPFX_MAX
         Shape sh;
         sh.lanes = 1;
         sh.chunk = v < 3 ? 1 << v : 1 << ((v - 3) & 1);
