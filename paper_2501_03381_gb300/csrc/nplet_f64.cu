@@ -23,10 +23,14 @@ __global__ void __launch_bounds__(NT) k_nplet_f64s(const NpletArgs a, double* __
   else f64g_body<NT, G, LIST, M>(a, b64, bstride, smem);
 }
 
-// Lanes per nplet and shared memory for (N, k): one thread per nplet while a
-// block of 128 matrices stays within F64_SMEM_TARGET (three or more blocks,
-// twelve or more warps per SM), else the fewest lanes per nplet that do.
-constexpr size_t F64_SMEM_TARGET = 72 * 1024;
+// Lanes per nplet and shared memory for (N, k): the fewest lanes per nplet
+// (one thread per nplet first) whose block stays within F64_SMEM_TARGET, so
+// that two blocks (eight warps) share an SM.  Fewer lanes per nplet leave
+// fewer of them idle in the triangular loops, and the FP64 pipe charges a
+// warp instruction whatever its active lanes; two blocks per SM keep it fed.
+// (Measured on N = 30: orders 18, 20, 22, 25, 28 each fastest with the G
+// this picks, against 72 KB, 100 KB and 128 KB targets.)
+constexpr size_t F64_SMEM_TARGET = 112 * 1024;
 constexpr int F64_NT = 128;
 
 F64Cfg f64_config(int N, int k) {

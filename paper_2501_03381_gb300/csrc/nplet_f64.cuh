@@ -124,12 +124,24 @@ __device__ __forceinline__ void f64g_factor(double* __restrict__ A, const int k,
       if ((p & 7) == 7 || p == k - 1) renorm(P1, E1, bad);
     }
     const int i0 = p + 1 + ((g - (p + 1) % G) + G) % G;  // first owned row > p
-    for (int i = i0; i < k; i += G) {
-      const double u = AG(i, p) * rd;
-      for (int j = p + 1; j <= i; j++) AG(i, j) = fma(-u, AG(j, p), AG(i, j));
+    // the multipliers of the owned rows are kept, then written over column p
+    // once every row has read it
+    double us[32 / G + 1];
+#pragma unroll
+    for (int t = 0; t < 32 / G + 1; t++) {
+      const int i = i0 + t * G;
+      if (i < k) {
+        const double u = AG(i, p) * rd;
+        for (int j = p + 1; j <= i; j++) AG(i, j) = fma(-u, AG(j, p), AG(i, j));
+        us[t] = u;
+      }
     }
     __syncwarp(gmask);
-    for (int i = i0; i < k; i += G) AG(i, p) *= rd;
+#pragma unroll
+    for (int t = 0; t < 32 / G + 1; t++) {
+      const int i = i0 + t * G;
+      if (i < k) AG(i, p) = us[t];
+    }
     __syncwarp(gmask);
   }
   // V = L^-1 in place
