@@ -130,7 +130,7 @@ struct Shape {
 };
 constexpr int KPFX_MIN = 3;   // orders with a prefix-shared kernel
 constexpr int KPFX_MAX = 20;   // the one-level kernel
-constexpr int KPFX2_MAX = 22;  // the two-, three- and four-level kernels
+constexpr int KPFX2_MAX = 24;  // the two-, three- and four-level kernels
 // Built-in launch shape of the FP32 kernel for order k (used when no tuned
 // shape is cached).
 Shape default_shape(int k);

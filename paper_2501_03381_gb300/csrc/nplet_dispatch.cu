@@ -61,6 +61,8 @@ cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, c
 #undef CASE_P
       case 21: return launch_pfx2_k<21>(a, sh, num_sms, s, grid_out, max_blocks);
       case 22: return launch_pfx2_k<22>(a, sh, num_sms, s, grid_out, max_blocks);
+      case 23: return launch_pfx2_k<23>(a, sh, num_sms, s, grid_out, max_blocks);
+      case 24: return launch_pfx2_k<24>(a, sh, num_sms, s, grid_out, max_blocks);
       default: break;
     }
   }

@@ -1,0 +1,7 @@
+// Instantiation of the two-, three- and four-level prefix-shared FP32 nplet
+// kernels for order 23 (beyond the one-level kernel's orders).
+#include "nplet_pfx2.cuh"
+
+namespace thoi {
+template cudaError_t launch_pfx2_k<23>(const NpletArgs&, const Shape&, int, cudaStream_t, int*, int);
+}  // namespace thoi

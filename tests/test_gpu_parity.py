@@ -596,12 +596,12 @@ def test_three_level_prefix_kernel_wide_masks(tmp_path):
 
 
 @pytest.mark.parametrize("variant", [2, 3, 4, 5])
-def test_prefix_kernels_orders_21_22(variant, tmp_path):
+@pytest.mark.parametrize("N,orders", [(24, [21, 22]), (26, [23, 24])])
+def test_prefix_kernels_orders_21_to_24(variant, N, orders, tmp_path):
     # the two-, three- and four-level kernels at the orders beyond the
-    # one-level kernel's (N = 24), every nplet against the oracle, per nplet
-    # and as records
-    S = workloads.random_corr(np.random.default_rng(33), 24)
-    orders = [21, 22]
+    # one-level kernel's, every nplet against the oracle, per nplet and as
+    # records
+    S = workloads.random_corr(np.random.default_rng(33), N)
     with _ctx(Sigma=S, out_f64=True, top_m=8) as c:
         for k in orders:
             _force_shape(c.h, k, 0, 1, 1, str(tmp_path / f"q{k}.json"), prefix=variant)
@@ -609,7 +609,7 @@ def test_prefix_kernels_orders_21_22(variant, tmp_path):
         got, _ = c.measures(orders)
         np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=TOL32)
         ids = np.arange(ref.shape[1], dtype=np.uint64)
-        ref_recs = oracle.reduce_per_order(24, orders, ref, ids, fl, top_m=8)
+        ref_recs = oracle.reduce_per_order(N, orders, ref, ids, fl, top_m=8)
         (recs, hi, lo), _ = c.measures(orders, reduction="per_order")
         for q, e in enumerate(ref_recs):
             np.testing.assert_allclose(recs[q]["min"], e["min"], atol=TOL32)
