@@ -51,7 +51,22 @@ __device__ __forceinline__ void bfused_tile(const BatchFArgs& b, const BatchFTil
   tb.cnt = s_tcnt;
   if (threadIdx.x == 0) s_tcnt[0] = s_tcnt[1] = 0;
   __syncthreads();
+  // start from the tightest bounds the slot's finished tiles have published
+  // (the M-th best of any subset bounds the M-th best of the slot)
   float thr_hi = -pinf<float>(), thr_lo = pinf<float>();
+  if (with_top && b.slot_thr) {
+    const unsigned khi = b.slot_thr[2 * tile.slot], klo = b.slot_thr[2 * tile.slot + 1];
+    if (khi) thr_hi = fkey32_value(khi);
+    if (klo) thr_lo = fkey32_value(~klo);
+  }
+  // a cut keeps the tighter of the tile's own M-th best and the slot's bound,
+  // and publishes it for the slot's other tiles
+  auto publish = [&]() {
+    if (threadIdx.x == 0 && b.slot_thr) {
+      if (thr_hi > -pinf<float>()) atomicMax(&b.slot_thr[2 * tile.slot], fkey32(thr_hi));
+      if (thr_lo < pinf<float>()) atomicMax(&b.slot_thr[2 * tile.slot + 1], ~fkey32(thr_lo));
+    }
+  };
   ThreadRed<float, unsigned> tr;
   tr.init();
   const CombineV<float> cmbv(sl.cmb);
@@ -90,12 +105,13 @@ __device__ __forceinline__ void bfused_tile(const BatchFArgs& b, const BatchFTil
       const bool c0 = tb.cnt[0] > BF_TRIGGER, c1 = tb.cnt[1] > BF_TRIGGER;
       if (c0) {
         top_sort_cut(tb, 0, top_m);
-        thr_hi = top_threshold(tb, 0, top_m);
+        thr_hi = fmaxf(thr_hi, top_threshold(tb, 0, top_m));
       }
       if (c1) {
         top_sort_cut(tb, 1, top_m);
-        thr_lo = top_threshold(tb, 1, top_m);
+        thr_lo = fminf(thr_lo, top_threshold(tb, 1, top_m));
       }
+      if (c0 | c1) publish();
       __syncthreads();
     }
   }
@@ -105,6 +121,9 @@ __device__ __forceinline__ void bfused_tile(const BatchFArgs& b, const BatchFTil
     top_sort_cut(tb, 1, top_m);
     th = tb.cnt[0];
     tl = tb.cnt[1];
+    thr_hi = fmaxf(thr_hi, top_threshold(tb, 0, top_m));
+    thr_lo = fminf(thr_lo, top_threshold(tb, 1, top_m));
+    publish();
     top_write(tb, top_m, id_off, b.part_top + (size_t)tile.pidx * 2 * top_m);
   }
   block_write_part<float, unsigned>(tr, 0u, id_off, sc, b.part + tile.pidx, th, tl);

@@ -343,6 +343,10 @@ struct BatchFArgs {
   PartRec* part;
   TopEnt* part_top;
   unsigned* tile_counter;           // zero before the launch
+  // per slot, the tightest top-M bounds any of its tiles has found (two
+  // order-preserving keys, the smallest side complemented; zero before the
+  // launch = none): later tiles of the slot start from them.  Null: none.
+  unsigned* slot_thr;
   int* status;
   const int* cancel;
   int chunk_k[KBATCH_MAX + 1];      // nplets per thread per round, by order

@@ -1760,6 +1760,7 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
   PartRec *part32, *part64;
   TopEnt *top32, *top64;
   unsigned* counters;
+  unsigned* slot_thr;
   const size_t n64 = (size_t)n_slots * B2;
   if ((st = plan_alloc(P, &d_ds, D)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &d_sl, n_slots)) != THOI_OK) return st;
@@ -1777,6 +1778,8 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
   if ((st = plan_alloc(P, &P->staging, per * (size_t)D)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &P->status, 1)) != THOI_OK) return st;
   if ((st = plan_alloc(P, &counters, BATCH_BANDS + 1)) != THOI_OK) return st;
+  if ((st = plan_alloc(P, &slot_thr, 2 * (size_t)(n_slots > 0 ? n_slots : 1))) != THOI_OK)
+    return st;
   for (int d = 0; d < D; d++) {
     for (int q = 0; q < no; q++) {
       const int si = slot_of[d * no + q];
@@ -1863,6 +1866,7 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
   ok(cudaMemsetAsync(P->status, 0, sizeof(int), s));
   ok(cudaMemsetAsync(P->flag_counts, 0, (size_t)(n_slots > 0 ? n_slots : 1) * 8, s));
   ok(cudaMemsetAsync(counters, 0, (BATCH_BANDS + 1) * sizeof(unsigned), s));
+  ok(cudaMemsetAsync(slot_thr, 0, 2 * (size_t)(n_slots > 0 ? n_slots : 1) * sizeof(unsigned), s));
   // the nplets: one persistent launch per band, largest orders first
   for (int b = BATCH_BANDS - 1; b >= 0 && e == cudaSuccess; b--) {
     if (band_t1[b] <= band_t0[b]) continue;
@@ -1870,6 +1874,7 @@ static thoi_status batch_build(thoi_ctx* const* ctxs, int D, int kmin, int kmax,
     bb.tiles = d_tiles + band_t0[b];
     bb.n_tiles = band_t1[b] - band_t0[b];
     bb.tile_counter = counters + b;
+    bb.slot_thr = slot_thr;
     ok(launch_batch_fused(b, wide, bb, maxN, 0, num_sms, s, nullptr));
     nl++;
     nnl++;
