@@ -31,8 +31,7 @@ __device__ void reduce_core(unsigned long long first, unsigned long long step,
                                                          PartRec* __restrict__ part,
                                                          TopEnt* __restrict__ part_top,
                                                          unsigned char* smem, RedScratch& sc,
-                                                         int* s_tcnt,
-                                                         unsigned long long scramble = 0) {
+                                                         int* s_tcnt) {
   using I = typename std::conditional<LIST, unsigned long long, unsigned>::type;
   const bool with_top = top_m > 0;
   TopBuf<V, I> tb;
@@ -71,19 +70,7 @@ __device__ void reduce_core(unsigned long long first, unsigned long long step,
       unsigned long long pos[RB_PER_THREAD];
 #pragma unroll
       for (int t = 0; t < RB_PER_THREAD; t++) pos[t] = e0 + t;
-      if (LIST && scramble) {
-        // a list read in the order e -> e * scramble mod n (a permutation when
-        // the multiplier is a prime not dividing n): values that trend along
-        // the list do not keep refilling the top buffers
-#pragma unroll
-        for (int t = 0; t < RB_PER_THREAD; t++) {
-          const bool ok = e0 + t < n;
-          pos[t] = ok ? ((e0 + t) * scramble) % n : 0ull;
-          lr[t] = ok ? blr[pos[t]] : pinf<V>() - pinf<V>();
-          sp[t] = ok ? bsp[pos[t]] : (V)0;
-          ls[t] = ok ? bls[pos[t]] : (V)0;
-        }
-      } else if (sizeof(V) == 4 && e0 + RB_PER_THREAD <= n) {
+      if (sizeof(V) == 4 && e0 + RB_PER_THREAD <= n) {
 #pragma unroll
         for (int g = 0; g < RB_VEC; g++) {
           const float4 fx = reinterpret_cast<const float4*>(blr)[q * RB_VEC + g];
