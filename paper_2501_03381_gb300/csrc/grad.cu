@@ -208,6 +208,22 @@ __global__ void __launch_bounds__(RED_NT) k_grad_reg(const NpletArgs a, const in
       const unsigned long long left = a.rank_end - r0;
       const int cnt = left < (unsigned long long)GRAD_CHUNK ? (int)left : GRAD_CHUNK;
       M mask = unrank_s<M>(r0, K, N, sb, K + 1);
+      // Consecutive ranks usually share their first K-1 variables: the
+      // contributions among those (the pairs x, y < K-1) are summed in
+      // registers while the prefix stays the same and added to the shared
+      // accumulator when it changes.  Neighbouring lanes share prefixes too,
+      // so per-nplet atomics on those pairs would serialise on one address.
+      constexpr int KP = K > 1 ? K - 1 : 1;
+      float Gacc[KP][KP];
+      int accc[KP];
+      M accp = 0;
+      bool has_acc = false;
+      auto flush_acc = [&]() {
+#pragma unroll
+        for (int x = 0; x < K - 1; x++)
+#pragma unroll
+          for (int y = 0; y <= x; y++) atomicAdd(&Gs[accc[x] * N + accc[y]], Gacc[x][y]);
+      };
       for (int jn = 0; jn < cnt; jn++) {
         int c[K];
         {
@@ -275,6 +291,21 @@ __global__ void __launch_bounds__(RED_NT) k_grad_reg(const NpletArgs a, const in
           float dinv[K];
 #pragma unroll
           for (int j = 0; j < K; j++) dinv[j] = 1.f / Pm[j][j];
+          const M pmask = mask & (mask - 1);  // the nplet without its largest variable
+          if (has_acc && pmask != accp) {
+            flush_acc();
+            has_acc = false;
+          }
+          if (!has_acc) {
+#pragma unroll
+            for (int x = 0; x < K - 1; x++) {
+              accc[x] = c[x];
+#pragma unroll
+              for (int y = 0; y <= x; y++) Gacc[x][y] = 0.f;
+            }
+            accp = pmask;
+            has_acc = true;
+          }
 #pragma unroll
           for (int x = 0; x < K; x++)
 #pragma unroll
@@ -288,11 +319,14 @@ __global__ void __launch_bounds__(RED_NT) k_grad_reg(const NpletArgs a, const in
                   qxy = fmaf(pxj * dinv[j], pjy, qxy);
                 }
               }
-              atomicAdd(&Gs[c[x] * N + c[y]], grad_entry_reg<K>(measure, x == y, Pm[x][y], qxy));
+              const float g = grad_entry_reg<K>(measure, x == y, Pm[x][y], qxy);
+              if (x < K - 1) Gacc[x][y] += g;
+              else atomicAdd(&Gs[c[x] * N + c[y]], g);
             }
         }
         if (jn + 1 < cnt) mask = lex_succ(mask, full);
       }
+      if (has_acc) flush_acc();
     }
     if (threadIdx.x == 0 && a.cancel && *(volatile const int*)a.cancel) s_stop = 1;
     __syncthreads();
