@@ -397,8 +397,10 @@ def run_ours(args, rank, world, local_rank):
     finally:
         P.thoi_destroy(h)
     try:
+        # the shapes the records path uses (the cache also holds the
+        # per-nplet output ones, "out": 1)
         shapes = {e["k"]: [e["lanes"], e["chunk"], e.get("prefix", 0)]
-                  for e in json.load(open(tune_path))}
+                  for e in json.load(open(tune_path)) if not e.get("out", 0)}
     except Exception:
         shapes = {}
     # measured FFMA and DFMA peaks of this GPU (self-written multiply-add

@@ -66,6 +66,10 @@ cudaError_t launch_nplet_f32(const NpletArgs& a, const Shape& sh, int num_sms, c
       default: break;
     }
   }
+  // a prefix shape's chunk counts prefixes per fetch: where the dense kernels
+  // run instead (a sub-range, an order the prefix kernels do not cover) they
+  // take their own default shape
+  if (sh.prefix) return launch_nplet_f32(a, default_shape(a.k), num_sms, s, grid_out, max_blocks);
   const int lanes = shape_available(a.k, sh.lanes) ? sh.lanes : default_shape(a.k).lanes;
   if (lanes == 2) {
     switch (a.k) {

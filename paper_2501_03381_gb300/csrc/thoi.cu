@@ -72,6 +72,10 @@ struct thoi_ctx {
   size_t b64_2_cap = 0;
   cudaStream_t s2 = nullptr;
   std::vector<cudaEvent_t> sev;  // per-slot "list filled" and "re-factor done" events
+  // group objectives (first context of a group): streams on which the
+  // datasets' passes run side by side, their join events and a fork event
+  std::vector<cudaStream_t> gs;
+  std::vector<cudaEvent_t> gev;
   unsigned long long* flag_counts = nullptr;  // [MAX_SLOTS]
   unsigned long long* work_ctr = nullptr;     // [MAX_SLOTS] prefix-kernel work counters
   PartRec* part32 = nullptr;
@@ -150,7 +154,10 @@ cudaError_t occupancy_cached(const void* fn, int block, size_t smem, int* occ) {
 }  // namespace thoi
 
 // ------------------------------------------------------------------ autotune cache
-// Process-wide: (GPU name, SM count, order, mask width) -> launch shape.
+// Process-wide: (GPU name, SM count, order, mask width, use) -> launch shape.
+// Two uses per order: records reduced in place (nothing stored per nplet),
+// and per-nplet output (every value stored at its rank, where the dense
+// kernels' coalesced stores can outweigh the prefix kernels' fewer FLOPs).
 static std::mutex g_tune_mu;
 static std::map<std::string, Shape> g_tune;
 // the batched kernel's per-order chunks, tuned on a batch (kept apart from
@@ -158,17 +165,18 @@ static std::map<std::string, Shape> g_tune;
 static std::map<std::string, Shape> g_tune_batch;
 static unsigned long long g_tune_gen = 0;  // bumped whenever g_tune changes
 
-static std::string tune_key(const char* gpu, int sms, int k, int wide) {
+static std::string tune_key(const char* gpu, int sms, int k, int wide, int out = 0) {
   char b[320];
-  snprintf(b, sizeof b, "%s|%d|%d|%d", gpu, sms, k, wide);
+  snprintf(b, sizeof b, "%s|%d|%d|%d|%d", gpu, sms, k, wide, out);
   return b;
 }
 
-static Shape shape_for(const thoi_ctx* c, int k) {
+// out: the launch stores every nplet's measures (per-nplet output)
+static Shape shape_for(const thoi_ctx* c, int k, int out) {
   if (c->force_shape_valid) return c->force_shape;
   if (c->opt.autotune) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune.find(tune_key(c->gpu_name, c->num_sms, k, c->N > 32));
+    auto it = g_tune.find(tune_key(c->gpu_name, c->num_sms, k, c->N > 32, out));
     if (it != g_tune.end()) return it->second;
   }
   return default_shape(k);
@@ -411,6 +419,8 @@ extern "C" void thoi_destroy(thoi_ctx* c) {
   free_ptr(c->b64_2);
   for (auto e : c->sev) cudaEventDestroy(e);
   if (c->s2) cudaStreamDestroy(c->s2);
+  for (auto e : c->gev) cudaEventDestroy(e);
+  for (auto q : c->gs) cudaStreamDestroy(q);
   free_ptr(c->flag_counts);
   free_ptr(c->work_ctr);
   free_ptr(c->part32);
@@ -912,7 +922,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
     md.p32_off = p32_off;
     md.p64_off = p64_off;
     md.refactored = f64 ? nullptr : c->flag_counts + si;
-    const Shape sh = shape_for(c, r.k);
+    const Shape sh = shape_for(c, r.k, kind == THOI_RED_NONE);
     // this order's re-factor list (the two lists alternate between orders)
     unsigned long long* const fids = (si & 1) ? c->flag_ids2 : c->flag_ids;
     double* const fb64 = (si & 1) ? c->b64_2 : c->b64;
@@ -1056,13 +1066,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
       if (f64 && !red && f64s_threads(c->N, r.k, nullptr) > 0)
         CK(launch_nplet_f64s(a, false, nullptr, 0, c->num_sms, s, &grid, cap));
       else if (f64) CK(launch_nplet_f64(a, c->num_sms, s, &grid, cap));
-      else if (!red && r.k <= 8) {
-        // per-nplet output of small orders is bound by its stores: the dense
-        // kernel writes them coalesced through shared memory
-        Shape sd = sh;
-        sd.prefix = 0;
-        CK(launch_nplet_f32(a, sd, c->num_sms, s, &grid, cap));
-      } else CK(launch_nplet_f32(a, sh, c->num_sms, s, &grid, cap));
+      else CK(launch_nplet_f32(a, sh, c->num_sms, s, &grid, cap));
       st = prof_end(c, s);
       if (st != THOI_OK) return st;
       launches++;
@@ -1266,6 +1270,9 @@ namespace {
 // each dataset's pass can use the prefix-shared kernels.
 constexpr unsigned long long GROUP_VALUE_BYTES = 1ull << 34;
 constexpr unsigned long long GROUP_PIECE_MIN = 1ull << 16;
+// streams for the datasets' passes: the passes of small orders are a few
+// short launches each, which run side by side instead of one after another
+constexpr int GROUP_STREAMS = 8;
 
 // Options of the group's contexts, restored on every exit (a context may
 // appear more than once: restored in reverse order).
@@ -1321,6 +1328,20 @@ static thoi_status group_meta(thoi_ctx* c0, cudaStream_t s, int** gstatus,
   return THOI_OK;
 }
 
+static thoi_status ensure_group_streams(thoi_ctx* c0, int ns) {
+  while ((int)c0->gs.size() < ns) {
+    cudaStream_t q;
+    CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+    c0->gs.push_back(q);
+  }
+  while ((int)c0->gev.size() < ns + 1) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c0->gev.push_back(e);
+  }
+  return THOI_OK;
+}
+
 // Queue the group pass (no synchronisation); the caller has set the
 // contexts' options (GroupSaved) and the group meta words.
 static thoi_status enqueue_group(thoi_ctx* const* ctxs, int D, const int32_t* orders,
@@ -1361,6 +1382,19 @@ static thoi_status enqueue_group(thoi_ctx* const* ctxs, int D, const int32_t* or
     ctxs[d]->opt.out_f64 = 1;
     ctxs[d]->opt.profile = 0;
   }
+  // one stream per distinct context (a context listed twice keeps its
+  // passes on one stream: they share its workspace), GROUP_STREAMS at most
+  std::vector<int> sidx(D);
+  int ns = 0;
+  for (int d = 0; d < D; d++) {
+    sidx[d] = -1;
+    for (int e = 0; e < d; e++)
+      if (ctxs[e] == ctxs[d]) sidx[d] = sidx[e];
+    if (sidx[d] < 0) sidx[d] = ns++ % GROUP_STREAMS;
+  }
+  if (ns > GROUP_STREAMS) ns = GROUP_STREAMS;
+  st = ensure_group_streams(c0, ns);
+  if (st != THOI_OK) return st;
   const Combine cg = group_combine();
   MergeDescs MD;
   memset(&MD, 0, sizeof MD);
@@ -1377,14 +1411,23 @@ static thoi_status enqueue_group(thoi_ctx* const* ctxs, int D, const int32_t* or
     for (unsigned long long a0 = r.r0; a0 < r.r1; a0 += piece) {
       const unsigned long long a1 = r.r1 - a0 > piece ? a0 + piece : r.r1;
       const unsigned long long n = a1 - a0;
+      // fork: the datasets' passes on the group streams, joined before the
+      // combine
+      CK(cudaEventRecord(c0->gev[ns], s));
+      for (int j = 0; j < ns; j++) CK(cudaStreamWaitEvent(c0->gs[j], c0->gev[ns], 0));
       for (int d = 0; d < D; d++) {
         thoi_ctx* cd = ctxs[d];
+        cudaStream_t sd = c0->gs[sidx[d]];
         int nl = 0;
         st = enqueue_measures(cd, &k, 1, a0, a1, THOI_RED_NONE, V + (size_t)d * ld, nullptr,
-                              nullptr, s, &nl);
+                              nullptr, sd, &nl);
         if (st != THOI_OK) return st;
-        CK(launch_group_fold(cd->status, cd->flag_counts, cd->flag_cap, gstatus, gnref + si, s));
+        CK(launch_group_fold(cd->status, cd->flag_counts, cd->flag_cap, gstatus, gnref + si, sd));
         launches += nl + 1;
+      }
+      for (int j = 0; j < ns; j++) {
+        CK(cudaEventRecord(c0->gev[j], c0->gs[j]));
+        CK(cudaStreamWaitEvent(s, c0->gev[j], 0));
       }
       ev += n * (uint64_t)D;
       CK(launch_group_combine(V, ld, n, nullptr, D, objective,
@@ -2466,13 +2509,19 @@ static void tune_load(const char* path, const char* gpu, int sms) {
     int prefix = 0;
     const char* pq = strstr(line, "\"prefix\"");
     if (pq && sscanf(pq, "\"prefix\": %d", &prefix) != 1) prefix = 0;
+    // "out": the use the shape was tuned for; an entry without it (a shape
+    // written by hand) serves both uses
+    int out = -1;
+    const char* oq = strstr(line, "\"out\"");
+    if (oq && sscanf(oq, "\"out\": %d", &out) != 1) out = -1;
     Shape sh;
     sh.lanes = lanes;
     sh.chunk = chunk;
     sh.blocks_per_sm = bps;
     sh.prefix = (prefix >= 0 && prefix <= 5) ? prefix : 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[tune_key(gpu, sms, k, wide)] = sh;
+    if (out != 1) g_tune[tune_key(gpu, sms, k, wide, 0)] = sh;
+    if (out != 0) g_tune[tune_key(gpu, sms, k, wide, 1)] = sh;
     g_tune_gen++;
   }
   fclose(f);
@@ -2486,13 +2535,13 @@ static void tune_save(const char* path, const char* gpu, int sms) {
   bool first = true;
   for (auto& kv : g_tune) {
     char g[256];
-    int sm, k, wide;
-    if (sscanf(kv.first.c_str(), "%255[^|]|%d|%d|%d", g, &sm, &k, &wide) != 4) continue;
+    int sm, k, wide, out;
+    if (sscanf(kv.first.c_str(), "%255[^|]|%d|%d|%d|%d", g, &sm, &k, &wide, &out) != 5) continue;
     if (strcmp(g, gpu) != 0 || sm != sms) continue;
     fprintf(f, "%s{\"gpu\": \"%s\", \"sms\": %d, \"k\": %d, \"wide\": %d, \"lanes\": %d, "
-               "\"chunk\": %d, \"blocks_per_sm\": %d, \"prefix\": %d}",
+               "\"chunk\": %d, \"blocks_per_sm\": %d, \"prefix\": %d, \"out\": %d}",
             first ? "" : ",\n", g, sm, k, wide, kv.second.lanes, kv.second.chunk,
-            kv.second.blocks_per_sm, kv.second.prefix);
+            kv.second.blocks_per_sm, kv.second.prefix, out);
     first = false;
   }
   fprintf(f, "\n]\n");
@@ -2500,8 +2549,11 @@ static void tune_save(const char* path, const char* gpu, int sms) {
 }
 
 // Time the FP32 nplet kernel of order k with shape sh on the first n nplets
-// (CUDA events on `s`); returns milliseconds or a negative value on error.
-static double time_shape(thoi_ctx* c, int k, uint64_t n, const Shape& sh, cudaStream_t s) {
+// (CUDA events on `s`), reducing to records, or with out (device, room for
+// the n nplets' five measures) storing every nplet's measures; returns
+// milliseconds or a negative value on error.
+static double time_shape(thoi_ctx* c, int k, uint64_t n, const Shape& sh, cudaStream_t s,
+                         void* out = nullptr) {
   const int saved_profile = c->opt.profile;
   c->opt.profile = 1;
   c->force_shape = sh;
@@ -2515,9 +2567,12 @@ static double time_shape(thoi_ctx* c, int k, uint64_t n, const Shape& sh, cudaSt
     for (int rep = 0; rep < 3; rep++) {
       int launches = 0;
       thoi_stats st;
-      if (enqueue_measures(c, &ord, 1, 0, n, THOI_RED_PER_ORDER, nullptr, recs, tops, s,
-                           &launches, true) != THOI_OK)
-        break;
+      const thoi_status es =
+          out ? enqueue_measures(c, &ord, 1, 0, n, THOI_RED_NONE, out, nullptr, nullptr, s,
+                                 &launches)
+              : enqueue_measures(c, &ord, 1, 0, n, THOI_RED_PER_ORDER, nullptr, recs, tops, s,
+                                 &launches, true);
+      if (es != THOI_OK) break;
       const thoi_status fs = finish_status(c, s, 1, &st, n, launches);
       if (fs != THOI_OK && fs != THOI_ERR_NOT_PD) break;
       if (rep > 0 && (best < 0 || st.nplet_ms < best)) best = st.nplet_ms;  // rep 0 warms up
@@ -2535,10 +2590,12 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
   cudaStream_t s = (cudaStream_t)stream;
   if (cache_path) tune_load(cache_path, c->gpu_name, c->num_sms);
   const int wide = c->N > 32;
+  void* ob = nullptr;  // output buffer for timing per-nplet output
+  size_t ob_cap = 0;
   for (int k = kmin; k <= kmax; k++) {
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
-      if (g_tune.count(tune_key(c->gpu_name, c->num_sms, k, wide))) continue;
+      if (g_tune.count(tune_key(c->gpu_name, c->num_sms, k, wide, 0))) continue;
     }
     const uint64_t total = binom_host(c->N, k);
     if (total < (1ull << 17)) continue;  // too small to matter: built-in shape
@@ -2567,6 +2624,9 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
         }
       }
     }
+    const Shape best_dense = best;
+    Shape best_pfx = best;
+    double pfx_ms = -1.0;
     // the prefix-shared kernel covers whole orders: timed on the whole order
     // when that is affordable (up to 2^28 nplets)
     if (pfx_candidate) {
@@ -2584,16 +2644,46 @@ extern "C" thoi_status thoi_autotune(thoi_ctx* c, int32_t kmin, int32_t kmax, co
         sh.blocks_per_sm = 0;
         sh.prefix = v < 3 ? 1 : (v < 5 ? 2 : (v < 7 ? 3 : (v < 9 ? 4 : 5)));
         const double ms = time_shape(c, k, total, sh, s);
+        if (ms > 0 && (pfx_ms < 0 || ms < pfx_ms)) {
+          pfx_ms = ms;
+          best_pfx = sh;
+        }
         if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
           best_ms = ms;
           best = sh;
         }
       }
     }
+    // per-nplet output: the best dense and the best prefix shape timed again
+    // storing every nplet's measures (the prefix kernels' stores are
+    // scattered); the dense shape where no prefix shape ran or the output
+    // buffer cannot be had
+    Shape best_out = best_dense;
+    if (pfx_ms > 0) {
+      const size_t ob_need = (size_t)5 * total * (c->opt.out_f64 ? 8 : 4);
+      if (ob_need > ob_cap) {
+        if (ob) cudaFree(ob);
+        ob = nullptr;
+        ob_cap = 0;
+        if (cudaMalloc(&ob, ob_need) == cudaSuccess) {
+          ob_cap = ob_need;
+        } else {
+          ob = nullptr;
+          cudaGetLastError();
+        }
+      }
+      if (ob) {
+        const double md = time_shape(c, k, total, best_dense, s, ob);
+        const double mp = time_shape(c, k, total, best_pfx, s, ob);
+        if (mp > 0 && (md < 0 || mp < md)) best_out = best_pfx;
+      }
+    }
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[tune_key(c->gpu_name, c->num_sms, k, wide)] = best;
+    g_tune[tune_key(c->gpu_name, c->num_sms, k, wide, 0)] = best;
+    g_tune[tune_key(c->gpu_name, c->num_sms, k, wide, 1)] = best_out;
     g_tune_gen++;
   }
+  if (ob) cudaFree(ob);
   if (cache_path) tune_save(cache_path, c->gpu_name, c->num_sms);
   return THOI_OK;
 }

@@ -426,6 +426,9 @@ def test_autotune_cache_and_parity(tmp_path):
         ks = sorted(e["k"] for e in ents)
         # the cache is process-wide: earlier tunings in this process are kept too
         assert {12, 13, 14} <= set(ks)
+        # one shape per order for records reduced in place, one for per-nplet output
+        uses = {(e["k"], e["out"]) for e in ents}
+        assert {(k, u) for k in (12, 13, 14) for u in (0, 1)} <= uses
         for e in (e for e in ents if 12 <= e["k"] <= 14):
             if e.get("prefix", 0):
                 assert e["lanes"] == 1 and e["chunk"] in (1, 2, 4)
