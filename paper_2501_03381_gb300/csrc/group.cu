@@ -28,11 +28,12 @@ constexpr int GRP_NT = 256;
 __global__ void k_group_fold(const int* status, const unsigned long long* flag_count,
                              unsigned long long flag_cap, int* gstatus,
                              unsigned long long* gnref) {
+  // atomics: the datasets' passes (and their folds) run on several streams
   const int st = *status;
-  if (st) *gstatus |= st;
+  if (st) atomicOr(gstatus, st);
   if (flag_count) {
     const unsigned long long f = *flag_count;
-    *gnref += f < flag_cap ? f : flag_cap;
+    atomicAdd(gnref, f < flag_cap ? f : flag_cap);
   }
 }
 

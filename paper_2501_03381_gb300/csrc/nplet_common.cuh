@@ -617,31 +617,40 @@ struct FusedAcc {
 };
 
 // Warp-aggregated append of one nplet (id and basis values) to the
-// candidate list; overflow raises ST_CAND_OVERFLOW (the order is then redone
-// with stored basis values).
+// candidate list, starting at the block's segment. Entries that do not fit
+// go on to the next segment: a kernel that takes its work dynamically may
+// leave most candidates to a few blocks. Only a full list raises
+// ST_CAND_OVERFLOW (the order is then redone with stored basis values).
 __device__ __forceinline__ void cand_append(const NpletArgs& a, bool cand, unsigned long long gid,
                                             float lr, float sp, float lsum) {
   const unsigned act = __activemask();
-  const unsigned fl = __ballot_sync(act, cand);
+  unsigned fl = __ballot_sync(act, cand);
   if (!fl) return;
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(fl) - 1;
-  const int seg = (int)(blockIdx.x % (unsigned)a.cand_nseg);
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(a.cand_count + seg, (unsigned long long)__popc(fl));
-  if (cand) {
-    base = __shfl_sync(fl, base, leader);
-    const unsigned long long pos = base + __popc(fl & ((1u << lane) - 1u));
-    if (pos < a.cand_seg) {
-      const unsigned long long e = (unsigned long long)seg * a.cand_seg + pos;
-      a.cand_ids[e] = gid;
-      a.cand_b[e] = lr;
-      a.cand_b[a.cand_cap + e] = sp;
-      a.cand_b[2 * a.cand_cap + e] = lsum;
-    } else {
-      atomicOr(a.status, ST_CAND_OVERFLOW);
+  int seg = (int)(blockIdx.x % (unsigned)a.cand_nseg);
+  // fl, t and seg are the same in every lane of act: the loop is warp-uniform
+  for (int t = 0; t < a.cand_nseg && fl; t++) {
+    const int leader = __ffs(fl) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(a.cand_count + seg, (unsigned long long)__popc(fl));
+    base = __shfl_sync(act, base, leader);
+    bool left = false;
+    if ((fl >> lane) & 1u) {
+      const unsigned long long pos = base + __popc(fl & ((1u << lane) - 1u));
+      if (pos < a.cand_seg) {
+        const unsigned long long e = (unsigned long long)seg * a.cand_seg + pos;
+        a.cand_ids[e] = gid;
+        a.cand_b[e] = lr;
+        a.cand_b[a.cand_cap + e] = sp;
+        a.cand_b[2 * a.cand_cap + e] = lsum;
+      } else {
+        left = true;
+      }
     }
+    fl = __ballot_sync(act, left);
+    seg = seg + 1 == a.cand_nseg ? 0 : seg + 1;
   }
+  if ((fl >> lane) & 1u) atomicOr(a.status, ST_CAND_OVERFLOW);
 }
 
 // Mode 4: a block's extremes of sampled nplets into the slot's bound keys

@@ -85,6 +85,49 @@ def test_fused_matches_oracle_fmri_like():
                                                                lo[q]["value"][:n]]), atol=TOL32)
 
 
+def _force_shape(h, k, prefix, chunk, path):
+    import json
+    props = torch.cuda.get_device_properties(0)
+    ent = {"gpu": props.name, "sms": props.multi_processor_count, "k": k, "wide": 0,
+           "lanes": 1, "chunk": chunk, "blocks_per_sm": 0, "prefix": prefix}
+    with open(path, "w") as fh:
+        fh.write("[\n" + json.dumps(ent) + "\n]\n")
+    P.thoi_autotune(h, k, k, path)
+
+
+@pytest.mark.parametrize("prefix,chunk", [(0, 8), (1, 1), (3, 1), (5, 2)])
+def test_fused_single_orders_need_no_retry(prefix, chunk, tmp_path):
+    # one small order per request (its candidate list is then sized to the
+    # order itself), with the dense kernel and with prefix kernels, which
+    # take their work dynamically and may leave most candidates to a few
+    # blocks: entries go on to other segments of the list instead of
+    # forcing the stored-value retry
+    X, _ = workloads.fmri_like()
+    S = oracle.copula_cov(X)
+    ks = (3, 4, 5, 6, 7, 8)
+    with P.Context(torch.as_tensor(X, device="cuda"), records_mode="fused") as c:
+        try:
+            for k in ks:
+                _force_shape(c.h, k, prefix, chunk, str(tmp_path / f"s{k}.json"))
+                vals, fl = oracle.measures(S, [k])
+                ids = np.arange(vals.shape[1], dtype=np.uint64)
+                e = oracle.reduce_per_order(20, [k], vals, ids, fl, top_m=256)[0]
+                (recs, hi, lo), st = c.measures([k], reduction="per_order")
+                assert st.fused_retries == 0, k
+                r = recs[0]
+                assert int(r["count"]) == e["count"] + e["n_not_pd"]
+                np.testing.assert_allclose(r["min"], e["min"], atol=TOL32)
+                np.testing.assert_allclose(r["max"], e["max"], atol=TOL32)
+                n = int(r["top_count"])
+                assert n == min(256, e["count"])
+                np.testing.assert_allclose(hi[0]["value"][:n], e["top_hi_val"][:n], atol=TOL32)
+                np.testing.assert_allclose(lo[0]["value"][:n], e["top_lo_val"][:n], atol=TOL32)
+        finally:
+            # the shape cache is process-wide: leave the dense default behind
+            for k in ks:
+                _force_shape(c.h, k, 0, 8, str(tmp_path / f"d{k}.json"))
+
+
 @pytest.mark.parametrize("top_m", [0, 1, 7, 1024])
 def test_fused_top_m_edges_and_subranges(top_m):
     X, orders = workloads.fmri_like()
