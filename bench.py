@@ -45,10 +45,11 @@ def flops_model(k: int) -> float:
 # DRAM bytes per nplet of the FP32 nplet kernels with records reduced inside
 # them, from ncu captures on this workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch / its nplets), each family at order 16
-# (145,422,675 nplets).  None: no capture of the current kernel.
-TRAFFIC_BYTES_PER_NPLET = {"dense": 0.00326, "group": 0.00375, "prefix": 0.00055,
-                           "prefix2": 0.00061, "prefix2_pair": 0.00167, "prefix3_pair": 0.00076,
-                           "prefix4_pair": 0.00070}
+# (145,422,675 nplets), taken after the last change to these kernels.
+# None: no capture of the current kernel.
+TRAFFIC_BYTES_PER_NPLET = {"dense": 0.00089, "group": 0.00096, "prefix": 0.00099,
+                           "prefix2": 0.00055, "prefix2_pair": 0.00062, "prefix3_pair": 0.00067,
+                           "prefix4_pair": 0.00294}
 
 
 def kernel_family(shape) -> str:
