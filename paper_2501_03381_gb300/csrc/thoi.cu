@@ -2127,10 +2127,13 @@ static uint64_t rank_to_mask(int N, int k, uint64_t rank) {
 // sets (k_greedy_expand), the FP64 list evaluation, the list reduction and
 // the merge into that order's records; the host reads all orders' top lists
 // once at the end.
+// sel: each order's list reduced by the radix select (else by the streaming
+// reduction, which the search falls back to when a select gathers too many
+// tied entries).
 static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int32_t k0,
                                int32_t k1, int32_t kappa, int32_t measure, int32_t maximize,
                                uint64_t* sets_out, double* values_out, thoi_stats* stats,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool sel = true) {
   thoi_ctx* c = ctxs[0];
   const bool group = objective >= 0;
   const int N = c->N;
@@ -2271,6 +2274,10 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
   // orders k0+1 .. k1: expansion of the selection, on the device
   int red_blocks = (int)(cap / 4096) + 1;  // few candidates: a few blocks, few lists to merge
   if (red_blocks > ref_cap) red_blocks = ref_cap;
+  if (sel) {
+    st = ensure_sel_ws(c);
+    if (st != THOI_OK) return st;
+  }
   for (int k = k0 + 1; k <= k1; k++) {
     const int lv = k - k0;
     unsigned long long* cnt = d_cnt + lv;
@@ -2315,8 +2322,14 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
       rb = gb;
     }
     int grid = 0;
-    CK(launch_reduce_list64(rb, lstride, d_ids, cnt, cap, rc, kappa, part, ptop, c->num_sms,
-                            red_blocks, s, &grid));
+    if (sel) {
+      CK(launch_select_list64(rb, lstride, d_ids, cnt, cap, rc, kappa, c->sel_ws, c->status, part,
+                              ptop, ref_cap, s, &grid));
+      launches += sel_kernels(kappa) - 1;  // (one counted below)
+    } else {
+      CK(launch_reduce_list64(rb, lstride, d_ids, cnt, cap, rc, kappa, part, ptop, c->num_sms,
+                              red_blocks, s, &grid));
+    }
     MergeDescs MD;
     memset(&MD, 0, sizeof MD);
     MD.d[0].p32_off = 0;
@@ -2345,6 +2358,9 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
     hs |= h;
   }
   CK(cudaStreamSynchronize(s));
+  if (sel && (hs & ST_INEXACT) && !(hs & ST_CANCELLED))
+    return greedy_impl(ctxs, D, objective, k0, k1, kappa, measure, maximize, sets_out, values_out,
+                       stats, s, false);
   uint64_t evaluated = binom_host(N, k0);
   for (int lv = 0; lv < levels; lv++) {
     const int k = k0 + lv;

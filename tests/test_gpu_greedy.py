@@ -69,3 +69,11 @@ def test_greedy_planted_redundancy():
         np.testing.assert_allclose(values[lvl], vals, rtol=0, atol=1e-10)
         if lvl + 3 <= 8:
             assert all(max(s) <= 9 for s in sets)
+
+
+def test_greedy_all_ties_fall_back_to_streaming_reduction():
+    # identity correlation: every candidate's O is exactly 0, so each order's
+    # radix select gathers more tied entries than it may keep and the search
+    # is repeated with the streaming reduction; ties go to the smallest rank
+    S = np.eye(60)
+    _compare(S, 3, 5, 256, "O", True)
