@@ -206,6 +206,13 @@ cudaError_t launch_select_basis(const float* basis, unsigned long long stride_el
                                 unsigned long long n, unsigned long long id0, Combine cmb,
                                 int top_m, unsigned char* ws, int* status, PartRec* part,
                                 TopEnt* part_top, int max_blocks, cudaStream_t s, int* grid_out);
+// A dense range of FP64 basis values (ids id0 + position; NaN = not
+// positive definite):
+cudaError_t launch_select_basis64(const double* basis, unsigned long long stride_elems,
+                                  unsigned long long n, unsigned long long id0, Combine cmb,
+                                  int top_m, unsigned char* ws, int* status, PartRec* part,
+                                  TopEnt* part_top, int max_blocks, cudaStream_t s,
+                                  int* grid_out);
 // A re-factor list of FP64 basis values (count on the device, at most cap
 // entries; NaN = not positive definite):
 cudaError_t launch_select_list64(const double* basis, unsigned long long stride_elems,

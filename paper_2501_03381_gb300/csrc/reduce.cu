@@ -597,6 +597,30 @@ cudaError_t launch_select_basis(const float* basis, unsigned long long stride_el
   return launch_select<float>(src, (int)gx, part, part_top, s, grid_out);
 }
 
+cudaError_t launch_select_basis64(const double* basis, unsigned long long stride_elems,
+                                  unsigned long long n, unsigned long long id0, Combine cmb,
+                                  int top_m, unsigned char* ws, int* status, PartRec* part,
+                                  TopEnt* part_top, int max_blocks, cudaStream_t s,
+                                  int* grid_out) {
+  SelSrc src;
+  memset(&src, 0, sizeof src);
+  src.basis = basis;
+  src.stride = stride_elems;
+  src.id0 = id0;
+  src.n = n;
+  src.nseg = 1;
+  src.nan_notpd = 1;  // the FP64 path marks a nplet that is not positive definite by a NaN
+  src.cmb = cmb;
+  src.top_m = top_m;
+  src.status = status;
+  src.ws = ws;
+  long long gx = (long long)((n + SEL_PER_BLOCK - 1) / SEL_PER_BLOCK);
+  if (gx < 1) gx = 1;
+  if (gx > max_blocks - 1) gx = max_blocks - 1;
+  if (gx < 1) return cudaErrorInvalidValue;
+  return launch_select<double>(src, (int)gx, part, part_top, s, grid_out);
+}
+
 cudaError_t launch_select_list64(const double* basis, unsigned long long stride_elems,
                                  const unsigned long long* ids, const unsigned long long* count,
                                  unsigned long long cap, Combine cmb, int top_m,

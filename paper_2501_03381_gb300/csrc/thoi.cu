@@ -828,7 +828,8 @@ static unsigned char* fz_ws(thoi_ctx* c) { return c->fz + FZ_HEAD + (size_t)c->f
 static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t n_orders,
                                     uint64_t id_begin, uint64_t id_end, int32_t kind, void* out_dev,
                                     thoi_order_record* recs_dev, TopEnt* tops_dev,
-                                    cudaStream_t s, int* launches_out, bool fuse = false) {
+                                    cudaStream_t s, int* launches_out, bool fuse = false,
+                                    bool sel64 = false) {
   std::vector<SlotRange> slots;
   thoi_status st = plan_slots(c, orders, n_orders, id_begin, &id_end, &slots);
   if (st != THOI_OK) return st;
@@ -860,7 +861,7 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
   // radix-select reductions (short stored ranges, re-factor lists) on the
   // first pass of a records request; a repeat uses the streaming reductions
   const bool sel = fuse && red && c->opt.records_mode != THOI_RECORDS_STORED;
-  if (sel) {
+  if (sel || sel64) {
     st = ensure_sel_ws(c);
     if (st != THOI_OK) return st;
   }
@@ -1032,10 +1033,20 @@ static thoi_status enqueue_measures(thoi_ctx* c, const int32_t* orders, int32_t 
         if (st != THOI_OK) return st;
         st = prof_begin(c, s, 3);
         if (st != THOI_OK) return st;
-        CK(launch_reduce_basis64(c->b64, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb, top_m,
-                                 c->part32 + p32_off,
-                                 top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
-                                 c->num_sms, blk_cap, s, &grid));
+        if (sel64 && sub.r1 - sub.r0 <= FUSE_MIN_N) {
+          // a short range by the radix select (ST_INEXACT: the caller repeats
+          // the request without it)
+          CK(launch_select_basis64(c->b64, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb,
+                                   top_m, c->sel_ws, c->status, c->part32 + p32_off,
+                                   top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
+                                   blk_cap, s, &grid));
+          launches += sel_kernels(top_m) - 1;
+        } else {
+          CK(launch_reduce_basis64(c->b64, bstride, sub.r1 - sub.r0, r.off + sub.r0, md.cmb,
+                                   top_m, c->part32 + p32_off,
+                                   top_m > 0 ? c->top32 + (size_t)p32_off * 2 * top_m : nullptr,
+                                   c->num_sms, blk_cap, s, &grid));
+        }
         st = prof_end(c, s);
         if (st != THOI_OK) return st;
         launches += 2;
@@ -2266,7 +2277,7 @@ static thoi_status greedy_impl(thoi_ctx* const* ctxs, int D, int objective, int3
                          &nl, &ev);
     } else {
       st = enqueue_measures(c, &ord, 1, 0, binom_host(N, k0), THOI_RED_PER_ORDER, nullptr,
-                            rec_at(0), tops_at(0), s, &nl);
+                            rec_at(0), tops_at(0), s, &nl, false, sel);
     }
     if (st != THOI_OK) return st;
     launches += nl;
