@@ -103,3 +103,14 @@ def test_dense_model_and_workload_totals():
     for k in range(5, 21):
         assert bench.prefix2_order_flops(30, k) < bench.prefix_order_flops(30, k) < \
             math.comb(30, k) * bench.flops_model(k)
+
+
+def test_traffic_figure_for_every_kernel_family():
+    # every launch shape the autotuner can store maps to a kernel family with
+    # a captured DRAM figure, and every figure is far below the 12 B of basis
+    # values per nplet that the stored records path wrote
+    shapes = [(1, 8, 0), (2, 8, 0), (4, 8, 0)] + [(1, c, p) for p in range(1, 6) for c in (1, 2)]
+    fams = {bench.kernel_family(s) for s in shapes}
+    assert fams == set(bench.TRAFFIC_BYTES_PER_NPLET)
+    for fam, b in bench.TRAFFIC_BYTES_PER_NPLET.items():
+        assert b is None or 0.0 < b < 0.01, fam
