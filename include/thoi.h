@@ -321,9 +321,9 @@ thoi_status thoi_set_cancel(thoi_ctx* ctx, int32_t flag);
  * (1 MiB per device, held from library load until process exit) is one
  * static device array shared by all calls: calls whose work overlaps on the
  * GPU (different streams, or different host threads) race on it and must be
- * serialised by the caller.  The call cannot be used while `stream` is being
- * captured into a graph: it queries pointer attributes, copies the status word
- * to host memory and synchronises `stream`.  Sigma, rec_out and top_out must
+ * serialised by the caller.  Before it returns, the call queries pointer
+ * attributes, copies the status word to host memory and synchronises
+ * `stream`.  Sigma, rec_out and top_out must
  * be memory of the current device (THOI_ERR_INVALID_ARG otherwise).  Returns
  * THOI_ERR_TOO_LARGE for N > 64, top_m > 16 or C(N, k) >= 2^32; synchronises
  * `stream`; THOI_ERR_NOT_PD when a nplet is not positive definite. */
